@@ -1,0 +1,430 @@
+"""Pins for the FP64 oracle, each against something other than the oracle.
+
+Section references are to Ganapathi (2022).  A plausible mistake in the
+oracle (a dropped term, a flipped sign, a transposed tap index, a wrong
+normalisation) fails at least one of these:
+
+* PRF pixel integral vs scipy quadrature; footprint orientation via the
+  centroid and via hand-placed sources;
+* hand-worked base pixels and phases (tests/golden/trajectory_shifts.txt);
+* a paper-literal dense-template brute force and a whole-frame numpy
+  implementation vs the C loops;
+* v = 0 vs scipy.signal.correlate2d; integer velocities and the single-tap
+  (shift-stack, Section 3.2) filter vs numpy roll-and-add;
+* noiseless injection (Section 4.1): flux estimate N/D equals the injected
+  flux and SNR = f sqrt(D);
+* linearity, noise scaling, mask invariance, translation equivariance;
+* on pure Gaussian noise with the right sigma, SNR has mean 0 and variance 1
+  (the matched filter is the maximum-likelihood detector, Section 3.2);
+* injected movers are recovered at their start pixel and trajectory.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, signal, stats
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- PRF ----
+
+@pytest.mark.parametrize("a,phase,sigma", [(0, 0.0, 0.7), (1, 0.3, 0.7), (-2, -0.45, 0.7),
+                                           (2, 0.5, 1.3), (-1, 0.1, 0.35)])
+def test_pixel_integral_matches_quadrature(oracle, a, phase, sigma):
+    pdf = stats.norm(loc=phase, scale=sigma).pdf
+    want, _ = integrate.quad(pdf, a - 0.5, a + 0.5, epsabs=1e-15, epsrel=1e-13)
+    got = oracle.oracle.pixel_integrated_gauss(a, phase, sigma)
+    assert abs(got - want) < 1e-13
+
+
+def test_prf_taps_from_quadrature(oracle):
+    phx, phy, sig = 0.31, -0.22, 0.7
+    pdf_x = stats.norm(loc=phx, scale=sig).pdf
+    pdf_y = stats.norm(loc=phy, scale=sig).pdf
+    want = np.zeros((5, 5))
+    for dy in range(-2, 3):
+        iy, _ = integrate.quad(pdf_y, dy - 0.5, dy + 0.5, epsabs=1e-15)
+        for dx in range(-2, 3):
+            ix, _ = integrate.quad(pdf_x, dx - 0.5, dx + 0.5, epsabs=1e-15)
+            want[dy + 2, dx + 2] = ix * iy
+    want /= want.sum()
+    got = oracle.prf_taps(phx, phy, sig, 0)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_prf_orientation_and_symmetry(oracle, kind):
+    d = np.arange(-2, 3)
+    w = oracle.prf_taps(0.4, 0.0, 0.7, kind)
+    assert abs(w.sum() - 1) < 1e-14
+    # a source displaced towards +x puts its mass at larger column index
+    assert (w * d[None, :]).sum() > 0.2
+    assert abs((w * d[:, None]).sum()) < 1e-14
+    w2 = oracle.prf_taps(0.0, -0.3, 0.7, kind)
+    assert (w2 * d[:, None]).sum() < -0.15
+    np.testing.assert_allclose(oracle.prf_taps(0.1, 0.35, 0.7, kind),
+                               oracle.prf_taps(0.35, 0.1, 0.7, kind).T, atol=1e-15)
+    np.testing.assert_allclose(oracle.prf_taps(0.2, -0.4, 0.7, kind),
+                               oracle.prf_taps(-0.2, 0.4, 0.7, kind)[::-1, ::-1], atol=1e-15)
+
+
+def test_point_sampled_kind(oracle):
+    w = oracle.prf_taps(0.0, 0.0, 0.7, 1)
+    # ratio of neighbour to centre of a sampled Gaussian is exp(-1/(2 s^2))
+    assert abs(w[2, 3] / w[2, 2] - np.exp(-1 / (2 * 0.49))) < 1e-14
+    assert abs(w[3, 3] / w[2, 2] - np.exp(-2 / (2 * 0.49))) < 1e-14
+
+
+# ---------------------------------------------------------- trajectories --
+
+def _golden_shifts():
+    rows = []
+    with open(os.path.join(HERE, "golden", "trajectory_shifts.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                v, t, s, ph = line.split()
+                rows.append((float(v), int(t), int(s), float(ph)))
+    return rows
+
+
+def test_trajectory_shifts_golden(oracle):
+    rows = _golden_shifts()
+    assert len(rows) >= 20
+    for v, t, s, ph in rows:
+        T = t + 1
+        shifts, taps = oracle.trajectory_table([v, 0.0], [0.0, v], T, 0.7, 0)
+        assert shifts[0, t, 0] == s and shifts[0, t, 1] == 0, (v, t)
+        assert shifts[1, t, 1] == s and shifts[1, t, 0] == 0, (v, t)
+        np.testing.assert_allclose(taps[0, t], oracle.prf_taps(ph, 0.0), atol=1e-14)
+        np.testing.assert_allclose(taps[1, t], oracle.prf_taps(0.0, ph), atol=1e-14)
+
+
+# ------------------------------------------------------ implementations --
+
+def _random_case(seed, T=3, H=7, W=9, K=3, smax=4, custom=True):
+    g = _rng(seed)
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.15).astype(np.uint8)
+    if custom:
+        shifts = g.integers(-smax, smax + 1, size=(K, T, 2)).astype(np.int32)
+        taps = g.random((K, T, 5, 5))  # not separable, not symmetric
+    else:
+        vx = g.uniform(-0.6, 0.6, K)
+        vy = g.uniform(-0.6, 0.6, K)
+        shifts, taps = None, None
+        return res, sigma, mask, vx, vy
+    return res, sigma, mask, shifts, taps
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_c_oracle_matches_dense_template(oracle, seed):
+    res, sigma, mask, shifts, taps = _random_case(seed)
+    lam = oracle.inverse_variance(sigma, mask)
+    N, D = oracle.search_full(res, lam, shifts, taps)
+    Nd, Dd = oracle.search_dense(res, lam, shifts, taps)
+    np.testing.assert_allclose(N, Nd, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D, Dd, rtol=1e-12, atol=1e-12)
+    Nn, Dn = oracle.search_numpy(res, lam, shifts, taps)
+    np.testing.assert_allclose(N, Nn, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D, Dn, rtol=1e-12, atol=1e-12)
+
+
+def test_gaussian_table_dense_and_points(oracle):
+    res, sigma, mask, vx, vy = _random_case(5, T=6, H=8, W=10, K=4, custom=False)
+    shifts, taps = oracle.trajectory_table(vx, vy, 6)
+    lam = oracle.inverse_variance(sigma, mask)
+    fs = np.linspace(0.5, 2.0, 6)
+    N, D = oracle.search_full(res, lam, shifts, taps, frame_scale=fs)
+    Nd, Dd = oracle.search_dense(res, lam, shifts, taps, frame_scale=fs)
+    np.testing.assert_allclose(N, Nd, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D, Dd, rtol=1e-12, atol=1e-12)
+    g = _rng(9)
+    ys, xs, ks = g.integers(0, 8, 40), g.integers(0, 10, 40), g.integers(0, 4, 40)
+    Np, Dp = oracle.search_points(res, lam, shifts, taps, ys, xs, ks, frame_scale=fs)
+    np.testing.assert_array_equal(Np, N[ks, ys, xs])
+    np.testing.assert_array_equal(Dp, D[ks, ys, xs])
+
+
+def test_frame_scale_equals_scaled_data(oracle):
+    res, sigma, mask, shifts, taps = _random_case(11, T=4)
+    lam = oracle.inverse_variance(sigma, mask)
+    fs = np.array([0.5, 2.0, 4.0, 0.25])  # powers of two: scaling is exact
+    N1, D1 = oracle.search_full(res, lam, shifts, taps, frame_scale=fs)
+    N2, D2 = oracle.search_full(res * fs[:, None, None].astype(np.float32), lam, shifts, taps)
+    np.testing.assert_allclose(N1, N2, rtol=1e-14, atol=1e-14)
+    np.testing.assert_array_equal(D1, D2)
+
+
+# ------------------------------------------------- library special cases --
+
+def test_zero_velocity_is_correlation_of_weighted_sum(oracle):
+    g = _rng(3)
+    T, H, W = 5, 13, 11
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.1).astype(np.uint8)
+    w0 = g.random((5, 5))  # asymmetric: catches a flipped or transposed kernel
+    shifts = np.zeros((1, T, 2), np.int32)
+    taps = np.broadcast_to(w0, (1, T, 5, 5)).copy()
+    lam = oracle.inverse_variance(sigma, mask)
+    N, D = oracle.search_full(res, lam, shifts, taps)
+    ysum = (res.astype(np.float64) * lam[None]).sum(0)
+    wantN = signal.correlate2d(ysum, w0, mode="same", boundary="fill")
+    wantD = T * signal.correlate2d(lam, w0 * w0, mode="same", boundary="fill")
+    np.testing.assert_allclose(N[0], wantN, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D[0], wantD, rtol=1e-12, atol=1e-12)
+
+
+def test_zero_velocity_gaussian_is_prf_convolved_mean_stack(oracle):
+    g = _rng(4)
+    T, H, W = 7, 12, 12
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.ones((H, W), np.float32)
+    shifts, taps = oracle.trajectory_table([0.0], [0.0], T)
+    lam = oracle.inverse_variance(sigma)
+    N, D = oracle.search_full(res, lam, shifts, taps)
+    w0 = oracle.prf_taps(0.0, 0.0)
+    mean = res.astype(np.float64).mean(0)
+    np.testing.assert_allclose(N[0], T * signal.correlate2d(mean, w0, mode="same"),
+                               rtol=1e-12, atol=1e-12)
+    # uniform sigma, no mask: D is T * sum(w0^2) away from the borders
+    assert np.allclose(D[0, 2:-2, 2:-2], T * (w0 ** 2).sum(), rtol=1e-13)
+
+
+def _roll_zero(img, oy, ox):
+    """img shifted so that out[y, x] = img[y + oy, x + ox], zero fill, via np.roll on a padded copy."""
+    H, W = img.shape
+    pad = max(abs(oy), abs(ox)) + 1
+    big = np.pad(img, pad)
+    big = np.roll(big, (-oy, -ox), axis=(0, 1))
+    return big[pad:pad + H, pad:pad + W]
+
+
+def test_single_tap_filter_is_shift_and_add(oracle):
+    """Section 3.2: shift-stacking is the matched filter with one unit tap per frame."""
+    g = _rng(6)
+    T, H, W = 9, 16, 14
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.exp(0.2 * g.standard_normal((H, W))).astype(np.float32)
+    lam = oracle.inverse_variance(sigma)
+    for vx, vy in [(1, 0), (0, -1), (1, 1), (-1, 1)]:
+        shifts = np.zeros((1, T, 2), np.int32)
+        shifts[0, :, 0] = vx * np.arange(T)
+        shifts[0, :, 1] = vy * np.arange(T)
+        taps = np.zeros((1, T, 5, 5))
+        taps[0, :, 2, 2] = 1.0
+        N, D = oracle.search_full(res, lam, shifts, taps)
+        want = np.zeros((H, W))
+        wantD = np.zeros((H, W))
+        for t in range(T):
+            want += _roll_zero(res[t].astype(np.float64) * lam, vy * t, vx * t)
+            wantD += _roll_zero(lam, vy * t, vx * t)
+        np.testing.assert_allclose(N[0], want, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(D[0], wantD, rtol=1e-12, atol=1e-12)
+
+
+def test_integer_velocity_gaussian_is_shifted_correlation(oracle):
+    g = _rng(7)
+    T, H, W = 6, 15, 15
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.ones((H, W), np.float32)
+    lam = oracle.inverse_variance(sigma)
+    shifts, taps = oracle.trajectory_table([1.0, -1.0, 0.0], [0.0, 1.0, -1.0], T)
+    N, D = oracle.search_full(res, lam, shifts, taps)
+    w0 = oracle.prf_taps(0.0, 0.0)
+    for k, (vx, vy) in enumerate([(1, 0), (-1, 1), (0, -1)]):
+        want = np.zeros((H, W))
+        for t in range(T):
+            # correlate on a zero-padded frame so that shifted footprints that
+            # straddle the border keep their in-frame part
+            big = signal.correlate2d(np.pad(res[t].astype(np.float64), 8), w0, mode="same")
+            want += _shift_padded(big, vy * t, vx * t, 8, H, W)
+        np.testing.assert_allclose(N[k], want, rtol=1e-12, atol=1e-12)
+
+
+def _shift_padded(big, oy, ox, pad, H, W):
+    return big[pad + oy:pad + oy + H, pad + ox:pad + ox + W]
+
+
+# ---------------------------------------------------------- closed forms --
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_noiseless_injection_closed_form(oracle, seed):
+    """Section 4.1: injection adds flux times the filter.  With no noise the
+    matched filter at the injected start pixel returns the flux (N/D = f) and
+    SNR = f sqrt(D) = sqrt(sum f^2 w^2 / sigma^2)."""
+    g = _rng(seed)
+    T, H, W = 12, 20, 24
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.05).astype(np.uint8)
+    vx = np.array([0.35, -0.2, 0.05])
+    vy = np.array([-0.15, 0.3, 0.0])
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma, mask)
+    for k in range(3):
+        py, px, f = 9, 11, 2.5
+        res = np.zeros((T, H, W))
+        oracle.inject(res, shifts[k], taps[k], py, px, f)
+        N, D = oracle.search_points(res.astype(np.float32), lam, shifts, taps, [py], [px], [k])
+        # injection values are float64; the float32 copy adds a relative 6e-8 per term
+        assert abs(N[0] / D[0] - f) < 1e-6 * f
+        direct = 0.0
+        for t in range(T):
+            for dy in range(-2, 3):
+                for dx in range(-2, 3):
+                    qy, qx = py + shifts[k, t, 1] + dy, px + shifts[k, t, 0] + dx
+                    direct += (f * taps[k, t, dy + 2, dx + 2]) ** 2 / float(sigma[qy, qx]) ** 2 \
+                        * (1 - mask[qy, qx])
+        snr = N[0] / np.sqrt(D[0])
+        assert abs(snr - np.sqrt(direct)) < 1e-6 * np.sqrt(direct)
+
+
+def test_injection_float64_exact(oracle):
+    """Same closed form with data exactly representable in float32."""
+    T, H, W = 8, 16, 16
+    sigma = np.full((H, W), 2.0, np.float32)
+    lam = oracle.inverse_variance(sigma)
+    shifts = np.zeros((1, T, 2), np.int32)
+    shifts[0, :, 0] = np.arange(T) // 2
+    taps = np.zeros((1, T, 5, 5))
+    taps[0, :, 1:4, 1:4] = [[0.0625, 0.125, 0.0625], [0.125, 0.25, 0.125], [0.0625, 0.125, 0.0625]]
+    res = np.zeros((T, H, W))
+    oracle.inject(res, shifts[0], taps[0], 6, 5, 4.0)
+    N, D = oracle.search_points(res.astype(np.float32), lam, shifts, taps, [6], [5], [0])
+    w2 = (taps[0, 0] ** 2).sum()  # 0.140625
+    assert D[0] == T * w2 / 4.0
+    assert N[0] == 4.0 * D[0]
+
+
+# -------------------------------------------------------------- invariants
+
+def test_linearity_scaling_mask_translation(oracle):
+    g = _rng(12)
+    T, H, W = 5, 18, 18
+    # dyadic values with few bits: 2 r1 - r2 / 2 is exact in float32
+    r1 = (np.round(64 * g.standard_normal((T, H, W))) / 64).astype(np.float32)
+    r2 = (np.round(64 * g.standard_normal((T, H, W))) / 64).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.1).astype(np.uint8)
+    vx = np.array([0.4, -0.3])
+    vy = np.array([0.1, 0.45])
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma, mask)
+    N1, D1 = oracle.search_full(r1, lam, shifts, taps)
+    N2, _ = oracle.search_full(r2, lam, shifts, taps)
+    N12, D12 = oracle.search_full((2 * r1 - 0.5 * r2).astype(np.float32), lam, shifts, taps)
+    np.testing.assert_allclose(N12, 2 * N1 - 0.5 * N2, atol=1e-10)
+    np.testing.assert_array_equal(D12, D1)
+    # sigma -> c sigma: SNR -> SNR / c
+    c = 2.0
+    lam_c = oracle.inverse_variance(sigma * np.float32(c), mask)
+    Nc, Dc = oracle.search_full(r1, lam_c, shifts, taps)
+    s1 = oracle.snr_and_best(N1, D1)[0]
+    sc = oracle.snr_and_best(Nc, Dc)[0]
+    np.testing.assert_allclose(sc, s1 / c, rtol=1e-12, atol=1e-12)
+    # values under the mask do not matter
+    r3 = r1.copy()
+    r3[:, mask.astype(bool)] = 1e6
+    N3, _ = oracle.search_full(r3, lam, shifts, taps)
+    np.testing.assert_allclose(N3, N1, atol=1e-9)
+    # translation: shifting data and noise map shifts the output (interior)
+    oy, ox = 2, 3
+    rs = np.zeros_like(r1)
+    rs[:, oy:, ox:] = r1[:, :H - oy, :W - ox]
+    ls = np.zeros_like(lam)
+    ls[oy:, ox:] = lam[:H - oy, :W - ox]
+    Ns, Ds = oracle.search_full(rs, ls, shifts, taps)
+    m = 6
+    np.testing.assert_allclose(Ns[:, oy + m:H - m, ox + m:W - m], N1[:, m:H - m - oy, m:W - m - ox],
+                               atol=1e-10)
+    np.testing.assert_allclose(Ds[:, oy + m:H - m, ox + m:W - m], D1[:, m:H - m - oy, m:W - m - ox],
+                               rtol=1e-13)
+
+
+# ------------------------------------------------------------ statistics --
+
+def test_pure_noise_snr_is_standard_normal(oracle):
+    """Matched filter with the right noise model: SNR ~ N(0, 1) on pure noise.
+
+    Samples are independent: start pixels 16 px apart (farther than a
+    trajectory's footprint over the stack) and a fresh noise draw each time.
+    """
+    g = _rng(21)
+    T, H, W = 24, 64, 64
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.01).astype(np.uint8)
+    vx = np.array([0.0, 0.3, -0.25, 0.1])
+    vy = np.array([0.0, 0.1, 0.2, -0.3])
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma, mask)
+    grid = np.array([8, 24, 40, 56])
+    ys, xs = [a.ravel() for a in np.meshgrid(grid, grid, indexing="ij")]
+    ys4, xs4 = np.repeat(ys, 4), np.repeat(xs, 4)
+    ks4 = np.tile(np.arange(4), ys.size)
+    draws = 200
+    snr = np.zeros((draws, ys.size, 4))
+    for d in range(draws):
+        res = (sigma[None] * g.standard_normal((T, H, W))).astype(np.float32)
+        N, D = oracle.search_points(res, lam, shifts, taps, ys4, xs4, ks4)
+        snr[d] = (N / np.sqrt(D)).reshape(ys.size, 4)
+    n = draws * ys.size
+    for k in range(4):
+        v = snr[:, :, k].ravel()
+        assert abs(v.mean()) < 4 / np.sqrt(n)
+        assert abs(v.var() - 1.0) < 4 * np.sqrt(2 / n)
+    # the same statistic with a wrong normalisation is far off
+    assert abs((snr / np.sqrt(2.0)).var() - 1.0) > 0.4
+
+
+def test_injected_movers_recovered(oracle):
+    """Section 4.1 protocol on Gaussian noise: movers on a 20 x 80 px grid at
+    grid velocities are found at their start pixel with their trajectory."""
+    g = _rng(31)
+    T, H, W = 40, 48, 176
+    sigma = np.ones((H, W), np.float32)
+    vx = np.array([-0.15, -0.05, 0.05, 0.15] * 4)
+    vy = np.repeat([-0.15, -0.05, 0.05, 0.15], 4)
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma)
+    res = g.standard_normal((T, H, W))
+    truth = []
+    for iy, py in enumerate([14, 34]):
+        for ix, px in enumerate([20, 100]):
+            k = int(g.integers(0, 16))
+            oracle.inject(res, shifts[k], taps[k], py, px, 5.0)  # SNR about 10
+            truth.append((py, px, k))
+    N, D = oracle.search_full(res.astype(np.float32), lam, shifts, taps)
+    snr, valid, smax, amax = oracle.snr_and_best(N, D)
+    for py, px, k in truth:
+        assert smax[py, px] > 8
+        assert amax[py, px] == k
+        win = smax[py - 3:py + 4, px - 3:px + 4]
+        assert win.max() == smax[py, px]
+
+
+# ----------------------------------------------------------- selection ---
+
+def test_best_tie_and_empty_rules(oracle):
+    N = np.array([[[1.0, 0.0]], [[1.0, 0.0]], [[0.5, 0.0]]])  # K=3, H=1, W=2
+    D = np.array([[[1.0, 0.0]], [[1.0, 0.0]], [[1.0, 0.0]]])
+    snr, valid, smax, amax = oracle.snr_and_best(N, D)
+    assert amax[0, 0] == 0 and smax[0, 0] == 1.0  # tie -> smallest k
+    assert amax[0, 1] == -1 and smax[0, 1] == 0.0  # no filter with D > 0
+    N = np.array([[[-3.0]], [[-2.0]]])
+    D = np.array([[[1.0]], [[0.0]]])
+    snr, valid, smax, amax = oracle.snr_and_best(N, D)
+    assert amax[0, 0] == 0 and smax[0, 0] == -3.0  # k with D = 0 is not a candidate
+
+
+def test_topk_order_rule(oracle):
+    smax = np.array([[3.0, 5.0, 3.0], [5.0, 1.0, 0.0]])
+    amax = np.array([[0, 1, 2], [3, 0, -1]])
+    assert list(oracle.topk_order(smax, amax, 4)) == [1, 3, 0, 2]
+    assert list(oracle.topk_order(smax, amax, 10)) == [1, 3, 0, 2, 4]
