@@ -1,0 +1,201 @@
+/*
+ * mf.h -- C ABI of libmf, a GB300 (sm_103a) trajectory matched filter.
+ *
+ * The operation is the matched filter of Ganapathi (2022), "Maximum
+ * Likelihood Systematic Effect Modeling and Matched Filtering to Detect
+ * Trans-Neptunian Objects with TESS", Section 3.2 (Matched Filter), Eq. 5:
+ * one filter per candidate trajectory (the trajectory line convolved with the
+ * pixel response function, PRF), its dot product with the residual stack at
+ * every start pixel, and the maximum over the filter bank.
+ *
+ * Notation used in the comments below.  T frames of H x W pixels; K
+ * trajectories.  r_t(q) is the residual at pixel q of frame t, sigma(q) the
+ * per-pixel noise, m(q) the mask.  lambda(q) = (1 - m(q)) / sigma(q)^2 is the
+ * inverse variance, taken as 0 outside the frame.  For trajectory k and frame
+ * t the library stores a base shift s_{k,t} (integer pixels) and a 5x5
+ * footprint W_{k,t}(a, b), a, b in -2..2.  Then, for start pixel p,
+ *     N_k(p) = sum_t sum_{a,b} W_{k,t}(a,b) lambda(q) r_t(q),
+ *     D_k(p) = sum_t sum_{a,b} W_{k,t}(a,b)^2 lambda(q),
+ *     q = p + s_{k,t} + (a, b),   SNR_k(p) = N_k(p) / sqrt(D_k(p)),
+ * and the flux estimate is N_k(p) / D_k(p).  N is the dot product of Eq. 5
+ * weighted by the Gaussian noise model of Section 3.2; D is its variance.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device memory on the current device, owned by
+ *     the caller.  The library owns only the table handle it creates.
+ *   - Work is enqueued on the given stream and is asynchronous; results are
+ *     valid once the caller synchronises that stream.  NULL stream means the
+ *     legacy default stream.
+ *   - Arguments are validated before anything is enqueued.  On a bad argument
+ *     the call returns MF_EINVAL, enqueues nothing and leaves outputs as they
+ *     were; mf_last_error() then describes the problem.
+ *   - mf_search and mf_rescore_topk allocate nothing: scratch memory is the
+ *     caller's workspace, sized by the matching *_workspace_size call.
+ *   - A device-side wait that runs out of its iteration budget records
+ *     MF_ETIMEOUT in a device status word instead of hanging or trapping;
+ *     mf_device_status() reads it.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream (a cudaStream_t). */
+typedef void *mf_stream;
+
+typedef enum {
+    MF_OK = 0,
+    MF_EINVAL = 1,        /* bad argument; nothing was enqueued */
+    MF_ENOMEM = 2,        /* table creation could not allocate device memory */
+    MF_ECUDA = 3,         /* a CUDA runtime call failed (text in mf_last_error) */
+    MF_ETIMEOUT = 4,      /* a bounded device wait gave up (see mf_device_status) */
+    MF_EUNSUPPORTED = 5   /* valid request this build does not handle */
+} mf_status;
+
+typedef enum {
+    MF_F32 = 0,   /* float32 residuals */
+    MF_BF16 = 1,  /* bfloat16 residuals, r_t = frame_scale[t] * value */
+    MF_F16 = 2    /* float16 residuals, r_t = frame_scale[t] * value */
+} mf_dtype;
+
+/* PRF used to build the filter bank (Section 2: a point source spreads over
+ * neighbouring pixels; the paper's TESS PRF has no closed form, so a Gaussian
+ * of width sigma_px stands in).  The footprint is always 5 x 5 pixels around
+ * the base pixel and is renormalised to unit sum at each sub-pixel phase.
+ *   kind 0: Gaussian integrated over each pixel (erf differences);
+ *   kind 1: Gaussian sampled at pixel centres. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double sigma_px;
+} mf_prf_params;
+
+/* A residual stack in device memory, frame-major: element (t, y, x) lives at
+ * data + t * frame_stride + y * row_stride + x (strides in elements).
+ * frame_scale is a device array of T floats (NULL means all 1); the residual
+ * used by the filter is frame_scale[t] * element.  Scaled bf16/fp16 storage
+ * is not in the paper; it halves the bytes of the stack. */
+typedef struct {
+    const void *data;
+    int32_t dtype;            /* mf_dtype */
+    int32_t reserved;
+    int64_t T, H, W;
+    int64_t frame_stride;     /* >= H * row_stride */
+    int64_t row_stride;       /* >= W */
+    const float *frame_scale; /* device, [T], or NULL */
+} mf_stack;
+
+/* One re-scored candidate (mf_rescore_topk). */
+typedef struct {
+    int32_t y, x;        /* start pixel */
+    int32_t k;           /* trajectory index (as given at table creation) */
+    int32_t reserved;
+    double snr;          /* FP64 N / sqrt(D) recomputed from the FP32 master stack */
+    double flux;         /* FP64 flux estimate N / D (Section 3.2: the score estimates the flux) */
+    float snr_search;    /* the value mf_search reported for this pixel */
+    float reserved2;
+} mf_candidate;
+
+/* Filter bank handle: per (k, t) base shift and 5x5 footprint, kept on the
+ * host in FP64 and on the device in the layouts the kernels read. */
+typedef struct mf_prf_table mf_prf_table;
+
+/* Build the filter bank for K linear trajectories over T frames (Section 2:
+ * trajectories are straight lines in pixel space; Section 3.2: a filter is
+ * the trajectory line convolved with the PRF).  vx[k], vy[k] are host arrays
+ * of velocities in pixels per frame (x = column, y = row).  For frame t the
+ * position is c = v * t (FP64); base shift s = floor(c + 1/2) per axis; phase
+ * c - s; footprint = the PRF at that phase.  Allocates device memory for the
+ * table (the only allocation the library makes) on the current device.
+ * Errors: MF_EINVAL (K < 1, T < 1, NULL pointers, non-finite velocity,
+ * sigma_px <= 0, unknown kind, |v| * T beyond 2^20 pixels), MF_ENOMEM. */
+mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy,
+                              int32_t K, int32_t T, mf_prf_table **out);
+
+/* Build a filter bank from explicit per-(k, t) shifts and footprints (host
+ * arrays): shifts[(k*T + t)*2 + 0] = s_x, [.. + 1] = s_y;
+ * taps[(k*T + t)*25 + (b + 2)*5 + (a + 2)] = W_{k,t}(a, b), a = column offset,
+ * b = row offset.  Any footprint is accepted (not necessarily separable or
+ * normalised), e.g. the single unit tap that turns the search into
+ * shift-and-add (Section 3.2, the shift-stack comparison).
+ * Errors as mf_prf_table_create, plus non-finite taps. */
+mf_status mf_prf_table_create_custom(const int32_t *shifts, const double *taps,
+                                     int32_t K, int32_t T, mf_prf_table **out);
+
+/* Free the table's host and device memory.  NULL is a no-op.  The caller must
+ * make sure no enqueued work still uses it. */
+void mf_prf_table_destroy(mf_prf_table *table);
+
+/* K and T of a table. */
+mf_status mf_prf_table_dims(const mf_prf_table *table, int32_t *K, int32_t *T);
+
+/* Copy the FP64 filter bank back to host arrays laid out as in
+ * mf_prf_table_create_custom (either pointer may be NULL). */
+mf_status mf_prf_table_export(const mf_prf_table *table, int32_t *shifts, double *taps);
+
+/* Bytes of workspace mf_search needs for this stack shape and table. */
+mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *table,
+                                   size_t *bytes);
+
+/* The matched-filter search (Section 3.2, Eq. 5 and the maximum over the
+ * filter bank).  Inputs, all device memory:
+ *   stack      residuals r (see mf_stack); T must equal the table's T;
+ *   sigma      float[H*W] row-major per-pixel noise;
+ *   mask       uint8[H*W] row-major, nonzero = pixel excluded (the paper
+ *              clips bright pixels), or NULL for none.  Unmasked pixels need
+ *              a finite sigma > 0; others are treated as masked;
+ *   table      filter bank (K trajectories);
+ * Outputs, device memory:
+ *   snr_max    float[H*W]: max_k SNR_k(p) over filters with D_k(p) > 0;
+ *   argmax     int32[H*W]: the smallest k attaining it; a pixel where no
+ *              filter has D > 0 gets snr_max 0 and argmax -1;
+ *   snr_all    float[K*H*W] (k-major) with every SNR_k(p), 0 where D = 0,
+ *              or NULL to skip it.
+ * workspace: device memory of at least mf_search_workspace_size bytes,
+ * 256-byte aligned; its contents on entry do not matter.
+ * Arithmetic: numerator in FP32 with blocked accumulation over frames;
+ * denominator from FP32 products accumulated in FP64.
+ * Errors: MF_EINVAL on shape/stride/pointer problems (nothing enqueued),
+ * MF_ECUDA if a launch fails. */
+mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *mask,
+                    const mf_prf_table *table, float *snr_max, int32_t *argmax,
+                    float *snr_all, void *workspace, size_t workspace_bytes,
+                    mf_stream stream);
+
+/* Bytes of workspace mf_rescore_topk needs. */
+mf_status mf_rescore_workspace_size(int64_t H, int64_t W, int32_t k_top, size_t *bytes);
+
+/* Candidate list (Section 3.3: scores above a threshold are candidates) with
+ * an FP64 re-score.  Picks the k_top pixels with the largest snr_max (ties:
+ * smaller flat index y*W + x first; pixels with argmax -1 never qualify),
+ * then recomputes N and D for (pixel, argmax) in FP64 from `master`, which
+ * should be the FP32 residuals (bf16/fp16 are accepted and read as stored).
+ * out: device mf_candidate[k_top], sorted by snr_search descending then flat
+ * index; n_out: device int32, the number written (<= k_top).
+ * Errors: MF_EINVAL (k_top < 1 or > H*W, shape mismatch, NULL pointers). */
+mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint8_t *mask,
+                          const mf_prf_table *table, const float *snr_max,
+                          const int32_t *argmax, int32_t k_top, mf_candidate *out,
+                          int32_t *n_out, void *workspace, size_t workspace_bytes,
+                          mf_stream stream);
+
+/* Text of the last error on this host thread ("" if none). */
+const char *mf_last_error(void);
+
+/* Read and clear the device status word of the current device (synchronises
+ * the device).  MF_OK, or MF_ETIMEOUT if a kernel's bounded wait gave up. */
+mf_status mf_device_status(void);
+
+/* Library version string. */
+const char *mf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H */

@@ -1,0 +1,11 @@
+"""GB300-native trajectory matched filter (Ganapathi 2022, Section 3.2).
+
+The compute path is the CUDA library ``libmf.so`` (sources in ``csrc/``, ABI
+in ``include/mf.h``); ``binding`` is a thin ctypes layer with the same names.
+Nothing here falls back to a CPU implementation: if the library is missing
+the binding raises.
+"""
+from .binding import (  # noqa: F401
+    MFError, PrfTable, prf_table_create, prf_table_create_custom, search, search_workspace_size,
+    rescore_topk, rescore_workspace_size, device_status, last_error, version, load, library_path,
+)

@@ -1,0 +1,260 @@
+"""ctypes binding for libmf (include/mf.h).  Argument marshalling only: every
+step of the search runs in the CUDA library.  PyTorch supplies device memory
+and streams.  Function names follow the C entry points without the ``mf_``
+prefix."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libmf.so")
+_lib = None
+_lock = threading.Lock()
+
+MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ETIMEOUT, MF_EUNSUPPORTED = range(6)
+MF_F32, MF_BF16, MF_F16 = 0, 1, 2
+_DTYPES = {torch.float32: MF_F32, torch.bfloat16: MF_BF16, torch.float16: MF_F16}
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libmf status %d: %s" % (status, msg))
+        self.status = status
+
+
+class PrfParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sigma_px", ctypes.c_double)]
+
+
+class Stack(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("T", ctypes.c_int64), ("H", ctypes.c_int64), ("W", ctypes.c_int64),
+                ("frame_stride", ctypes.c_int64), ("row_stride", ctypes.c_int64),
+                ("frame_scale", ctypes.c_void_p)]
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_int32), ("x", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("snr", ctypes.c_double), ("flux", ctypes.c_double),
+                ("snr_search", ctypes.c_float), ("reserved2", ctypes.c_float)]
+
+
+CANDIDATE_BYTES = ctypes.sizeof(Candidate)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libmf.so; raises if it has not been built (no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libmf.so not built; run __graft_entry__.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "mf_prf_table_create": ([ctypes.POINTER(PrfParams), P, P, I32, I32, pp], ctypes.c_int),
+            "mf_prf_table_create_custom": ([P, P, I32, I32, pp], ctypes.c_int),
+            "mf_prf_table_destroy": ([P], None),
+            "mf_prf_table_dims": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
+            "mf_prf_table_export": ([P, P, P], ctypes.c_int),
+            "mf_search_workspace_size": ([ctypes.POINTER(Stack), P, ctypes.POINTER(SZ)], ctypes.c_int),
+            "mf_search": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P, SZ, P], ctypes.c_int),
+            "mf_rescore_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
+            "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
+            "mf_last_error": ([], ctypes.c_char_p),
+            "mf_device_status": ([], ctypes.c_int),
+            "mf_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().mf_last_error().decode()
+
+
+def version() -> str:
+    return load().mf_version().decode()
+
+
+def _check(status):
+    if status != MF_OK:
+        raise MFError(status, last_error())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class PrfTable:
+    """Filter bank handle (mf_prf_table)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        K, T = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().mf_prf_table_dims(self._h, ctypes.byref(K), ctypes.byref(T)))
+        self.K, self.T = K.value, T.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        import numpy as np
+        shifts = np.zeros((self.K, self.T, 2), np.int32)
+        taps = np.zeros((self.K, self.T, 5, 5), np.float64)
+        _check(load().mf_prf_table_export(self._h, shifts.ctypes.data_as(ctypes.c_void_p),
+                                          taps.ctypes.data_as(ctypes.c_void_p)))
+        return shifts, taps
+
+    def destroy(self):
+        if self._h:
+            load().mf_prf_table_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0) -> PrfTable:
+    import numpy as np
+    vx = np.ascontiguousarray(vx, np.float64)
+    vy = np.ascontiguousarray(vy, np.float64)
+    if vx.shape != vy.shape or vx.ndim != 1:
+        raise ValueError("vx and vy must be 1-D of equal length")
+    prm = PrfParams(int(kind), 0, float(sigma_px))
+    h = ctypes.c_void_p()
+    _check(load().mf_prf_table_create(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                                      vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+                                      ctypes.byref(h)))
+    return PrfTable(h)
+
+
+def prf_table_create_custom(shifts, taps) -> PrfTable:
+    """shifts int32 [K, T, 2] as (s_x, s_y); taps float64 [K, T, 5, 5] as [.., dy+2, dx+2]."""
+    import numpy as np
+    shifts = np.ascontiguousarray(shifts, np.int32)
+    taps = np.ascontiguousarray(taps, np.float64)
+    K, T = shifts.shape[:2]
+    if shifts.shape != (K, T, 2) or taps.shape != (K, T, 5, 5):
+        raise ValueError("shifts must be [K, T, 2] and taps [K, T, 5, 5]")
+    h = ctypes.c_void_p()
+    _check(load().mf_prf_table_create_custom(shifts.ctypes.data_as(ctypes.c_void_p),
+                                             taps.ctypes.data_as(ctypes.c_void_p), K, T, ctypes.byref(h)))
+    return PrfTable(h)
+
+
+def make_stack(data: torch.Tensor, frame_scale: torch.Tensor | None = None) -> Stack:
+    if data.dim() != 3:
+        raise ValueError("stack must be [T, H, W]")
+    if data.dtype not in _DTYPES:
+        raise ValueError("stack dtype must be float32, bfloat16 or float16")
+    if data.stride(2) != 1:
+        raise ValueError("stack rows must be contiguous")
+    T, H, W = data.shape
+    if frame_scale is not None:
+        if frame_scale.dtype != torch.float32 or frame_scale.numel() != T or not frame_scale.is_contiguous():
+            raise ValueError("frame_scale must be a contiguous float32 tensor of length T")
+    return Stack(data.data_ptr(), _DTYPES[data.dtype], 0, T, H, W, data.stride(0), data.stride(1),
+                 None if frame_scale is None else frame_scale.data_ptr())
+
+
+def search_workspace_size(shape, table: PrfTable) -> int:
+    T, H, W = shape
+    st = Stack(None, MF_F32, 0, T, H, W, H * W, W, None)
+    n = ctypes.c_size_t()
+    _check(load().mf_search_workspace_size(ctypes.byref(st), table.handle, ctypes.byref(n)))
+    return n.value
+
+
+def _workspace(nbytes, device, workspace):
+    if workspace is not None:
+        return workspace  # size and alignment are checked by the library
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def search(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torch.Tensor | None = None,
+           frame_scale: torch.Tensor | None = None, want_all: bool = False, workspace=None, out=None,
+           stream=None):
+    """mf_search: returns (snr_max [H, W] f32, argmax [H, W] i32, snr_all [K, H, W] f32 or None)."""
+    st = make_stack(stack, frame_scale)
+    T, H, W = stack.shape
+    dev = stack.device
+    for name, t in (("sigma", sigma), ("mask", mask)):
+        if t is not None and (t.device != dev or not t.is_contiguous() or t.shape != (H, W)):
+            raise ValueError("%s must be a contiguous [H, W] tensor on the stack's device" % name)
+    if sigma.dtype != torch.float32:
+        raise ValueError("sigma must be float32")
+    if mask is not None and mask.dtype != torch.uint8:
+        raise ValueError("mask must be uint8")
+    if out is None:
+        snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
+        argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
+        snr_all = torch.empty((table.K, H, W), dtype=torch.float32, device=dev) if want_all else None
+    else:
+        snr_max, argmax, snr_all = out
+    nbytes = search_workspace_size((T, H, W), table)
+    ws = _workspace(nbytes, dev, workspace)
+    _check(load().mf_search(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
+                            _ptr(argmax), _ptr(snr_all), _ptr(ws), ws.numel() * ws.element_size(),
+                            _stream_ptr(stream)))
+    return snr_max, argmax, snr_all
+
+
+def rescore_workspace_size(H, W, k_top) -> int:
+    n = ctypes.c_size_t()
+    _check(load().mf_rescore_workspace_size(int(H), int(W), int(k_top), ctypes.byref(n)))
+    return n.value
+
+
+def rescore_topk(master: torch.Tensor, sigma: torch.Tensor, table: PrfTable, snr_max: torch.Tensor,
+                 argmax: torch.Tensor, k_top: int, mask: torch.Tensor | None = None,
+                 frame_scale: torch.Tensor | None = None, workspace=None, stream=None):
+    """mf_rescore_topk: returns (candidates as a uint8 tensor of k_top records, n_out int32 [1])."""
+    st = make_stack(master, frame_scale)
+    T, H, W = master.shape
+    dev = master.device
+    out = torch.zeros((k_top, CANDIDATE_BYTES), dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int32, device=dev)
+    nbytes = rescore_workspace_size(H, W, k_top)
+    ws = _workspace(nbytes, dev, workspace)
+    _check(load().mf_rescore_topk(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
+                                  _ptr(argmax), int(k_top), _ptr(out), _ptr(n_out), _ptr(ws),
+                                  ws.numel() * ws.element_size(), _stream_ptr(stream)))
+    return out, n_out
+
+
+def decode_candidates(raw: torch.Tensor, n: int):
+    """Candidate records (uint8 tensor from rescore_topk) -> list of dicts."""
+    import numpy as np
+    buf = raw[:n].cpu().numpy().tobytes()
+    dt = np.dtype([("y", "<i4"), ("x", "<i4"), ("k", "<i4"), ("r", "<i4"), ("snr", "<f8"),
+                   ("flux", "<f8"), ("snr_search", "<f4"), ("r2", "<f4")])
+    return np.frombuffer(buf, dtype=dt, count=n)
+
+
+def device_status() -> int:
+    return load().mf_device_status()

@@ -1,0 +1,529 @@
+// Host side of libmf: filter-bank construction, trajectory grouping, argument
+// validation and the C entry points declared in include/mf.h.
+//
+// The filter bank follows Section 3.2 of Ganapathi (2022): one filter per
+// trajectory, the trajectory line convolved with the PRF.  It is stored in
+// sparse form, a base shift and a 5x5 footprint per (trajectory, frame).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+
+#include "mf_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+mf_status fail(mf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+mf_status ok() {
+    g_err.clear();
+    return MF_OK;
+}
+
+int64_t floor_div(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Pixel-integrated 1-D Gaussian (PRF kind 0) over pixel [a - 1/2, a + 1/2].
+double pixel_gauss(int a, double phase, double sigma) {
+    const double s = sigma * std::sqrt(2.0);
+    return 0.5 * (std::erf((a + 0.5 - phase) / s) - std::erf((a - 0.5 - phase) / s));
+}
+
+// 5x5 footprint of the PRF for a source at sub-pixel offset (phx, phy) from
+// the base pixel, renormalised to unit sum (Section 2: the PRF shares a point
+// source's flux between neighbouring pixels).
+void footprint(int kind, double sigma, double phx, double phy, double *w) {
+    double gx[5], gy[5];
+    double total = 0.0;
+    for (int i = 0; i < 5; i++) {
+        const int d = i - 2;
+        if (kind == 0) {
+            gx[i] = pixel_gauss(d, phx, sigma);
+            gy[i] = pixel_gauss(d, phy, sigma);
+        } else {
+            gx[i] = std::exp(-(d - phx) * (d - phx) / (2.0 * sigma * sigma));
+            gy[i] = std::exp(-(d - phy) * (d - phy) / (2.0 * sigma * sigma));
+        }
+    }
+    for (int b = 0; b < 5; b++)
+        for (int a = 0; a < 5; a++) {
+            w[b * 5 + a] = gy[b] * gx[a];
+            total += w[b * 5 + a];
+        }
+    for (int i = 0; i < 25; i++) w[i] /= total;
+}
+
+// Balanced k-d split of the velocity set into `groups` parts of at most
+// kWarpsPerCta members, so that trajectories sharing a CTA (and its frame
+// window) have similar shifts at every frame.
+void kd_split(std::vector<int> &idx, int lo, int hi, int groups, const std::vector<double> &ex,
+              const std::vector<double> &ey, std::vector<std::vector<int>> &out) {
+    const int n = hi - lo;
+    if (groups <= 1 || n <= 1) {
+        out.emplace_back(idx.begin() + lo, idx.begin() + hi);
+        for (int g = 1; g < groups; g++) out.emplace_back();
+        return;
+    }
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int i = lo; i < hi; i++) {
+        x0 = std::min(x0, ex[idx[i]]);
+        x1 = std::max(x1, ex[idx[i]]);
+        y0 = std::min(y0, ey[idx[i]]);
+        y1 = std::max(y1, ey[idx[i]]);
+    }
+    // x spread is cheaper than y spread (window rows are padded to 32-word
+    // pitch anyway), so split y first when they are comparable.
+    const bool by_x = (x1 - x0) > 1.5 * (y1 - y0);
+    auto key = [&](int a, int b) {
+        const double pa = by_x ? ex[a] : ey[a], pb = by_x ? ex[b] : ey[b];
+        if (pa != pb) return pa < pb;
+        const double qa = by_x ? ey[a] : ex[a], qb = by_x ? ey[b] : ex[b];
+        if (qa != qb) return qa < qb;
+        return a < b;
+    };
+    std::sort(idx.begin() + lo, idx.begin() + hi, key);
+    const int g1 = groups / 2, g2 = groups - g1;
+    int n1 = (int)std::llround((double)n * g1 / groups);
+    n1 = std::max(n1, n - g2 * mf::kWarpsPerCta);
+    n1 = std::min(n1, g1 * mf::kWarpsPerCta);
+    n1 = std::max(0, std::min(n, n1));
+    kd_split(idx, lo, lo + n1, g1, ex, ey, out);
+    kd_split(idx, lo + n1, hi, g2, ex, ey, out);
+}
+
+size_t smem_bytes(const mf::Plan &p) {
+    return (size_t)mf::kStages * p.BH * p.S * sizeof(float) +
+           (size_t)mf::kStages * sizeof(mf::FrameBlock) + 8192 + 256 + 1024;
+}
+
+// Window geometry of a grouping: fills S, BH; false if it does not fit.
+bool measure(mf::Plan &p, const mf_prf_table &t) {
+    int max_offx = 0, max_rows = 0;
+    for (int g = 0; g < p.G; g++) {
+        for (int f = 0; f < t.T; f++) {
+            int64_t mnx = INT64_MAX, mxx = INT64_MIN, mny = INT64_MAX, mxy = INT64_MIN;
+            bool any = false;
+            for (int w = 0; w < mf::kWarpsPerCta; w++) {
+                const int k = p.members[g * mf::kWarpsPerCta + w];
+                if (k < 0) continue;
+                any = true;
+                const int64_t sx = t.shifts[((size_t)k * t.T + f) * 2 + 0];
+                const int64_t sy = t.shifts[((size_t)k * t.T + f) * 2 + 1];
+                mnx = std::min(mnx, sx);
+                mxx = std::max(mxx, sx);
+                mny = std::min(mny, sy);
+                mxy = std::max(mxy, sy);
+            }
+            if (!any) continue;
+            const int64_t rox = 4 * floor_div(mnx - 2, 4);
+            max_offx = (int)std::max<int64_t>(max_offx, mxx - 2 - rox);
+            max_rows = (int)std::max<int64_t>(max_rows, (mxy - mny) + 36);
+        }
+    }
+    p.S = (int)round_up(max_offx + 43, 32);
+    p.BH = (int)round_up(max_rows, mf::kLoadRows);
+    return p.S <= 256 && p.BH <= 256 && smem_bytes(p) <= (size_t)mf::kSmemBudget;
+}
+
+mf_status plan_groups(mf_prf_table &t) {
+    const int K = t.K;
+    std::vector<double> ex(K), ey(K);
+    for (int k = 0; k < K; k++) {
+        // displacement over the stack, in pixels: what sets the window spread
+        const size_t last = ((size_t)k * t.T + (t.T - 1)) * 2;
+        const size_t first = (size_t)k * t.T * 2;
+        ex[k] = (double)t.shifts[last + 0] - t.shifts[first + 0];
+        ey[k] = (double)t.shifts[last + 1] - t.shifts[first + 1];
+        // trajectories with equal endpoints but different start shifts (custom
+        // tables) still differ at frame 0: fold that in
+        ex[k] += 1e-3 * t.shifts[first + 0];
+        ey[k] += 1e-3 * t.shifts[first + 1];
+    }
+    int G = (K + mf::kWarpsPerCta - 1) / mf::kWarpsPerCta;
+    for (;;) {
+        std::vector<int> idx(K);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::vector<std::vector<int>> parts;
+        kd_split(idx, 0, K, G, ex, ey, parts);
+        mf::Plan p;
+        p.G = 0;
+        for (auto &part : parts)
+            if (!part.empty()) p.G++;
+        p.members.assign((size_t)p.G * mf::kWarpsPerCta, -1);
+        int g = 0;
+        for (auto &part : parts) {
+            if (part.empty()) continue;
+            std::sort(part.begin(), part.end());
+            for (size_t i = 0; i < part.size(); i++) p.members[(size_t)g * mf::kWarpsPerCta + i] = part[i];
+            g++;
+        }
+        if (measure(p, t)) {
+            int mx = 0;
+            for (size_t i = 0; i < t.shifts.size(); i++) mx = std::max(mx, std::abs(t.shifts[i]));
+            p.max_abs_shift = mx;
+            t.plan = std::move(p);
+            return MF_OK;
+        }
+        if (G >= K) break;
+        G = std::min(K, std::max(G + 1, G * 5 / 4));
+    }
+    return fail(MF_EUNSUPPORTED, "trajectory shifts too far apart for the frame window");
+}
+
+template <class T>
+mf_status upload(T **dst, const T *src, size_t n) {
+    if (n == 0) {
+        *dst = nullptr;
+        return MF_OK;
+    }
+    cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+    if (e != cudaSuccess) return fail(MF_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    return MF_OK;
+}
+
+// Build the device layouts from shifts/taps: plan, frame blocks, headers,
+// denominator segments, FP64 copies.
+mf_status finish_table(mf_prf_table *t) {
+    mf_status s = plan_groups(*t);
+    if (s != MF_OK) return s;
+    const int K = t->K, T = t->T;
+    const mf::Plan &p = t->plan;
+    std::vector<mf::FrameHdr> hdr((size_t)p.G * T);
+    for (int g = 0; g < p.G; g++) {
+        for (int f = 0; f < T; f++) {
+            int64_t mnx = INT64_MAX, mny = INT64_MAX, mxy = INT64_MIN;
+            for (int w = 0; w < mf::kWarpsPerCta; w++) {
+                const int k = p.members[(size_t)g * mf::kWarpsPerCta + w];
+                if (k < 0) continue;
+                mnx = std::min<int64_t>(mnx, t->shifts[((size_t)k * T + f) * 2 + 0]);
+                mny = std::min<int64_t>(mny, t->shifts[((size_t)k * T + f) * 2 + 1]);
+                mxy = std::max<int64_t>(mxy, t->shifts[((size_t)k * T + f) * 2 + 1]);
+            }
+            mf::FrameHdr &h = hdr[(size_t)g * T + f];
+            h.roy = (int32_t)(mny - 2);
+            h.rox = (int32_t)(4 * floor_div(mnx - 2, 4));
+            h.nrows = (int32_t)round_up(mxy - mny + 36, mf::kLoadRows);
+            h.pad = 0;
+        }
+    }
+    std::vector<mf::FrameBlock> blocks((size_t)p.G * T);
+    for (int g = 0; g < p.G; g++) {
+        for (int f = 0; f < T; f++) {
+            mf::FrameBlock &b = blocks[(size_t)g * T + f];
+            std::memset(&b, 0, sizeof b);
+            if (f + mf::kStages < T) b.next = hdr[(size_t)g * T + f + mf::kStages];
+            const mf::FrameHdr &h = hdr[(size_t)g * T + f];
+            for (int w = 0; w < mf::kWarpsPerCta; w++) {
+                const int k = p.members[(size_t)g * mf::kWarpsPerCta + w];
+                mf::SlotRec &r = b.slot[w];
+                r.k = k;
+                if (k < 0) continue;
+                const size_t kt = (size_t)k * T + f;
+                for (int i = 0; i < 25; i++) r.taps[i] = (float)t->taps[kt * 25 + i];
+                r.offy = t->shifts[kt * 2 + 1] - 2 - h.roy;
+                r.offx = t->shifts[kt * 2 + 0] - 2 - h.rox;
+            }
+        }
+    }
+    // Denominator: collapse runs of frames with the same base shift; the
+    // footprint energies of a run add up because lambda does not depend on t.
+    std::vector<mf::SegRec> segs;
+    std::vector<int32_t> seg_off(K + 1, 0);
+    for (int k = 0; k < K; k++) {
+        seg_off[k] = (int32_t)segs.size();
+        int f = 0;
+        while (f < T) {
+            const int32_t sx = t->shifts[((size_t)k * T + f) * 2 + 0];
+            const int32_t sy = t->shifts[((size_t)k * T + f) * 2 + 1];
+            double acc[25] = {0};
+            int e = f;
+            while (e < T && t->shifts[((size_t)k * T + e) * 2 + 0] == sx &&
+                   t->shifts[((size_t)k * T + e) * 2 + 1] == sy) {
+                for (int i = 0; i < 25; i++) {
+                    const double w = t->taps[((size_t)k * T + e) * 25 + i];
+                    acc[i] += w * w;
+                }
+                e++;
+            }
+            mf::SegRec r;
+            std::memset(&r, 0, sizeof r);
+            for (int i = 0; i < 25; i++) r.w2[i] = (float)acc[i];
+            r.sx = sx;
+            r.sy = sy;
+            segs.push_back(r);
+            f = e;
+        }
+    }
+    seg_off[K] = (int32_t)segs.size();
+    t->n_seg = (int)segs.size();
+    if ((s = upload(&t->d_blocks, blocks.data(), blocks.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_hdr, hdr.data(), hdr.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_segs, segs.data(), segs.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_seg_off, seg_off.data(), seg_off.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_taps64, t->taps.data(), t->taps.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_shifts, t->shifts.data(), t->shifts.size())) != MF_OK) return s;
+    return MF_OK;
+}
+
+void free_device(mf_prf_table *t) {
+    cudaFree(t->d_blocks);
+    cudaFree(t->d_hdr);
+    cudaFree(t->d_segs);
+    cudaFree(t->d_seg_off);
+    cudaFree(t->d_taps64);
+    cudaFree(t->d_shifts);
+    t->d_blocks = nullptr;
+    t->d_hdr = nullptr;
+    t->d_segs = nullptr;
+    t->d_seg_off = nullptr;
+    t->d_taps64 = nullptr;
+    t->d_shifts = nullptr;
+}
+
+mf_status create_common(mf_prf_table *t, mf_prf_table **out) {
+    if (cudaGetDevice(&t->device) != cudaSuccess) {
+        delete t;
+        return fail(MF_ECUDA, "no current CUDA device");
+    }
+    mf_status s = finish_table(t);
+    if (s != MF_OK) {
+        const std::string msg = g_err;
+        free_device(t);
+        delete t;
+        g_err = msg;
+        return s;
+    }
+    *out = t;
+    return ok();
+}
+
+size_t elem_size(int dtype) { return dtype == MF_F32 ? 4 : 2; }
+
+mf_status check_stack(const mf_stack *st) {
+    if (!st) return fail(MF_EINVAL, "stack is NULL");
+    if (st->dtype != MF_F32 && st->dtype != MF_BF16 && st->dtype != MF_F16)
+        return fail(MF_EINVAL, "unknown dtype %d", st->dtype);
+    if (st->T < 1 || st->H < 0 || st->W < 0) return fail(MF_EINVAL, "bad stack shape T=%lld H=%lld W=%lld",
+                                                         (long long)st->T, (long long)st->H, (long long)st->W);
+    if (st->H > (1 << 20) || st->W > (1 << 20) || st->T > (1 << 20))
+        return fail(MF_EINVAL, "stack dimension above 2^20");
+    if (st->H * st->W == 0) return MF_OK;
+    if (!st->data) return fail(MF_EINVAL, "stack data is NULL");
+    if (st->row_stride < st->W) return fail(MF_EINVAL, "row_stride %lld < W %lld", (long long)st->row_stride,
+                                            (long long)st->W);
+    if (st->T > 1 && st->frame_stride < st->H * st->row_stride)
+        return fail(MF_EINVAL, "frame_stride %lld < H * row_stride", (long long)st->frame_stride);
+    if ((uintptr_t)st->data % elem_size(st->dtype) != 0) return fail(MF_EINVAL, "stack data misaligned");
+    return MF_OK;
+}
+
+}  // namespace
+
+namespace mf {
+
+WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab) {
+    WorkspaceLayout L;
+    L.pad = (int64_t)tab->plan.max_abs_shift + 2 + kTile + 8;
+    L.lam_w = round_up(W + 2 * L.pad, 4);
+    L.lam_h = H + 2 * L.pad;
+    L.y_pitch = round_up(W, 4);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return o;
+    };
+    L.lam_off = take((size_t)L.lam_w * L.lam_h * sizeof(float));
+    L.y_off = take((size_t)T * H * L.y_pitch * sizeof(float));
+    L.isd_off = take((size_t)tab->K * H * W * sizeof(float));
+    L.keys_off = take((size_t)H * W * sizeof(unsigned long long));
+    L.total = off;
+    return L;
+}
+
+}  // namespace mf
+
+extern "C" {
+
+mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                              int32_t T, mf_prf_table **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!prf || !vx || !vy) return fail(MF_EINVAL, "NULL argument");
+    if (K < 1 || T < 1) return fail(MF_EINVAL, "K=%d and T=%d must be >= 1", K, T);
+    if (T > (1 << 20) || K > (1 << 22)) return fail(MF_EINVAL, "K or T too large");
+    if (prf->kind != 0 && prf->kind != 1) return fail(MF_EINVAL, "unknown PRF kind %d", prf->kind);
+    if (!(prf->sigma_px > 0.0) || !std::isfinite(prf->sigma_px))
+        return fail(MF_EINVAL, "sigma_px must be finite and > 0");
+    for (int k = 0; k < K; k++) {
+        if (!std::isfinite(vx[k]) || !std::isfinite(vy[k])) return fail(MF_EINVAL, "velocity %d not finite", k);
+        if (std::fabs(vx[k]) * T > (1 << 20) || std::fabs(vy[k]) * T > (1 << 20))
+            return fail(MF_EINVAL, "velocity %d moves more than 2^20 pixels", k);
+    }
+    auto *t = new mf_prf_table;
+    t->K = K;
+    t->T = T;
+    t->shifts.resize((size_t)K * T * 2);
+    t->taps.resize((size_t)K * T * 25);
+    for (int k = 0; k < K; k++) {
+        for (int f = 0; f < T; f++) {
+            // position after f frames, base pixel floor(c + 1/2), phase c - s
+            const double cx = vx[k] * (double)f;
+            const double cy = vy[k] * (double)f;
+            const double sx = std::floor(cx + 0.5);
+            const double sy = std::floor(cy + 0.5);
+            const size_t kt = (size_t)k * T + f;
+            t->shifts[kt * 2 + 0] = (int32_t)sx;
+            t->shifts[kt * 2 + 1] = (int32_t)sy;
+            footprint(prf->kind, prf->sigma_px, cx - sx, cy - sy, &t->taps[kt * 25]);
+        }
+    }
+    return create_common(t, out);
+}
+
+mf_status mf_prf_table_create_custom(const int32_t *shifts, const double *taps, int32_t K, int32_t T,
+                                     mf_prf_table **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!shifts || !taps) return fail(MF_EINVAL, "NULL argument");
+    if (K < 1 || T < 1) return fail(MF_EINVAL, "K=%d and T=%d must be >= 1", K, T);
+    if (T > (1 << 20) || K > (1 << 22)) return fail(MF_EINVAL, "K or T too large");
+    const size_t n = (size_t)K * T;
+    for (size_t i = 0; i < n * 2; i++)
+        if (std::abs((int64_t)shifts[i]) > (1 << 20)) return fail(MF_EINVAL, "shift beyond 2^20 pixels");
+    for (size_t i = 0; i < n * 25; i++)
+        if (!std::isfinite(taps[i])) return fail(MF_EINVAL, "tap %zu not finite", i);
+    auto *t = new mf_prf_table;
+    t->K = K;
+    t->T = T;
+    t->shifts.assign(shifts, shifts + n * 2);
+    t->taps.assign(taps, taps + n * 25);
+    return create_common(t, out);
+}
+
+void mf_prf_table_destroy(mf_prf_table *table) {
+    if (!table) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != table->device) cudaSetDevice(table->device);
+    free_device(table);
+    if (cur != table->device) cudaSetDevice(cur);
+    delete table;
+}
+
+mf_status mf_prf_table_dims(const mf_prf_table *table, int32_t *K, int32_t *T) {
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (K) *K = table->K;
+    if (T) *T = table->T;
+    return ok();
+}
+
+mf_status mf_prf_table_export(const mf_prf_table *table, int32_t *shifts, double *taps) {
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (shifts) std::memcpy(shifts, table->shifts.data(), table->shifts.size() * sizeof(int32_t));
+    if (taps) std::memcpy(taps, table->taps.data(), table->taps.size() * sizeof(double));
+    return ok();
+}
+
+mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *table, size_t *bytes) {
+    if (!bytes) return fail(MF_EINVAL, "bytes is NULL");
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (!stack) return fail(MF_EINVAL, "stack is NULL");
+    if (stack->T < 1 || stack->H < 0 || stack->W < 0) return fail(MF_EINVAL, "bad stack shape");
+    *bytes = mf::search_layout(stack->T, stack->H, stack->W, table).total;
+    return ok();
+}
+
+mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *mask, const mf_prf_table *table,
+                    float *snr_max, int32_t *argmax, float *snr_all, void *workspace, size_t workspace_bytes,
+                    mf_stream stream) {
+    mf_status s = check_stack(stack);
+    if (s != MF_OK) return s;
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (stack->T != table->T) return fail(MF_EINVAL, "stack has T=%lld, table has T=%d", (long long)stack->T,
+                                          table->T);
+    if (stack->H * stack->W == 0) return ok();  // nothing to search
+    if (!sigma || !snr_max || !argmax) return fail(MF_EINVAL, "sigma, snr_max and argmax are required");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != table->device)
+        return fail(MF_EINVAL, "table lives on device %d, current device is %d", table->device, dev);
+    const mf::WorkspaceLayout L = mf::search_layout(stack->T, stack->H, stack->W, table);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", L.total, workspace_bytes);
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    mf::SearchArgs a{stack, sigma, mask, table, snr_max, argmax, snr_all, (char *)workspace, L, stream};
+    char err[256] = {0};
+    const int rc = mf::launch_search(a, err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
+mf_status mf_rescore_workspace_size(int64_t H, int64_t W, int32_t k_top, size_t *bytes) {
+    if (!bytes) return fail(MF_EINVAL, "bytes is NULL");
+    if (H < 1 || W < 1 || k_top < 1) return fail(MF_EINVAL, "bad sizes");
+    *bytes = mf::rescore_workspace(H, W, k_top);
+    return ok();
+}
+
+mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint8_t *mask,
+                          const mf_prf_table *table, const float *snr_max, const int32_t *argmax, int32_t k_top,
+                          mf_candidate *out, int32_t *n_out, void *workspace, size_t workspace_bytes,
+                          mf_stream stream) {
+    mf_status s = check_stack(master);
+    if (s != MF_OK) return s;
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (master->T != table->T) return fail(MF_EINVAL, "stack T differs from table T");
+    if (master->H * master->W == 0) return fail(MF_EINVAL, "empty stack");
+    if (!sigma || !snr_max || !argmax || !out || !n_out) return fail(MF_EINVAL, "NULL argument");
+    if (k_top < 1 || (int64_t)k_top > master->H * master->W) return fail(MF_EINVAL, "k_top=%d out of range", k_top);
+    if (k_top > (1 << 16)) return fail(MF_EUNSUPPORTED, "k_top above 65536");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != table->device)
+        return fail(MF_EINVAL, "table lives on device %d, current device is %d", table->device, dev);
+    const size_t need = mf::rescore_workspace(master->H, master->W, k_top);
+    if (!workspace || workspace_bytes < need)
+        return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", need, workspace_bytes);
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    mf::RescoreArgs a{master, sigma, mask, table, snr_max, argmax, k_top, out, n_out, (char *)workspace,
+                      workspace_bytes, stream};
+    char err[256] = {0};
+    const int rc = mf::launch_rescore(a, err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
+const char *mf_last_error(void) { return g_err.c_str(); }
+
+mf_status mf_device_status(void) {
+    int st = 0;
+    const int rc = mf::read_device_status(&st);
+    if (rc != 0) return fail(MF_ECUDA, "%s", cudaGetErrorString((cudaError_t)rc));
+    if (st != 0) return fail(MF_ETIMEOUT, "a device wait ran out of its budget (code %d)", st);
+    return ok();
+}
+
+const char *mf_version(void) { return "libmf 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+"""Parity of mf_search (CUDA, through the C ABI) with the FP64 oracle.
+
+Element-by-element on seeded inputs at sizes the oracle finishes in seconds,
+spanning several tiles and ragged tails; the bar is |delta SNR| <= 1e-5 *
+max(1, |SNR|) and identical argmax wherever the two best filters differ by
+more than 1e-3."""
+import numpy as np
+import pytest
+
+from _util import check_search
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2209_09848_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    m.load()
+    return m
+
+
+def _run(mf, res, sigma, mask, table, want_all=True, frame_scale=None, dtype=torch.float32):
+    dev = "cuda"
+    r = torch.from_numpy(res).to(dev).to(dtype)
+    s = torch.from_numpy(sigma).to(dev)
+    m = None if mask is None else torch.from_numpy(mask).to(dev)
+    fs = None if frame_scale is None else torch.as_tensor(frame_scale, dtype=torch.float32, device=dev)
+    smax, amax, sall = mf.search(r, s, table, mask=m, frame_scale=fs, want_all=want_all)
+    torch.cuda.synchronize()
+    assert mf.device_status() == 0
+    return smax.cpu().numpy(), amax.cpu().numpy(), None if sall is None else sall.cpu().numpy()
+
+
+def test_small_config_full_cube(mf, oracle):
+    from paper_2209_09848_gb300 import synth
+    c = synth.small_config(0)
+    table = mf.prf_table_create(c["vx"], c["vy"], 32)
+    sh, tp = table.export()
+    sh_o, tp_o = oracle.trajectory_table(c["vx"], c["vy"], 32)
+    assert np.array_equal(sh, sh_o)
+    np.testing.assert_allclose(tp, tp_o, rtol=0, atol=1e-15)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh_o, tp_o)
+    smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    check_search(smax, amax, sall, N, D, oracle, label="small config")
+
+
+CASES = [
+    # T, H, W, K, seed, mask_frac, max speed, custom
+    (1, 37, 45, 1, 1, 0.0, 0.5, False),
+    (2, 64, 96, 7, 2, 0.02, 0.6, False),
+    (33, 50, 70, 16, 3, 0.01, 0.3, False),
+    (5, 100, 33, 9, 4, 0.05, 1.2, False),
+    (17, 41, 77, 11, 5, 0.02, 0.0, True),
+    (40, 70, 130, 24, 6, 0.01, 0.15, False),
+]
+
+
+@pytest.mark.parametrize("T,H,W,K,seed,mask_frac,vmax,custom", CASES)
+def test_random_shapes(mf, oracle, T, H, W, K, seed, mask_frac, vmax, custom):
+    from paper_2209_09848_gb300 import synth
+    c = synth.small_case(T, H, W, seed, mask_frac=mask_frac, movers=2)
+    g = np.random.default_rng(100 + seed)
+    if custom:
+        sh = g.integers(-6, 7, size=(K, T, 2)).astype(np.int32)
+        tp = g.uniform(-0.2, 1.0, size=(K, T, 5, 5))  # arbitrary footprints
+        table = mf.prf_table_create_custom(sh, tp)
+    else:
+        vx = g.uniform(-vmax, vmax, K)
+        vy = g.uniform(-vmax, vmax, K)
+        table = mf.prf_table_create(vx, vy, T)
+        sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    check_search(smax, amax, sall, N, D, oracle, label="case %s" % ((T, H, W, K),))
+
+
+def test_frame_scale_and_half_precision_storage(mf, oracle):
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 12, 48, 80
+    c = synth.small_case(T, H, W, 7, mask_frac=0.01, movers=2)
+    vx, vy = synth.velocity_grid(3, 3, -0.3, 0.3)
+    table = mf.prf_table_create(vx, vy, T)
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    for dt in (torch.bfloat16, torch.float16):
+        scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14).astype(np.float32) if dt == torch.float16 \
+            else np.ones(T, np.float32)
+        q = torch.from_numpy(c["res"] / scale[:, None, None]).to(dt)
+        deq = q.float().numpy()  # the values the GPU reads, before scaling
+        N, D = oracle.search_full(deq, lam, sh, tp, frame_scale=scale.astype(np.float64))
+        smax, amax, sall = _run(mf, q.float().numpy(), c["sigma"], c["mask"], table, frame_scale=scale, dtype=dt)
+        check_search(smax, amax, sall, N, D, oracle, label=str(dt))
+
+
+def test_velocity_zero_and_single_pixel_frames(mf, oracle):
+    from paper_2209_09848_gb300 import synth
+    for (T, H, W) in [(3, 1, 1), (4, 1, 40), (2, 33, 1), (1, 5, 5)]:
+        c = synth.small_case(T, H, W, 9)
+        vx = np.array([0.0, 0.4, -0.7])
+        vy = np.array([0.0, -0.2, 0.9])
+        table = mf.prf_table_create(vx, vy, T)
+        sh, tp = oracle.trajectory_table(vx, vy, T)
+        lam = oracle.inverse_variance(c["sigma"], None)
+        N, D = oracle.search_full(c["res"], lam, sh, tp)
+        smax, amax, sall = _run(mf, c["res"], c["sigma"], None, table)
+        check_search(smax, amax, sall, N, D, oracle, label="tiny %s" % ((T, H, W),))
+
+
+def test_fully_masked_gives_minus_one(mf):
+    T, H, W = 4, 20, 20
+    res = np.random.default_rng(0).standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.ones((H, W), np.float32)
+    mask = np.ones((H, W), np.uint8)
+    table = mf.prf_table_create([0.1, -0.1], [0.0, 0.2], T)
+    smax, amax, sall = _run(mf, res, sigma, mask, table)
+    assert np.all(amax == -1) and np.all(smax == 0) and np.all(sall == 0)
+
+
+def test_empty_frame_is_a_no_op(mf):
+    table = mf.prf_table_create([0.1], [0.0], 3)
+    r = torch.zeros((3, 0, 7), device="cuda")
+    s = torch.ones((0, 7), device="cuda")
+    smax, amax, _ = mf.search(r, s, table)
+    torch.cuda.synchronize()
+    assert smax.numel() == 0 and amax.numel() == 0
+
+
+def test_invalid_arguments_enqueue_nothing(mf):
+    T, H, W = 4, 16, 16
+    table = mf.prf_table_create([0.1], [0.0], T)
+    r = torch.zeros((T + 1, H, W), device="cuda")
+    s = torch.ones((H, W), device="cuda")
+    with pytest.raises(mf.MFError) as e:
+        mf.search(r, s, table)
+    assert e.value.status == 1 and "T=" in str(e.value)
+    r = torch.zeros((T, H, W), device="cuda")
+    with pytest.raises(mf.MFError):
+        mf.search(r, s, table, workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(mf.MFError):
+        mf.prf_table_create([float("nan")], [0.0], T)
+    with pytest.raises(mf.MFError):
+        mf.prf_table_create([0.1], [0.0], T, sigma_px=-1.0)
+    with pytest.raises(mf.MFError):
+        mf.prf_table_create([0.1], [0.0], T, kind=7)
+
+
+def test_deterministic_reruns(mf):
+    from paper_2209_09848_gb300 import synth
+    c = synth.small_case(20, 64, 64, 11, mask_frac=0.01, movers=3)
+    vx, vy = synth.velocity_grid(4, 4, -0.2, 0.2)
+    table = mf.prf_table_create(vx, vy, 20)
+    a = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    b = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
