@@ -1,0 +1,409 @@
+#!/usr/bin/env python3
+"""Benchmark of the trajectory matched filter (Ganapathi 2022, Section 3.2).
+
+Workload: the paper-shaped search -- 1000 frames of 2048 x 2048 float32
+residuals, log-normal per-pixel sigma, 1 % clustered star mask, 200 injected
+linear movers, 100 trajectories on a 10 x 10 velocity grid over +-0.1 px/frame
+(synthetic stand-ins for TESS full-frame images; seeded).
+
+One step = one pass of the hot path over that stack: mf_search (inverse
+variance, weighted stack, FP64-accumulated denominator, FP32 numerator
+stencil, SNR max/argmax over the filter bank) followed by mf_rescore_topk
+(top 4096 candidates re-scored in FP64).  The filter-bank table is built once
+before timing.  Metric: trajectory x pixel x frame updates per second.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank searches its own stack (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "traj*pixel*frame/s at 1000x2048^2x100 traj"
+UNIT = "traj*pixel*frame/s"
+T_FR, HH, WW, NXG, NYG, VMAX = 1000, 2048, 2048, 10, 10, 0.1
+K_TOP = 4096
+FLOP_PER_UNIT = 50  # 25 FP32 FMAs per (trajectory, pixel, frame): the general 5x5 footprint
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+def _fp32_peak_tflops(sm_mhz):
+    """FFMA peak from unit counts and clock: SMs x FP32 lanes x 2 flop x clock."""
+    return SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+                power.append(float(parts[3].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _traffic_from_profiles():
+    """DRAM bytes per numerator launch from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "k_numerator_paper_shaped.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_full_launch:"):
+                    v = line.split(":", 1)[1].strip()
+                    return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+def cpu_oracle_sample(res_dev, sigma_np, mask_np, vx, vy, T, budget_s=15.0, threads=None):
+    """Time the FP64 oracle on host cores over a crop of the same workload:
+    all trajectories and frames, start pixels in a centred square sized for
+    about `budget_s` seconds of CPU work.  Returns (units/s, cores, sample text,
+    (oracle snr, crop origin, side))."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    cores = threads or oracle.threads()
+    H, W = sigma_np.shape
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    halo = int(np.abs(shifts).max()) + 3
+
+    def run(side):
+        y0, x0 = (H - side) // 2, (W - side) // 2
+        ya, yb = max(0, y0 - halo), min(H, y0 + side + halo)
+        xa, xb = max(0, x0 - halo), min(W, x0 + side + halo)
+        sub = res_dev[:, ya:yb, xa:xb].contiguous().cpu().numpy()
+        sig = np.ascontiguousarray(sigma_np[ya:yb, xa:xb])
+        msk = None if mask_np is None else np.ascontiguousarray(mask_np[ya:yb, xa:xb])
+        lam = oracle.inverse_variance(sig, msk)
+        ys, xs = np.meshgrid(np.arange(y0 - ya, y0 - ya + side), np.arange(x0 - xa, x0 - xa + side),
+                             indexing="ij")
+        K = len(vx)
+        ys = np.repeat(ys.ravel(), K)
+        xs = np.repeat(xs.ravel(), K)
+        ks = np.tile(np.arange(K), side * side)
+        t0 = time.perf_counter()
+        N, D = oracle.search_points(sub, lam, shifts, taps, ys, xs, ks)
+        dt = time.perf_counter() - t0
+        return dt, N.reshape(side, side, K), D.reshape(side, side, K), (y0, x0)
+
+    dt, *_ = run(8)
+    per_px = dt / 64.0
+    side = int(max(8, min(256, (budget_s / max(per_px, 1e-9)) ** 0.5)))
+    dt, N, D, origin = run(side)
+    units = side * side * len(vx) * T
+    sample = "%dx%d start pixels x %d trajectories x %d frames (crop of the same stack)" % (side, side, len(vx), T)
+    return units / dt, cores, sample, (N, D, origin, side)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, each step a bounded
+    sample of the same workload (generated on the host with the same recipe)."""
+    import numpy as np
+
+    import oracle
+    from paper_2209_09848_gb300 import synth
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    oracle.build()
+    side = int(os.environ.get("MF_REF_SIDE", "48"))
+    vx, vy = synth.velocity_grid(NXG, NYG, -VMAX, VMAX)
+    shifts, taps = oracle.trajectory_table(vx, vy, T_FR)
+    halo = int(np.abs(shifts).max()) + 3
+    hs = side + 2 * halo
+    rng = np.random.default_rng(7)
+    sigma = np.exp(0.3 * rng.standard_normal((hs, hs))).astype(np.float32)
+    mask = synth.star_mask(hs, hs, rng, 0.01)
+    res = (sigma[None] * rng.standard_normal((T_FR, hs, hs), dtype=np.float32)).astype(np.float32)
+    lam = oracle.inverse_variance(sigma, mask)
+    K = len(vx)
+    yy, xx = np.meshgrid(np.arange(halo, halo + side), np.arange(halo, halo + side), indexing="ij")
+    ys, xs = np.repeat(yy.ravel(), K), np.repeat(xx.ravel(), K)
+    ks = np.tile(np.arange(K), side * side)
+    for _ in range(args.warmup):
+        oracle.search_points(res, lam, shifts, taps, ys[:K * 4], xs[:K * 4], ks[:K * 4])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        N, D = oracle.search_points(res, lam, shifts, taps, ys, xs, ks)
+        snr, valid, smax, amax = oracle.snr_and_best(N.reshape(side * side, K).T[:, :, None],
+                                                     D.reshape(side * side, K).T[:, :, None])
+        times.append(time.perf_counter() - t0)
+    units = side * side * K * T_FR
+    dt = sum(times) / len(times)
+    value = units / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper-shaped search, 1000 frames x 2048^2 px x 100 trajectories (FP64 oracle "
+                               "on a %dx%d start-pixel sample per step)" % (side, side),
+                   "frames": T_FR, "height": HH, "width": WW, "trajectories": K},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": "%dx%d start pixels x %d trajectories x %d frames per step" % (side, side, K,
+                                                                                                   T_FR)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the search runs only in the CUDA library)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2209_09848_gb300 import _build
+    _build.build()
+    import paper_2209_09848_gb300 as mf
+    from paper_2209_09848_gb300 import synth
+
+    T, H, W = args.frames, args.size, args.size
+    case = synth.paper_case_gpu(T=T, H=H, W=W, seed=1 + rank, device=dev)
+    vx, vy = synth.velocity_grid(NXG, NYG, -VMAX, VMAX)
+    K = len(vx)
+    table = mf.prf_table_create(vx, vy, T)
+    info = table.info()
+    res, sigma, mask = case["res"], case["sigma"], case["mask"]
+    ws_search = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
+    ws_rescore = torch.empty(mf.rescore_workspace_size(H, W, K_TOP), dtype=torch.uint8, device=dev)
+    snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
+    argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        mf.search(res, sigma, table, mask=mask, workspace=ws_search, out=(snr_max, argmax, None), stream=stream)
+        if not args.no_rescore:
+            mf.rescore_topk(res, sigma, table, snr_max, argmax, K_TOP, mask=mask, workspace=ws_rescore,
+                            stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if mf.device_status() != 0:
+        raise SystemExit("device status word set during warm-up")
+    mf.profile_enable(True)
+    mf.profile_read(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = mf.profile_read(reset=True)
+    mf.profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units_rank = K * T * H * W
+    value = units_rank * ws / (ms * 1e-3)
+
+    peaks, peak_src = _peaks()
+    num_launches, num_ms_total = prof["k_numerator"]
+    num_ms = num_ms_total / max(1, num_launches)
+    peak_tf = _fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    achieved_tf = units_rank * FLOP_PER_UNIT / (num_ms * 1e-3) / 1e12
+    traffic = _traffic_from_profiles()
+    kernel_ms = {k: round(v[1] / max(1, v[0]), 3) for k, v in prof.items() if k != "_launches" and v[0]}
+    launches = int(prof["_launches"])
+
+    # end to end through the same public calls, stack in pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((T, H, W), dtype=torch.float32, pin_memory=True)
+        host.copy_(res)
+        out_max = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+        out_arg = torch.empty((H, W), dtype=torch.int32, pin_memory=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        dev_stack = res  # reuse the device buffer as the upload target
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            dev_stack.copy_(host, non_blocking=True)
+            mf.search(dev_stack, sigma, table, mask=mask, workspace=ws_search, out=(snr_max, argmax, None),
+                      stream=stream)
+            if not args.no_rescore:
+                mf.rescore_topk(dev_stack, sigma, table, snr_max, argmax, K_TOP, mask=mask,
+                                workspace=ws_rescore, stream=stream)
+            out_max.copy_(snr_max, non_blocking=True)
+            out_arg.copy_(argmax, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": units_rank * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
+               "d2h_bytes_per_step": H * W * 8, "steps": e2e_steps}
+        del host
+
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu:
+        sig_np = case["sigma_np"]
+        msk_np = case["mask_np"]
+        rate, cores, sample, (N, D, (y0, x0), side) = cpu_oracle_sample(res, sig_np, msk_np, vx, vy, T,
+                                                                        budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        # the same crop searched on the GPU just above: report the agreement
+        import oracle
+        snr = np.where(D > 0, N / np.sqrt(np.where(D > 0, D, 1)), -np.inf)
+        o_max = snr.max(axis=2)
+        g_max = snr_max[y0:y0 + side, x0:x0 + side].cpu().numpy().astype(np.float64)
+        err = np.abs(g_max - o_max) / np.maximum(1.0, np.abs(o_max))
+        parity = {"crop": [int(y0), int(x0), int(side)], "max_rel_err_snr_max": float(err.max()),
+                  "tolerance": 1e-5}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper-shaped search: %d frames x %dx%d px float32, %d trajectories "
+                                   "(%dx%d grid, |v|<=%.2f px/frame), sigma log-normal, 1%% star mask, "
+                                   "200 movers; search + top-%d FP64 rescore per step" % (
+                                       T, H, W, K, NXG, NYG, VMAX, K_TOP),
+                       "frames": T, "height": H, "width": W, "trajectories": K,
+                       "l2": "inputs larger than L2 (%.1f GB stack per step)" % (T * H * W * 4 / 1e9),
+                       "plan": {k: info[k] for k in ("groups", "warps_per_group", "tile_h", "tile_w",
+                                                      "window_pitch", "window_rows", "vec")},
+                       "parallelism": "weak scaling: independent stack per GPU" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_numerator", "achieved": achieved_tf, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s)" % (
+                             float(peaks.get("sm_max_mhz", 2070.0)), peak_src),
+                         "flop_per_unit": FLOP_PER_UNIT, "avg_launch_ms": num_ms},
+            "kernel_ms": kernel_ms,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if parity:
+            line["parity"] = parity
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=T_FR)
+    ap.add_argument("--size", type=int, default=HH)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-rescore", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -117,6 +117,27 @@ typedef struct mf_prf_table mf_prf_table;
 mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy,
                               int32_t K, int32_t T, mf_prf_table **out);
 
+/* Kernel-layout choices for a table (not in the paper).  shape selects how a
+ * numerator CTA's 16 warps split between trajectories and 32 x 32 sub-tiles:
+ * 0: 16 trajectories x 1 sub-tile, 1: 8 x (1 x 2), 2: 4 x (2 x 2),
+ * 3: 2 x (2 x 4) (rows x columns of sub-tiles); -1 lets the planner's cost
+ * model choose.
+ * An autotuner times several shapes and keeps the fastest. */
+typedef struct {
+    int32_t shape;
+    int32_t vec;         /* floats per shared-memory load in the numerator: 1, 2, 4; 0 = default */
+    int32_t lockstep;    /* numerator frame hand-off: 1 = CTA barrier per frame, 0 = last warp
+                            out refills the stage, -1 = default */
+    int32_t reserved[5];
+} mf_plan_opts;
+
+/* mf_prf_table_create with layout options (opts NULL = automatic).
+ * MF_EUNSUPPORTED if the requested shape cannot hold the trajectories'
+ * frame windows in shared memory. */
+mf_status mf_prf_table_create_ex(const mf_prf_params *prf, const double *vx, const double *vy,
+                                 int32_t K, int32_t T, const mf_plan_opts *opts,
+                                 mf_prf_table **out);
+
 /* Build a filter bank from explicit per-(k, t) shifts and footprints (host
  * arrays): shifts[(k*T + t)*2 + 0] = s_x, [.. + 1] = s_y;
  * taps[(k*T + t)*25 + (b + 2)*5 + (a + 2)] = W_{k,t}(a, b), a = column offset,
@@ -137,6 +158,35 @@ mf_status mf_prf_table_dims(const mf_prf_table *table, int32_t *K, int32_t *T);
 /* Copy the FP64 filter bank back to host arrays laid out as in
  * mf_prf_table_create_custom (either pointer may be NULL). */
 mf_status mf_prf_table_export(const mf_prf_table *table, int32_t *shifts, double *taps);
+
+/* How the library laid out a filter bank for the kernels (not in the paper):
+ * trajectories are grouped so that a CTA's warps share one staged frame
+ * window; these numbers describe that grouping and its memory. */
+typedef struct {
+    int32_t K, T;
+    int32_t groups;           /* trajectory groups = CTAs per output tile */
+    int32_t warps_per_group;  /* trajectories per CTA */
+    int32_t tile_h, tile_w;   /* output tile of one CTA, start pixels */
+    int32_t window_pitch;     /* floats per staged window row */
+    int32_t window_rows;      /* rows of the largest staged window */
+    int32_t segments;         /* rows of the collapsed denominator kernels */
+    int32_t max_abs_shift;    /* largest |s| over all (k, t), pixels */
+    int64_t g_nnz;            /* nonzero weights of the collapsed denominator kernels */
+    int64_t smem_bytes;       /* dynamic shared memory of the numerator kernel */
+    int64_t device_bytes;     /* device memory the table holds */
+    double cost;              /* planner's estimate, SM cycles per start pixel */
+    int32_t vec;              /* floats per shared-memory load in the numerator */
+    int32_t lockstep;         /* numerator frame hand-off (see mf_plan_opts) */
+} mf_table_info;
+
+/* Layout of an existing table. */
+mf_status mf_prf_table_info(const mf_prf_table *table, mf_table_info *info);
+
+/* Plan a Gaussian-PRF filter bank on the host only (same arguments and errors
+ * as mf_prf_table_create) and report its layout; allocates no device memory
+ * and needs no GPU.  device_bytes is what mf_prf_table_create would allocate. */
+mf_status mf_prf_plan(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                      int32_t T, const mf_plan_opts *opts, mf_table_info *info);
 
 /* Bytes of workspace mf_search needs for this stack shape and table. */
 mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *table,
@@ -177,12 +227,37 @@ mf_status mf_rescore_workspace_size(int64_t H, int64_t W, int32_t k_top, size_t 
  * should be the FP32 residuals (bf16/fp16 are accepted and read as stored).
  * out: device mf_candidate[k_top], sorted by snr_search descending then flat
  * index; n_out: device int32, the number written (<= k_top).
- * Errors: MF_EINVAL (k_top < 1 or > H*W, shape mismatch, NULL pointers). */
+ * Errors: MF_EINVAL (k_top < 1 or > H*W, shape mismatch, NULL pointers),
+ * MF_EUNSUPPORTED (k_top above 16384). */
 mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint8_t *mask,
                           const mf_prf_table *table, const float *snr_max,
                           const int32_t *argmax, int32_t k_top, mf_candidate *out,
                           int32_t *n_out, void *workspace, size_t workspace_bytes,
                           mf_stream stream);
+
+/* Per-kernel accounting of the library's own launches (for benchmarks and
+ * roofline reports; not in the paper).  Launch counts are always kept; device
+ * times are recorded with CUDA events on the launching stream only while
+ * profiling is enabled. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double ms;          /* summed device time while profiling was on */
+} mf_kernel_stat;
+
+typedef struct {
+    int32_t n;          /* entries filled in k[] */
+    int32_t reserved;
+    int64_t launches;   /* all kernel launches counted */
+    mf_kernel_stat k[16];
+} mf_profile;
+
+/* Turn event timing on (1) or off (0) for subsequent launches. */
+mf_status mf_profile_enable(int32_t on);
+
+/* Copy the counters out (waits for the recorded events); reset != 0 clears
+ * them afterwards. */
+mf_status mf_profile_read(mf_profile *out, int32_t reset);
 
 /* Text of the last error on this host thread ("" if none). */
 const char *mf_last_error(void);

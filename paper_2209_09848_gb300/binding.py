@@ -46,6 +46,43 @@ class Candidate(ctypes.Structure):
 CANDIDATE_BYTES = ctypes.sizeof(Candidate)
 
 
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("vec", ctypes.c_int32), ("lockstep", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+def _opts(shape=None, vec=None, lockstep=None):
+    if shape is None and vec is None and lockstep is None:
+        return None
+    o = PlanOpts()
+    o.shape = -1 if shape is None else int(shape)
+    o.vec = 0 if vec is None else int(vec)
+    o.lockstep = -1 if lockstep is None else int(lockstep)
+    return ctypes.byref(o)
+
+
+class TableInfo(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("T", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("warps_per_group", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("window_pitch", ctypes.c_int32),
+                ("window_rows", ctypes.c_int32), ("segments", ctypes.c_int32),
+                ("max_abs_shift", ctypes.c_int32), ("g_nnz", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("cost", ctypes.c_double), ("vec", ctypes.c_int32),
+                ("lockstep", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("reserved", ctypes.c_int32), ("launches", ctypes.c_int64),
+                ("k", KernelStat * 16)]
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -63,14 +100,21 @@ def load():
         pp = ctypes.POINTER(ctypes.c_void_p)
         sig = {
             "mf_prf_table_create": ([ctypes.POINTER(PrfParams), P, P, I32, I32, pp], ctypes.c_int),
+            "mf_prf_table_create_ex": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(PlanOpts), pp],
+                                       ctypes.c_int),
             "mf_prf_table_create_custom": ([P, P, I32, I32, pp], ctypes.c_int),
             "mf_prf_table_destroy": ([P], None),
             "mf_prf_table_dims": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
             "mf_prf_table_export": ([P, P, P], ctypes.c_int),
+            "mf_prf_table_info": ([P, ctypes.POINTER(TableInfo)], ctypes.c_int),
+            "mf_prf_plan": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(PlanOpts),
+                             ctypes.POINTER(TableInfo)], ctypes.c_int),
             "mf_search_workspace_size": ([ctypes.POINTER(Stack), P, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_search": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P, SZ, P], ctypes.c_int),
             "mf_rescore_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
+            "mf_profile_enable": ([I32], ctypes.c_int),
+            "mf_profile_read": ([ctypes.POINTER(Profile), I32], ctypes.c_int),
             "mf_last_error": ([], ctypes.c_char_p),
             "mf_device_status": ([], ctypes.c_int),
             "mf_version": ([], ctypes.c_char_p),
@@ -127,6 +171,11 @@ class PrfTable:
                                           taps.ctypes.data_as(ctypes.c_void_p)))
         return shifts, taps
 
+    def info(self) -> dict:
+        inf = TableInfo()
+        _check(load().mf_prf_table_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
     def destroy(self):
         if self._h:
             load().mf_prf_table_destroy(self._h)
@@ -139,7 +188,8 @@ class PrfTable:
             pass
 
 
-def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0) -> PrfTable:
+def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, shape=None, vec=None, lockstep=None) -> PrfTable:
+    """mf_prf_table_create / mf_prf_table_create_ex (shape = CTA layout, None = automatic)."""
     import numpy as np
     vx = np.ascontiguousarray(vx, np.float64)
     vy = np.ascontiguousarray(vy, np.float64)
@@ -147,10 +197,28 @@ def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0) -> PrfTable:
         raise ValueError("vx and vy must be 1-D of equal length")
     prm = PrfParams(int(kind), 0, float(sigma_px))
     h = ctypes.c_void_p()
-    _check(load().mf_prf_table_create(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                                      vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
-                                      ctypes.byref(h)))
+    if shape is None and vec is None and lockstep is None:
+        _check(load().mf_prf_table_create(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                                          vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+                                          ctypes.byref(h)))
+    else:
+        _check(load().mf_prf_table_create_ex(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                                             vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+                                             _opts(shape, vec, lockstep), ctypes.byref(h)))
     return PrfTable(h)
+
+
+def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, shape=None, vec=None, lockstep=None) -> dict:
+    """mf_prf_plan: host-only layout of a Gaussian-PRF filter bank (no GPU needed)."""
+    import numpy as np
+    vx = np.ascontiguousarray(vx, np.float64)
+    vy = np.ascontiguousarray(vy, np.float64)
+    prm = PrfParams(int(kind), 0, float(sigma_px))
+    inf = TableInfo()
+    _check(load().mf_prf_plan(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                              vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T), _opts(shape, vec, lockstep),
+                              ctypes.byref(inf)))
+    return inf.as_dict()
 
 
 def prf_table_create_custom(shifts, taps) -> PrfTable:
@@ -254,6 +322,19 @@ def decode_candidates(raw: torch.Tensor, n: int):
     dt = np.dtype([("y", "<i4"), ("x", "<i4"), ("k", "<i4"), ("r", "<i4"), ("snr", "<f8"),
                    ("flux", "<f8"), ("snr_search", "<f4"), ("r2", "<f4")])
     return np.frombuffer(buf, dtype=dt, count=n)
+
+
+def profile_enable(on: bool = True):
+    _check(load().mf_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = True) -> dict:
+    """{kernel name: (launches, summed device ms)} plus '_launches' total."""
+    p = Profile()
+    _check(load().mf_profile_read(ctypes.byref(p), 1 if reset else 0))
+    out = {p.k[i].name.decode(): (int(p.k[i].launches), float(p.k[i].ms)) for i in range(p.n)}
+    out["_launches"] = int(p.launches)
+    return out
 
 
 def device_status() -> int:

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 
@@ -73,10 +74,10 @@ void footprint(int kind, double sigma, double phx, double phy, double *w) {
     for (int i = 0; i < 25; i++) w[i] /= total;
 }
 
-// Balanced k-d split of the velocity set into `groups` parts of at most
-// kWarpsPerCta members, so that trajectories sharing a CTA (and its frame
-// window) have similar shifts at every frame.
-void kd_split(std::vector<int> &idx, int lo, int hi, int groups, const std::vector<double> &ex,
+// Balanced k-d split of the velocity set into `groups` parts of at most `cap`
+// members, so that trajectories sharing a CTA (and its frame window) have
+// similar shifts at every frame.
+void kd_split(std::vector<int> &idx, int lo, int hi, int groups, int cap, const std::vector<double> &ex,
               const std::vector<double> &ey, std::vector<std::vector<int>> &out) {
     const int n = hi - lo;
     if (groups <= 1 || n <= 1) {
@@ -91,8 +92,8 @@ void kd_split(std::vector<int> &idx, int lo, int hi, int groups, const std::vect
         y0 = std::min(y0, ey[idx[i]]);
         y1 = std::max(y1, ey[idx[i]]);
     }
-    // x spread is cheaper than y spread (window rows are padded to 32-word
-    // pitch anyway), so split y first when they are comparable.
+    // a column of spread costs less than a row (rows are padded to a 32-word
+    // pitch anyway), so split along y unless x is clearly wider
     const bool by_x = (x1 - x0) > 1.5 * (y1 - y0);
     auto key = [&](int a, int b) {
         const double pa = by_x ? ex[a] : ey[a], pb = by_x ? ex[b] : ey[b];
@@ -104,27 +105,33 @@ void kd_split(std::vector<int> &idx, int lo, int hi, int groups, const std::vect
     std::sort(idx.begin() + lo, idx.begin() + hi, key);
     const int g1 = groups / 2, g2 = groups - g1;
     int n1 = (int)std::llround((double)n * g1 / groups);
-    n1 = std::max(n1, n - g2 * mf::kWarpsPerCta);
-    n1 = std::min(n1, g1 * mf::kWarpsPerCta);
+    n1 = std::max(n1, n - g2 * cap);
+    n1 = std::min(n1, g1 * cap);
     n1 = std::max(0, std::min(n, n1));
-    kd_split(idx, lo, lo + n1, g1, ex, ey, out);
-    kd_split(idx, lo + n1, hi, g2, ex, ey, out);
+    kd_split(idx, lo, lo + n1, g1, cap, ex, ey, out);
+    kd_split(idx, lo + n1, hi, g2, cap, ex, ey, out);
 }
 
-size_t smem_bytes(const mf::Plan &p) {
-    return (size_t)mf::kStages * p.BH * p.S * sizeof(float) +
-           (size_t)mf::kStages * sizeof(mf::FrameBlock) + 8192 + 256 + 1024;
-}
+size_t smem_bytes(const mf::Plan &p) { return mf::numerator_smem_bytes(p.S, p.BH, p.kt()); }
 
-// Window geometry of a grouping: fills S, BH; false if it does not fit.
+// Window geometry and estimated cost of a grouping; false if it does not fit.
+// Cost model per CTA and frame, in SM cycles: the numerator is latency-bound
+// with one 16-warp CTA per SM, so a CTA-frame costs about the issue time of
+// all its warps (idle slots included: they leave the SM with fewer warps to
+// switch between), unless the shared-memory traffic of the loads plus the
+// staged window takes longer.  Summed over groups and frames and divided by
+// the tile area.
 bool measure(mf::Plan &p, const mf_prf_table &t) {
-    int max_offx = 0, max_rows = 0;
+    const int kt = p.kt();
+    const mf::Shape sh = mf::kShapes[p.shape];
+    int max_offx = 0, max_spread_y = 0;
+    std::vector<int> rows((size_t)p.G * t.T, 0);
     for (int g = 0; g < p.G; g++) {
         for (int f = 0; f < t.T; f++) {
             int64_t mnx = INT64_MAX, mxx = INT64_MIN, mny = INT64_MAX, mxy = INT64_MIN;
             bool any = false;
-            for (int w = 0; w < mf::kWarpsPerCta; w++) {
-                const int k = p.members[g * mf::kWarpsPerCta + w];
+            for (int w = 0; w < kt; w++) {
+                const int k = p.members[(size_t)g * kt + w];
                 if (k < 0) continue;
                 any = true;
                 const int64_t sx = t.shifts[((size_t)k * t.T + f) * 2 + 0];
@@ -137,12 +144,27 @@ bool measure(mf::Plan &p, const mf_prf_table &t) {
             if (!any) continue;
             const int64_t rox = 4 * floor_div(mnx - 2, 4);
             max_offx = (int)std::max<int64_t>(max_offx, mxx - 2 - rox);
-            max_rows = (int)std::max<int64_t>(max_rows, (mxy - mny) + 36);
+            max_spread_y = (int)std::max<int64_t>(max_spread_y, mxy - mny);
+            rows[(size_t)g * t.T + f] = (int)round_up(mxy - mny + p.tile_h() + 4, mf::kLoadRows);
         }
     }
-    p.S = (int)round_up(max_offx + 43, 32);
-    p.BH = (int)round_up(max_rows, mf::kLoadRows);
-    return p.S <= 256 && p.BH <= 256 && smem_bytes(p) <= (size_t)mf::kSmemBudget;
+    // widest read: offx + tile_w - 32 + 24 (lanes) + 7 (skew) + 3 (alignment) + 12
+    p.S = (int)round_up(max_offx + p.tile_w() + 14, 32);
+    p.BH = (int)round_up(max_spread_y + p.tile_h() + 4, mf::kLoadRows);
+    if (!(p.S <= 256 && p.BH <= 256 && smem_bytes(p) <= (size_t)mf::kSmemBudget)) return false;
+    double cyc = 0.0;
+    for (int g = 0; g < p.G; g++) {
+        int active = 0;
+        for (int w = 0; w < kt; w++) active += p.members[(size_t)g * kt + w] >= 0;
+        const int aw = active * sh.txs * sh.tys;
+        const double issue = mf::kWarps * 950.0 / 4.0;
+        for (int f = 0; f < t.T; f++) {
+            const double smem = aw * 105.0 + rows[(size_t)g * t.T + f] * (double)p.S / 32.0;
+            cyc += std::max(issue, smem);
+        }
+    }
+    p.cost = cyc / ((double)p.tile_h() * p.tile_w());
+    return true;
 }
 
 mf_status plan_groups(mf_prf_table &t) {
@@ -159,35 +181,49 @@ mf_status plan_groups(mf_prf_table &t) {
         ex[k] += 1e-3 * t.shifts[first + 0];
         ey[k] += 1e-3 * t.shifts[first + 1];
     }
-    int G = (K + mf::kWarpsPerCta - 1) / mf::kWarpsPerCta;
-    for (;;) {
-        std::vector<int> idx(K);
-        std::iota(idx.begin(), idx.end(), 0);
-        std::vector<std::vector<int>> parts;
-        kd_split(idx, 0, K, G, ex, ey, parts);
-        mf::Plan p;
-        p.G = 0;
-        for (auto &part : parts)
-            if (!part.empty()) p.G++;
-        p.members.assign((size_t)p.G * mf::kWarpsPerCta, -1);
-        int g = 0;
-        for (auto &part : parts) {
-            if (part.empty()) continue;
-            std::sort(part.begin(), part.end());
-            for (size_t i = 0; i < part.size(); i++) p.members[(size_t)g * mf::kWarpsPerCta + i] = part[i];
-            g++;
+    int mx = 0;
+    for (size_t i = 0; i < t.shifts.size(); i++) mx = std::max(mx, std::abs(t.shifts[i]));
+    bool have = false;
+    mf::Plan best;
+    for (int si = 0; si < mf::kNumShapes; si++) {
+        if (t.forced_shape >= 0 && si != t.forced_shape) continue;
+        const int kt = mf::kShapes[si].kt;
+        int G = (K + kt - 1) / kt;
+        for (;;) {
+            std::vector<int> idx(K);
+            std::iota(idx.begin(), idx.end(), 0);
+            std::vector<std::vector<int>> parts;
+            kd_split(idx, 0, K, G, kt, ex, ey, parts);
+            mf::Plan p;
+            p.shape = si;
+            p.vec = t.forced_vec > 0 ? t.forced_vec : 2;
+            p.lockstep = t.forced_lockstep >= 0 ? t.forced_lockstep : 0;
+            p.G = 0;
+            for (auto &part : parts)
+                if (!part.empty()) p.G++;
+            p.members.assign((size_t)p.G * kt, -1);
+            int g = 0;
+            for (auto &part : parts) {
+                if (part.empty()) continue;
+                std::sort(part.begin(), part.end());
+                for (size_t i = 0; i < part.size(); i++) p.members[(size_t)g * kt + i] = part[i];
+                g++;
+            }
+            if (measure(p, t)) {
+                p.max_abs_shift = mx;
+                if (!have || p.cost < best.cost) {
+                    best = std::move(p);
+                    have = true;
+                }
+                break;
+            }
+            if (G >= K) break;
+            G = std::min(K, std::max(G + 1, G * 5 / 4));
         }
-        if (measure(p, t)) {
-            int mx = 0;
-            for (size_t i = 0; i < t.shifts.size(); i++) mx = std::max(mx, std::abs(t.shifts[i]));
-            p.max_abs_shift = mx;
-            t.plan = std::move(p);
-            return MF_OK;
-        }
-        if (G >= K) break;
-        G = std::min(K, std::max(G + 1, G * 5 / 4));
     }
-    return fail(MF_EUNSUPPORTED, "trajectory shifts too far apart for the frame window");
+    if (!have) return fail(MF_EUNSUPPORTED, "trajectory shifts too far apart for the frame window");
+    t.plan = std::move(best);
+    return MF_OK;
 }
 
 template <class T>
@@ -203,19 +239,34 @@ mf_status upload(T **dst, const T *src, size_t n) {
     return MF_OK;
 }
 
-// Build the device layouts from shifts/taps: plan, frame blocks, headers,
-// denominator segments, FP64 copies.
-mf_status finish_table(mf_prf_table *t) {
+struct HostLayouts {
+    std::vector<mf::FrameHdr> hdr;
+    std::vector<unsigned char> blocks;
+    std::vector<mf::RunRec> runs;
+    std::vector<int32_t> run_off;
+    std::vector<float> wts;
+};
+
+size_t layout_bytes(const mf_prf_table *t, const HostLayouts &h) {
+    return h.blocks.size() + h.hdr.size() * sizeof(mf::FrameHdr) + h.runs.size() * sizeof(mf::RunRec) +
+           h.run_off.size() * sizeof(int32_t) + h.wts.size() * sizeof(float) + t->taps.size() * sizeof(double) +
+           t->shifts.size() * sizeof(int32_t);
+}
+
+// Plan the groups and build the layouts the kernels read: frame headers and
+// blocks (numerator), constant-shift runs (denominator).
+mf_status host_layouts(mf_prf_table *t, HostLayouts &out) {
     mf_status s = plan_groups(*t);
     if (s != MF_OK) return s;
     const int K = t->K, T = t->T;
     const mf::Plan &p = t->plan;
+    const int kt = p.kt();
     std::vector<mf::FrameHdr> hdr((size_t)p.G * T);
     for (int g = 0; g < p.G; g++) {
         for (int f = 0; f < T; f++) {
             int64_t mnx = INT64_MAX, mny = INT64_MAX, mxy = INT64_MIN;
-            for (int w = 0; w < mf::kWarpsPerCta; w++) {
-                const int k = p.members[(size_t)g * mf::kWarpsPerCta + w];
+            for (int w = 0; w < kt; w++) {
+                const int k = p.members[(size_t)g * kt + w];
                 if (k < 0) continue;
                 mnx = std::min<int64_t>(mnx, t->shifts[((size_t)k * T + f) * 2 + 0]);
                 mny = std::min<int64_t>(mny, t->shifts[((size_t)k * T + f) * 2 + 1]);
@@ -224,80 +275,139 @@ mf_status finish_table(mf_prf_table *t) {
             mf::FrameHdr &h = hdr[(size_t)g * T + f];
             h.roy = (int32_t)(mny - 2);
             h.rox = (int32_t)(4 * floor_div(mnx - 2, 4));
-            h.nrows = (int32_t)round_up(mxy - mny + 36, mf::kLoadRows);
+            h.nrows = (int32_t)round_up(mxy - mny + p.tile_h() + 4, mf::kLoadRows);
             h.pad = 0;
         }
     }
-    std::vector<mf::FrameBlock> blocks((size_t)p.G * T);
+    const size_t bb = mf::frame_block_bytes(kt);
+    std::vector<unsigned char> blocks((size_t)p.G * T * bb, 0);
     for (int g = 0; g < p.G; g++) {
         for (int f = 0; f < T; f++) {
-            mf::FrameBlock &b = blocks[(size_t)g * T + f];
-            std::memset(&b, 0, sizeof b);
-            if (f + mf::kStages < T) b.next = hdr[(size_t)g * T + f + mf::kStages];
+            unsigned char *b = blocks.data() + ((size_t)g * T + f) * bb;
+            mf::FrameHdr next{0, 0, 0, 0};
+            if (f + mf::kStages < T) next = hdr[(size_t)g * T + f + mf::kStages];
+            std::memcpy(b, &next, sizeof next);
             const mf::FrameHdr &h = hdr[(size_t)g * T + f];
-            for (int w = 0; w < mf::kWarpsPerCta; w++) {
-                const int k = p.members[(size_t)g * mf::kWarpsPerCta + w];
-                mf::SlotRec &r = b.slot[w];
+            for (int w = 0; w < kt; w++) {
+                const int k = p.members[(size_t)g * kt + w];
+                mf::SlotRec r;
+                std::memset(&r, 0, sizeof r);
                 r.k = k;
-                if (k < 0) continue;
-                const size_t kt = (size_t)k * T + f;
-                for (int i = 0; i < 25; i++) r.taps[i] = (float)t->taps[kt * 25 + i];
-                r.offy = t->shifts[kt * 2 + 1] - 2 - h.roy;
-                r.offx = t->shifts[kt * 2 + 0] - 2 - h.rox;
-            }
-        }
-    }
-    // Denominator: collapse runs of frames with the same base shift; the
-    // footprint energies of a run add up because lambda does not depend on t.
-    std::vector<mf::SegRec> segs;
-    std::vector<int32_t> seg_off(K + 1, 0);
-    for (int k = 0; k < K; k++) {
-        seg_off[k] = (int32_t)segs.size();
-        int f = 0;
-        while (f < T) {
-            const int32_t sx = t->shifts[((size_t)k * T + f) * 2 + 0];
-            const int32_t sy = t->shifts[((size_t)k * T + f) * 2 + 1];
-            double acc[25] = {0};
-            int e = f;
-            while (e < T && t->shifts[((size_t)k * T + e) * 2 + 0] == sx &&
-                   t->shifts[((size_t)k * T + e) * 2 + 1] == sy) {
-                for (int i = 0; i < 25; i++) {
-                    const double w = t->taps[((size_t)k * T + e) * 25 + i];
-                    acc[i] += w * w;
+                if (k >= 0) {
+                    const size_t ktf = (size_t)k * T + f;
+                    for (int i = 0; i < 25; i++) r.taps[i] = (float)t->taps[ktf * 25 + i];
+                    r.offy = t->shifts[ktf * 2 + 1] - 2 - h.roy;
+                    r.offx = t->shifts[ktf * 2 + 0] - 2 - h.rox;
                 }
-                e++;
+                std::memcpy(b + sizeof(mf::FrameHdr) + (size_t)w * sizeof(mf::SlotRec), &r, sizeof r);
             }
-            mf::SegRec r;
-            std::memset(&r, 0, sizeof r);
-            for (int i = 0; i < 25; i++) r.w2[i] = (float)acc[i];
-            r.sx = sx;
-            r.sy = sy;
-            segs.push_back(r);
-            f = e;
         }
     }
-    seg_off[K] = (int32_t)segs.size();
-    t->n_seg = (int)segs.size();
-    if ((s = upload(&t->d_blocks, blocks.data(), blocks.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_hdr, hdr.data(), hdr.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_segs, segs.data(), segs.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_seg_off, seg_off.data(), seg_off.size())) != MF_OK) return s;
+    // Denominator: lambda does not depend on t, so D_k(p) = sum_u G_k(u)
+    // lambda(p + u) with the collapsed kernel G_k(u) = sum over (t, a, b)
+    // with s_{k,t} + (a, b) = u of W_{k,t}(a, b)^2, summed here in FP64.
+    // Each row of G_k's support becomes one run of weights starting at a
+    // column that is a multiple of 4 and padded to whole chunks of 8.
+    std::vector<mf::RunRec> runs;
+    std::vector<int32_t> run_off(K + 1, 0);
+    std::vector<float> wts;
+    int64_t nnz_total = 0;
+    for (int k = 0; k < K; k++) {
+        run_off[k] = (int32_t)runs.size();
+        std::map<std::pair<int32_t, int32_t>, double> g;  // (row, column) -> weight
+        for (int f = 0; f < T; f++) {
+            const size_t kt_ = (size_t)k * T + f;
+            const int32_t sx = t->shifts[kt_ * 2 + 0], sy = t->shifts[kt_ * 2 + 1];
+            for (int b = 0; b < 5; b++)
+                for (int a = 0; a < 5; a++) {
+                    const double w = t->taps[kt_ * 25 + b * 5 + a];
+                    g[{sy + b - 2, sx + a - 2}] += w * w;
+                }
+        }
+        nnz_total += (int64_t)g.size();
+        auto it = g.begin();
+        while (it != g.end()) {
+            const int32_t row = it->first.first;
+            auto jt = it;
+            int32_t xmax = it->first.second;
+            while (jt != g.end() && jt->first.first == row) {
+                xmax = jt->first.second;
+                ++jt;
+            }
+            const int32_t x0 = (int32_t)(4 * floor_div(it->first.second, 4));
+            const int32_t nch = (int32_t)((xmax - x0 + 1 + 7) / 8);
+            while (wts.size() % 4) wts.push_back(0.f);
+            mf::RunRec r;
+            r.dy = row;
+            r.x0 = x0;
+            r.nch = nch;
+            r.woff = (int32_t)wts.size();
+            const size_t base = wts.size();
+            wts.resize(base + (size_t)nch * 8, 0.f);
+            for (auto q = it; q != jt; ++q) wts[base + (q->first.second - x0)] = (float)q->second;
+            runs.push_back(r);
+            it = jt;
+        }
+    }
+    run_off[K] = (int32_t)runs.size();
+    t->n_seg = (int)runs.size();
+    t->g_nnz = nnz_total;
+    out.hdr = std::move(hdr);
+    out.blocks = std::move(blocks);
+    out.runs = std::move(runs);
+    out.run_off = std::move(run_off);
+    out.wts = std::move(wts);
+    return MF_OK;
+}
+
+mf_status finish_table(mf_prf_table *t) {
+    HostLayouts h;
+    mf_status s = host_layouts(t, h);
+    if (s != MF_OK) return s;
+    if ((s = upload(&t->d_blocks, h.blocks.data(), h.blocks.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_hdr, h.hdr.data(), h.hdr.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_runs, h.runs.data(), h.runs.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_run_off, h.run_off.data(), h.run_off.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_wts, h.wts.data(), h.wts.size())) != MF_OK) return s;
     if ((s = upload(&t->d_taps64, t->taps.data(), t->taps.size())) != MF_OK) return s;
     if ((s = upload(&t->d_shifts, t->shifts.data(), t->shifts.size())) != MF_OK) return s;
+    t->device_bytes = layout_bytes(t, h);
     return MF_OK;
+}
+
+void fill_info(const mf_prf_table *t, mf_table_info *info) {
+    std::memset(info, 0, sizeof *info);
+    info->K = t->K;
+    info->T = t->T;
+    info->groups = t->plan.G;
+    info->warps_per_group = t->plan.kt();
+    info->tile_h = t->plan.tile_h();
+    info->tile_w = t->plan.tile_w();
+    info->window_pitch = t->plan.S;
+    info->window_rows = t->plan.BH;
+    info->segments = t->n_seg;
+    info->g_nnz = t->g_nnz;
+    info->max_abs_shift = t->plan.max_abs_shift;
+    info->smem_bytes = (int64_t)mf::numerator_smem_bytes(t->plan.S, t->plan.BH, t->plan.kt());
+    info->cost = t->plan.cost;
+    info->vec = t->plan.vec;
+    info->lockstep = t->plan.lockstep;
+    info->device_bytes = (int64_t)t->device_bytes;
 }
 
 void free_device(mf_prf_table *t) {
     cudaFree(t->d_blocks);
     cudaFree(t->d_hdr);
-    cudaFree(t->d_segs);
-    cudaFree(t->d_seg_off);
+    cudaFree(t->d_runs);
+    cudaFree(t->d_run_off);
+    cudaFree(t->d_wts);
     cudaFree(t->d_taps64);
     cudaFree(t->d_shifts);
     t->d_blocks = nullptr;
     t->d_hdr = nullptr;
-    t->d_segs = nullptr;
-    t->d_seg_off = nullptr;
+    t->d_runs = nullptr;
+    t->d_run_off = nullptr;
+    t->d_wts = nullptr;
     t->d_taps64 = nullptr;
     t->d_shifts = nullptr;
 }
@@ -345,9 +455,11 @@ namespace mf {
 
 WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab) {
     WorkspaceLayout L;
-    L.pad = (int64_t)tab->plan.max_abs_shift + 2 + kTile + 8;
-    L.lam_w = round_up(W + 2 * L.pad, 4);
-    L.lam_h = H + 2 * L.pad;
+    // zero border wide enough for every denominator read: shifts up to
+    // max_abs_shift, footprint 2, run padding and the last partial row block
+    L.pad = round_up((int64_t)tab->plan.max_abs_shift + 2 + 16, 4);
+    L.lam_w = round_up(round_up(W, kDenCols) + 2 * L.pad + 32, 4);
+    L.lam_h = round_up(H, 8) + 2 * L.pad;
     L.y_pitch = round_up(W, 4);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -367,10 +479,8 @@ WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_tabl
 
 extern "C" {
 
-mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
-                              int32_t T, mf_prf_table **out) {
-    if (!out) return fail(MF_EINVAL, "out is NULL");
-    *out = nullptr;
+static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                                  int32_t T, mf_prf_table **out_t) {
     if (!prf || !vx || !vy) return fail(MF_EINVAL, "NULL argument");
     if (K < 1 || T < 1) return fail(MF_EINVAL, "K=%d and T=%d must be >= 1", K, T);
     if (T > (1 << 20) || K > (1 << 22)) return fail(MF_EINVAL, "K or T too large");
@@ -400,7 +510,63 @@ mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const 
             footprint(prf->kind, prf->sigma_px, cx - sx, cy - sy, &t->taps[kt * 25]);
         }
     }
+    *out_t = t;
+    return MF_OK;
+}
+
+static mf_status apply_opts(mf_prf_table *t, const mf_plan_opts *opts) {
+    if (!opts) return MF_OK;
+    if (opts->shape < -1 || opts->shape >= mf::kNumShapes) {
+        delete t;
+        return fail(MF_EINVAL, "shape %d out of range", opts->shape);
+    }
+    if (opts->vec != 0 && opts->vec != 1 && opts->vec != 2 && opts->vec != 4) {
+        delete t;
+        return fail(MF_EINVAL, "vec %d must be 0, 1, 2 or 4", opts->vec);
+    }
+    t->forced_shape = opts->shape;
+    t->forced_vec = opts->vec;
+    t->forced_lockstep = opts->lockstep;
+    return MF_OK;
+}
+
+mf_status mf_prf_table_create_ex(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                                 int32_t T, const mf_plan_opts *opts, mf_prf_table **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    mf_prf_table *t = nullptr;
+    mf_status s = build_gauss_host(prf, vx, vy, K, T, &t);
+    if (s != MF_OK) return s;
+    if ((s = apply_opts(t, opts)) != MF_OK) return s;
     return create_common(t, out);
+}
+
+mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                              int32_t T, mf_prf_table **out) {
+    return mf_prf_table_create_ex(prf, vx, vy, K, T, nullptr, out);
+}
+
+mf_status mf_prf_plan(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K, int32_t T,
+                      const mf_plan_opts *opts, mf_table_info *info) {
+    if (!info) return fail(MF_EINVAL, "info is NULL");
+    mf_prf_table *t = nullptr;
+    mf_status s = build_gauss_host(prf, vx, vy, K, T, &t);
+    if (s != MF_OK) return s;
+    if ((s = apply_opts(t, opts)) != MF_OK) return s;
+    HostLayouts h;
+    s = host_layouts(t, h);
+    if (s == MF_OK) {
+        t->device_bytes = layout_bytes(t, h);
+        fill_info(t, info);
+    }
+    delete t;
+    return s == MF_OK ? ok() : s;
+}
+
+mf_status mf_prf_table_info(const mf_prf_table *table, mf_table_info *info) {
+    if (!table || !info) return fail(MF_EINVAL, "NULL argument");
+    fill_info(table, info);
+    return ok();
 }
 
 mf_status mf_prf_table_create_custom(const int32_t *shifts, const double *taps, int32_t K, int32_t T,
@@ -498,7 +664,7 @@ mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint
     if (master->H * master->W == 0) return fail(MF_EINVAL, "empty stack");
     if (!sigma || !snr_max || !argmax || !out || !n_out) return fail(MF_EINVAL, "NULL argument");
     if (k_top < 1 || (int64_t)k_top > master->H * master->W) return fail(MF_EINVAL, "k_top=%d out of range", k_top);
-    if (k_top > (1 << 16)) return fail(MF_EUNSUPPORTED, "k_top above 65536");
+    if (k_top > 16384) return fail(MF_EUNSUPPORTED, "k_top above 16384");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != table->device)
         return fail(MF_EINVAL, "table lives on device %d, current device is %d", table->device, dev);
@@ -511,6 +677,17 @@ mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint
     char err[256] = {0};
     const int rc = mf::launch_rescore(a, err, sizeof err);
     if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
+mf_status mf_profile_enable(int32_t on) {
+    mf::profile_enable(on);
+    return ok();
+}
+
+mf_status mf_profile_read(mf_profile *out, int32_t reset) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    mf::profile_read(out, reset);
     return ok();
 }
 

@@ -10,23 +10,31 @@
 
 namespace mf {
 
-// Output tile of the numerator kernel: 32 x 32 start pixels per trajectory.
-// Lane (tx, ty), tx in 0..3, ty in 0..7, owns rows 4*ty .. 4*ty+3 and columns
-// 8*tx + ty .. 8*tx + ty + 7 of the tile: the column skew ty keeps the 32
-// lanes on 32 distinct shared-memory banks when the window pitch is a
-// multiple of 32 words.
+// Numerator CTA: kWarps warps sharing one staged frame window.  A CTA covers
+// an output tile of (32 * tys) x (32 * txs) start pixels for kt trajectories;
+// each warp owns one (trajectory, 32 x 32 sub-tile) pair.  In a sub-tile,
+// lane (tx, ty), tx in 0..3, ty in 0..7, owns rows 4*ty .. 4*ty+3 and
+// columns 8*tx + ty .. 8*tx + ty + 7: the column skew ty keeps the 32 lanes on
+// 32 distinct shared-memory banks when the window pitch is a multiple of 32
+// words.  The skew is the same in every tile, so tiles cover the plane.
 constexpr int kTile = 32;
 constexpr int kMicroRows = 4;
 constexpr int kMicroCols = 8;
-constexpr int kSkew = 7;             // largest column skew of a lane
 constexpr int kTileOriginX = -8;     // first tile column (covers the skewed rows at x = 0)
-constexpr int kWarpsPerCta = 8;      // trajectories per CTA (one warp each)
+constexpr int kWarps = 16;           // warps per numerator CTA
 constexpr int kStages = 3;           // frame windows in flight per CTA
 constexpr int kLoadRows = 8;         // rows per TMA box
-constexpr int kRecFloats = 32;       // per-(trajectory, frame) record: 25 taps + offsets
 constexpr int kFrameBlock = 16;      // frames per FP32 partial sum in the numerator
-constexpr int kSegBlock = 4;         // segments per FP32 partial in the denominator
-constexpr int kSmemBudget = 110 * 1024;  // per CTA, so that two CTAs share an SM
+constexpr int kDenTaps = 256;        // denominator taps per FP32 partial before the FP64 add
+constexpr int kDenCols = 256;        // denominator: start pixels per warp (one row)
+constexpr int kSmemBudget = 220 * 1024;  // dynamic shared memory of one CTA per SM
+
+// CTA shapes: trajectories per CTA x sub-tiles across x sub-tiles down = kWarps.
+struct Shape {
+    int kt, txs, tys;
+};
+constexpr Shape kShapes[] = {{16, 1, 1}, {8, 2, 1}, {4, 2, 2}, {2, 4, 2}};
+constexpr int kNumShapes = 4;
 
 // Record of one trajectory slot for one frame, 128 bytes.
 struct alignas(16) SlotRec {
@@ -47,29 +55,38 @@ struct alignas(16) FrameHdr {
     int32_t pad;
 };
 
-// Block read by one TMA bulk copy per (group, frame): header of frame
-// t + kStages (the frame the issuing warp loads next into this slot) and the
-// kWarpsPerCta slot records of frame t.
-struct alignas(16) FrameBlock {
-    FrameHdr next;
-    SlotRec slot[kWarpsPerCta];
-};
+// Block read by one bulk copy per (group, frame): the header of frame
+// t + kStages (the frame the issuing warp loads next into this stage) followed
+// by kt slot records of frame t.
+inline size_t frame_block_bytes(int kt) { return sizeof(FrameHdr) + (size_t)kt * sizeof(SlotRec); }
 
-// One run of frames with a constant base shift (denominator kernel).
-struct alignas(16) SegRec {
-    float w2[25];     // sum over the run of W^2, FP64 sum rounded to FP32
-    int32_t sx, sy;
-    int32_t pad[5];
+// One row of the collapsed denominator kernel G_k: weights for columns
+// x0 .. x0 + 8 * nch - 1 (x0 a multiple of 4) of row offset dy.
+struct alignas(16) RunRec {
+    int32_t dy, x0, nch, woff;  // woff: index of the first weight (multiple of 4)
 };
-static_assert(sizeof(SegRec) == 128, "SegRec is 128 bytes");
 
 struct Plan {
+    int shape = 0;        // index into kShapes
+    int vec = 2;          // width of the numerator's shared-memory loads (1, 2 or 4 floats)
+    int lockstep = 0;     // numerator frame hand-off: 1 = CTA barrier per frame
     int G = 0;            // groups (CTAs per tile)
     int S = 0;            // window pitch in floats (multiple of 32, <= 256)
     int BH = 0;           // window rows (multiple of kLoadRows)
     int max_abs_shift = 0;
-    std::vector<int32_t> members;  // G * kWarpsPerCta original k, or -1
+    double cost = 0.0;    // planner estimate, cycles per output pixel
+    std::vector<int32_t> members;  // G * kt original k, or -1
+    int kt() const { return kShapes[shape].kt; }
+    int tile_h() const { return kTile * kShapes[shape].tys; }
+    int tile_w() const { return kTile * kShapes[shape].txs; }
 };
+
+// Dynamic shared memory of the numerator kernel: windows (the key tile of the
+// epilogue reuses them), frame blocks, barriers and counters, alignment slack.
+inline size_t numerator_smem_bytes(int S, int BH, int kt) {
+    return 1024 + (size_t)kStages * BH * S * sizeof(float) + (size_t)kStages * frame_block_bytes(kt) +
+           (size_t)kStages * sizeof(uint64_t) + 3 * kStages * sizeof(int) + sizeof(int) + 64;
+}
 
 }  // namespace mf
 
@@ -79,12 +96,18 @@ struct mf_prf_table {
     std::vector<int32_t> shifts;  // K*T*2, (s_x, s_y)
     std::vector<double> taps;     // K*T*25
     mf::Plan plan;
-    int n_seg = 0;
+    int forced_shape = -1;  // -1: cost model
+    int forced_vec = 0;     // 0: default
+    int forced_lockstep = -1;
+    int n_seg = 0;          // runs of the collapsed denominator kernels
+    int64_t g_nnz = 0;      // nonzero weights of the collapsed kernels
+    size_t device_bytes = 0;
     // device copies
-    mf::FrameBlock *d_blocks = nullptr;  // [G][T]
+    unsigned char *d_blocks = nullptr;   // [G][T] frame blocks of frame_block_bytes(kt)
     mf::FrameHdr *d_hdr = nullptr;       // [G][T]
-    mf::SegRec *d_segs = nullptr;        // [n_seg]
-    int32_t *d_seg_off = nullptr;        // [K + 1]
+    mf::RunRec *d_runs = nullptr;        // [n_seg]
+    int32_t *d_run_off = nullptr;        // [K + 1]
+    float *d_wts = nullptr;              // run weights
     double *d_taps64 = nullptr;          // [K][T][25]
     int32_t *d_shifts = nullptr;         // [K][T][2]
 };
@@ -136,5 +159,11 @@ size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top);
 int launch_rescore(const RescoreArgs &a, char *err, size_t errlen);
 
 int read_device_status(int *status);
+
+// Launch accounting (mf_profile_*).  Kernel ids index kKernelNames.
+enum KernelId { kKLambda = 0, kKWeight, kKDenominator, kKNumerator, kKFinalize, kKSelect, kKRescore,
+                kKCompact, kKSort, kKernelCount };
+int profile_enable(int on);
+int profile_read(mf_profile *out, int reset);
 
 }  // namespace mf

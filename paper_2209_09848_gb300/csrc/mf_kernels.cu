@@ -23,8 +23,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "mf_internal.h"
 
@@ -166,104 +168,132 @@ __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rst
 
 // -------------------------------------------------------- denominator ---
 
-// One warp per (32 x 32 tile, trajectory); lane (tx, ty) owns a 4 x 8 block.
-__global__ void __launch_bounds__(128) k_denominator(const float *__restrict__ lam, int64_t lw, int64_t pad,
-                                                     const SegRec *__restrict__ segs,
-                                                     const int32_t *__restrict__ seg_off, int64_t H, int64_t W,
-                                                     int tiles_x, int tiles, float *__restrict__ isd) {
+// D_k(p) = sum_u G_k(u) lambda(p + u) over the rows (runs) of the collapsed
+// kernel G_k.  A thread owns 8 consecutive start pixels of one row, a warp 256
+// of them, a CTA 8 rows; blockIdx.y walks the trajectories.  For each run the
+// thread slides an 8-wide register window along the lambda row (one aligned
+// float4 pair per 8 taps), so every loaded value feeds 8 FMAs.  Products and
+// partial sums are FP32 over at most kDenTaps taps; the partials are added in
+// FP64.  The result is stored as 1 / sqrt(D) (0 where D = 0).
+__global__ void __launch_bounds__(256) k_denominator(const float *__restrict__ lam, int64_t lw, int64_t pad,
+                                                     const RunRec *__restrict__ runs,
+                                                     const int32_t *__restrict__ run_off,
+                                                     const float *__restrict__ wts, int K, int64_t H, int64_t W,
+                                                     int nbx, float *__restrict__ isd) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * 4 + warp;
-    if (tile >= tiles) return;
-    const int k = blockIdx.y;
-    const int tx = lane & 3, ty = lane >> 2;
-    const int64_t y0 = (int64_t)(tile / tiles_x) * kTile + kMicroRows * ty;
-    const int64_t x0 = (int64_t)(tile % tiles_x) * kTile + kMicroCols * tx;
-    double d[kMicroRows][kMicroCols];
-    float blk[kMicroRows][kMicroCols];
+    const int64_t py = (int64_t)(blockIdx.x / nbx) * 8 + warp;
+    const int64_t px0 = (int64_t)(blockIdx.x % nbx) * kDenCols + 8 * lane;
+    const int64_t P = H * W;
+    for (int k = blockIdx.y; k < K; k += gridDim.y) {
+        double d[8];
+        float a[8];
 #pragma unroll
-    for (int r = 0; r < kMicroRows; r++)
-#pragma unroll
-        for (int c = 0; c < kMicroCols; c++) {
-            d[r][c] = 0.0;
-            blk[r][c] = 0.f;
+        for (int c = 0; c < 8; c++) {
+            d[c] = 0.0;
+            a[c] = 0.f;
         }
-    const int j0 = seg_off[k], j1 = seg_off[k + 1];
-    int cnt = 0;
-    for (int j = j0; j < j1; j++) {
-        const SegRec *sr = segs + j;
-        float w[28];
-        const float4 *w4 = reinterpret_cast<const float4 *>(sr->w2);
+        int taps = 0;
+        const int r0 = run_off[k], r1 = run_off[k + 1];
+        for (int r = r0; r < r1; r++) {
+            const RunRec rr = runs[r];
+            const float4 *row = reinterpret_cast<const float4 *>(lam + (py + rr.dy + pad) * lw + px0 + rr.x0 + pad);
+            const float4 *wp = reinterpret_cast<const float4 *>(wts + rr.woff);
+            float v[16];
+            {
+                const float4 p0 = __ldg(row), p1 = __ldg(row + 1);
+                v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+                v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+            }
+            for (int ch = 0; ch < rr.nch; ch++) {
+                const float4 p2 = __ldg(row + 2 * ch + 2), p3 = __ldg(row + 2 * ch + 3);
+                v[8] = p2.x; v[9] = p2.y; v[10] = p2.z; v[11] = p2.w;
+                v[12] = p3.x; v[13] = p3.y; v[14] = p3.z; v[15] = p3.w;
+                const float4 w0 = __ldg(wp + 2 * ch), w1 = __ldg(wp + 2 * ch + 1);
+                const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-        for (int i = 0; i < 7; i++) {
-            const float4 v = __ldg(w4 + i);
-            w[4 * i + 0] = v.x;
-            w[4 * i + 1] = v.y;
-            w[4 * i + 2] = v.z;
-            w[4 * i + 3] = v.w;
-        }
-        const int sx = __float_as_int(w[25]);
-        const int sy = __float_as_int(w[26]);
-        const float *base = lam + (y0 + sy - 2 + pad) * lw + (x0 + sx - 2 + pad);
+                for (int i = 0; i < 8; i++)
 #pragma unroll
-        for (int i = 0; i < kMicroRows + 4; i++) {
-            float v[kMicroCols + 4];
+                    for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[i + c], a[c]);
 #pragma unroll
-            for (int c = 0; c < kMicroCols + 4; c++) v[c] = __ldg(base + i * lw + c);
+                for (int c = 0; c < 8; c++) v[c] = v[c + 8];
+            }
+            taps += rr.nch * 8;
+            if (taps >= kDenTaps) {
 #pragma unroll
-            for (int r = 0; r < kMicroRows; r++) {
-                const int a = i - r;
-                if (a < 0 || a > 4) continue;
-#pragma unroll
-                for (int c = 0; c < kMicroCols; c++)
-#pragma unroll
-                    for (int b = 0; b < 5; b++) blk[r][c] = fmaf(w[a * 5 + b], v[c + b], blk[r][c]);
+                for (int c = 0; c < 8; c++) {
+                    d[c] += (double)a[c];
+                    a[c] = 0.f;
+                }
+                taps = 0;
             }
         }
-        if (++cnt == kSegBlock) {
-            cnt = 0;
+        if (py < H) {
 #pragma unroll
-            for (int r = 0; r < kMicroRows; r++)
-#pragma unroll
-                for (int c = 0; c < kMicroCols; c++) {
-                    d[r][c] += (double)blk[r][c];
-                    blk[r][c] = 0.f;
-                }
+            for (int c = 0; c < 8; c++) {
+                const double dd = d[c] + (double)a[c];
+                const int64_t px = px0 + c;
+                if (px < W) isd[(int64_t)k * P + py * W + px] = dd > 0.0 ? rsqrtf((float)dd) : 0.f;
+            }
         }
     }
-    const int64_t P = H * W;
-#pragma unroll
-    for (int r = 0; r < kMicroRows; r++)
-#pragma unroll
-        for (int c = 0; c < kMicroCols; c++) {
-            const double dd = d[r][c] + (double)blk[r][c];
-            const int64_t py = y0 + r, px = x0 + c;
-            if (py < H && px < W) isd[(int64_t)k * P + py * W + px] = dd > 0.0 ? rsqrtf((float)dd) : 0.f;
-        }
 }
 
 // ---------------------------------------------------------- numerator ---
 
 struct NumParams {
-    const FrameBlock *blocks;  // [G][T]
-    const FrameHdr *hdr;       // [G][T]
-    const float *isd;          // [K][H][W]
-    unsigned long long *keys;  // [H][W]
-    float *snr_all;            // [K][H][W] or null
+    const unsigned char *blocks;  // [G][T] frame blocks
+    const FrameHdr *hdr;          // [G][T]
+    const float *isd;             // [K][H][W]
+    unsigned long long *keys;     // [H][W]
+    float *snr_all;               // [K][H][W] or null
     int T, G;
     int64_t H, W;
     int tiles_x;
     int S, BH;
+    int lockstep;  // 1: CTA barrier after every frame; 0: the last warp out refills the stage
 };
 
+// Column skew of lane row-group ty for window loads of VEC floats: it keeps
+// the lanes of every shared-memory wavefront on distinct banks (pitch a
+// multiple of 32 words) and is a multiple of VEC, so a lane's row segment
+// starts VEC-aligned whenever the warp's window offset is.
+template <int VEC>
+__device__ __forceinline__ int lane_skew(int ty) {
+    return VEC == 1 ? ty : (VEC == 2 ? 2 * (ty & 3) : 4 * (ty & 1));
+}
+__host__ __device__ __forceinline__ int skew_of(int vec, int ty) {
+    return vec == 1 ? ty : (vec == 2 ? 2 * (ty & 3) : 4 * (ty & 1));
+}
+
 // The 4 x 8 block of one lane for one (trajectory, frame): 8 window rows of
-// 12 values each, 25 FMAs per output.
+// 12 values each, 25 FMAs per output.  `base` is the lane's first window value
+// minus M (so VEC-aligned); M = window offset mod VEC is a compile-time
+// constant of the variant, so the row segment is read with aligned VEC-wide
+// loads and the register selection costs nothing.
+template <int VEC, int M>
 __device__ __forceinline__ void stencil_4x8(const float *__restrict__ base, int S, const float (&w)[28],
                                             float (&blk)[kMicroRows][kMicroCols]) {
+    constexpr int NV = (kMicroCols + 4 + M + VEC - 1) / VEC;  // vector loads per row
 #pragma unroll
     for (int i = 0; i < kMicroRows + 4; i++) {
-        float v[kMicroCols + 4];
+        float f[NV * VEC];
+        const float *rp = base + i * S;
 #pragma unroll
-        for (int c = 0; c < kMicroCols + 4; c++) v[c] = base[i * S + c];
+        for (int q = 0; q < NV; q++) {
+            if (VEC == 4) {
+                const float4 x = reinterpret_cast<const float4 *>(rp)[q];
+                f[4 * q] = x.x;
+                f[4 * q + 1] = x.y;
+                f[4 * q + 2] = x.z;
+                f[4 * q + 3] = x.w;
+            } else if (VEC == 2) {
+                const float2 x = reinterpret_cast<const float2 *>(rp)[q];
+                f[2 * q] = x.x;
+                f[2 * q + 1] = x.y;
+            } else {
+                f[q] = rp[q];
+            }
+        }
 #pragma unroll
         for (int r = 0; r < kMicroRows; r++) {
             const int a = i - r;
@@ -271,32 +301,60 @@ __device__ __forceinline__ void stencil_4x8(const float *__restrict__ base, int 
 #pragma unroll
             for (int c = 0; c < kMicroCols; c++)
 #pragma unroll
-                for (int b = 0; b < 5; b++) blk[r][c] = fmaf(w[a * 5 + b], v[c + b], blk[r][c]);
+                for (int b = 0; b < 5; b++) blk[r][c] = fmaf(w[a * 5 + b], f[M + c + b], blk[r][c]);
         }
     }
 }
 
-template <int KG, int NS>
-__global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant__ CUtensorMap ymap,
-                                                          const NumParams p) {
-    extern __shared__ unsigned char smem_raw[];
-    const uintptr_t base_addr = ((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023;
-    float *win = reinterpret_cast<float *>(base_addr);
+template <int VEC>
+__device__ __forceinline__ void stencil_dispatch(const float *__restrict__ base, int m, int S, const float (&w)[28],
+                                                 float (&blk)[kMicroRows][kMicroCols]) {
+    if (VEC == 1) {
+        stencil_4x8<1, 0>(base, S, w, blk);
+    } else if (VEC == 2) {
+        if (m == 0) stencil_4x8<2, 0>(base, S, w, blk);
+        else stencil_4x8<2, 1>(base - 1, S, w, blk);
+    } else {
+        switch (m) {
+            case 0: stencil_4x8<4, 0>(base, S, w, blk); break;
+            case 1: stencil_4x8<4, 1>(base - 1, S, w, blk); break;
+            case 2: stencil_4x8<4, 2>(base - 2, S, w, blk); break;
+            default: stencil_4x8<4, 3>(base - 3, S, w, blk); break;
+        }
+    }
+}
+
+// One CTA: an output tile of (32 TYS) x (32 TXS) start pixels for KT
+// trajectories, kWarps warps, one (trajectory, sub-tile) pair per warp.
+template <int KT, int TXS, int TYS, int VEC>
+__global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_constant__ CUtensorMap ymap,
+                                                              const NumParams p) {
+    static_assert(KT * TXS * TYS == kWarps, "one warp per (trajectory, sub-tile)");
+    constexpr int NS = kStages;
+    constexpr int TH = kTile * TYS, TW = kTile * TXS;
+    constexpr uint32_t kBlockBytes = (uint32_t)(sizeof(FrameHdr) + KT * sizeof(SlotRec));
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // keep every pointer derived from smem_raw so that loads stay shared-memory loads
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int win_floats = p.BH * p.S;
-    FrameBlock *fb = reinterpret_cast<FrameBlock *>(win + NS * win_floats);
-    unsigned long long *red = reinterpret_cast<unsigned long long *>(fb + NS);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(red + kTile * kTile);
+    float *win = reinterpret_cast<float *>(smem);
+    unsigned char *fb = smem + (size_t)NS * win_floats * sizeof(float);  // NS frame blocks
+    uint64_t *bars = reinterpret_cast<uint64_t *>(fb + NS * kBlockBytes);
     int *cnt = reinterpret_cast<int *>(bars + NS);
     int *last_issued = cnt + NS;
     int *bad_flag = last_issued + NS;
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem);  // epilogue reuses the windows
 
     const int g = (int)(blockIdx.x % (unsigned)p.G);
     const int tile = (int)(blockIdx.x / (unsigned)p.G);
-    const int tile_y0 = (tile / p.tiles_x) * kTile;
-    const int tile_x0 = (tile % p.tiles_x) * kTile + kTileOriginX;
+    const int tile_y0 = (tile / p.tiles_x) * TH;
+    const int tile_x0 = (tile % p.tiles_x) * TW + kTileOriginX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = warp % KT, sub = warp / KT;
+    const int stx = sub % TXS, sty = sub / TXS;
     const int tx = lane & 3, ty = lane >> 2;
-    const FrameBlock *gblocks = p.blocks + (size_t)g * p.T;
+    const int skew = lane_skew<VEC>(ty);
+    const unsigned char *gblocks = p.blocks + (size_t)g * p.T * kBlockBytes;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s++) {
@@ -307,7 +365,6 @@ __global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant_
         *bad_flag = status_now();  // an earlier CTA gave up: do not start
         fence_barrier_init();
     }
-    for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) red[i] = 0ull;
     __syncthreads();
     if (*bad_flag != 0) return;  // same value for every thread of the CTA
 
@@ -317,16 +374,20 @@ __global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant_
         const uint32_t bar = smem_u32(&bars[s]);
         const int nl = h.nrows / kLoadRows;
         const uint32_t row_bytes = (uint32_t)kLoadRows * p.S * 4;
-        mbar_expect_tx(bar, nl * row_bytes + (uint32_t)sizeof(FrameBlock));
+        mbar_expect_tx(bar, nl * row_bytes + kBlockBytes);
         const uint32_t dst = smem_u32(win + (size_t)s * win_floats);
         for (int l = 0; l < nl; l++)
             tma_load_3d(dst + l * row_bytes, &ymap, tile_x0 + h.rox, tile_y0 + h.roy + l * kLoadRows, f, bar);
-        bulk_load(smem_u32(&fb[s]), gblocks + f, (uint32_t)sizeof(FrameBlock), bar);
+        bulk_load(smem_u32(fb + s * kBlockBytes), gblocks + (size_t)f * kBlockBytes, kBlockBytes, bar);
         last_issued[s] = f;
     };
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS && s < p.T; s++) issue(s, s, p.hdr[(size_t)g * p.T + s]);
     }
+
+    // A warp whose sub-tile lies entirely outside the image only keeps pace.
+    const int sub_y0 = tile_y0 + kTile * sty, sub_x0 = tile_x0 + kTile * stx;
+    const bool inside = sub_y0 < p.H && sub_x0 + kTile + 7 > 0 && sub_x0 < p.W;
 
     float acc[kMicroRows][kMicroCols], blk[kMicroRows][kMicroCols];
 #pragma unroll
@@ -340,15 +401,16 @@ __global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant_
     bool bad = false;
     for (int t = 0; t < p.T; t++) {
         const int s = t % NS;
-        if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((t / NS) & 1), 1)) {
+        const bool ready = mbar_wait(smem_u32(&bars[s]), (uint32_t)((t / NS) & 1), 1);
+        if (!ready && !p.lockstep) {
             bad = true;
             break;
         }
-        const SlotRec &rec = fb[s].slot[warp];
-        kk = rec.k;
-        if (kk >= 0) {
+        const SlotRec *rec = reinterpret_cast<const SlotRec *>(fb + s * kBlockBytes + sizeof(FrameHdr)) + slot;
+        kk = rec->k;
+        if (ready && kk >= 0 && inside) {
             float w[28];
-            const float4 *w4 = reinterpret_cast<const float4 *>(rec.taps);
+            const float4 *w4 = reinterpret_cast<const float4 *>(rec->taps);
 #pragma unroll
             for (int i = 0; i < 7; i++) {
                 const float4 v = w4[i];
@@ -359,9 +421,10 @@ __global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant_
             }
             const int offy = __float_as_int(w[25]);
             const int offx = __float_as_int(w[26]);
-            const float *base =
-                win + (size_t)s * win_floats + (offy + kMicroRows * ty) * p.S + offx + kMicroCols * tx + ty;
-            stencil_4x8(base, p.S, w, blk);
+            const float *base = win + (size_t)s * win_floats +
+                                (offy + kTile * sty + kMicroRows * ty) * p.S + offx + kTile * stx +
+                                kMicroCols * tx + skew;
+            stencil_dispatch<VEC>(base, offx & (VEC - 1), p.S, w, blk);
         }
         if ((t + 1) % kFrameBlock == 0) {
 #pragma unroll
@@ -372,15 +435,28 @@ __global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant_
                     blk[r][c] = 0.f;
                 }
         }
+        if (p.lockstep) {
+            // every warp is done with stage s: refill it with frame t + NS
+            if (__syncthreads_or(!ready)) {
+                bad = true;
+                break;
+            }
+            if (threadIdx.x == 0 && t + NS < p.T) {
+                const FrameHdr h = *reinterpret_cast<const FrameHdr *>(fb + s * kBlockBytes);
+                fence_proxy_async();
+                issue(t + NS, s, h);
+            }
+            continue;
+        }
         // Release stage s; the last warp to release it loads frame t + NS.
         __syncwarp();
         if (lane == 0) {
             __threadfence_block();
             const int prev = atomicAdd(&cnt[s], 1);
-            if (prev == KG - 1) {
+            if (prev == kWarps - 1) {
                 cnt[s] = 0;
                 if (t + NS < p.T) {
-                    const FrameHdr h = fb[s].next;
+                    const FrameHdr h = *reinterpret_cast<const FrameHdr *>(fb + s * kBlockBytes);
                     fence_proxy_async();
                     issue(t + NS, s, h);
                 }
@@ -400,30 +476,35 @@ __global__ void __launch_bounds__(KG * 32, 2) k_numerator(const __grid_constant_
         return;
     }
 
+    // Epilogue: every issued frame has been consumed, so the windows are free
+    // for the tile of packed (SNR, k) keys.
+    for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) red[i] = 0ull;
+    __syncthreads();
     const int64_t P = p.H * p.W;
 #pragma unroll
     for (int r = 0; r < kMicroRows; r++)
 #pragma unroll
         for (int c = 0; c < kMicroCols; c++) {
             const float n = acc[r][c] + blk[r][c];
-            const int64_t py = tile_y0 + kMicroRows * ty + r;
-            const int64_t px = tile_x0 + kMicroCols * tx + ty + c;
+            const int64_t py = sub_y0 + kMicroRows * ty + r;
+            const int64_t px = sub_x0 + kMicroCols * tx + skew + c;
             if (kk >= 0 && py < p.H && px >= 0 && px < p.W) {
                 const int64_t q = py * p.W + px;
                 const float isd = p.isd[(int64_t)kk * P + q];
                 const float snr = n * isd;
                 if (p.snr_all) p.snr_all[(int64_t)kk * P + q] = isd > 0.f ? snr : 0.f;
                 if (isd > 0.f)
-                    atomicMax(&red[(kMicroRows * ty + r) * kTile + kMicroCols * tx + c], pack_key(snr, kk));
+                    atomicMax(&red[(kTile * sty + kMicroRows * ty + r) * TW + kTile * stx + kMicroCols * tx + c],
+                              pack_key(snr, kk));
             }
         }
     __syncthreads();
-    for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) {
+    for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
         const unsigned long long key = red[i];
         if (key == 0ull) continue;
-        const int ly = i / kTile, lx = i % kTile;
+        const int ly = i / TW, lx = i % TW;
         const int64_t py = tile_y0 + ly;
-        const int64_t px = tile_x0 + lx + ly / kMicroRows;
+        const int64_t px = tile_x0 + lx + lane_skew<VEC>((ly / kMicroRows) % 8);
         atomicMax(&p.keys[py * p.W + px], key);
     }
 }
@@ -474,14 +555,6 @@ int grid_for(int64_t n, int threads) {
     return (int)b;
 }
 
-size_t numerator_smem(const Plan &pl) {
-    size_t s = 1024;  // alignment slack
-    s += (size_t)kStages * pl.BH * pl.S * sizeof(float);
-    s += (size_t)kStages * sizeof(FrameBlock);
-    s += (size_t)kTile * kTile * sizeof(unsigned long long);
-    s += (size_t)kStages * sizeof(uint64_t) + 3 * kStages * sizeof(int) + sizeof(int) + 64;
-    return s;
-}
 
 #define MF_CHECK_LAUNCH(what)                                                             \
     do {                                                                                  \
@@ -492,7 +565,76 @@ size_t numerator_smem(const Plan &pl) {
         }                                                                                 \
     } while (0)
 
+// ---------------------------------------------------------- profiling ---
+
+const char *kKernelNames[kKernelCount] = {"k_lambda",  "k_weight", "k_denominator", "k_numerator", "k_finalize",
+                                          "k_select", "k_rescore", "k_compact",     "k_sort"};
+
+struct ProfPending {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfPending> g_pending;
+double g_prof_ms[kKernelCount];
+long long g_prof_count[kKernelCount];
+
+// Bracket one launch: call with stage 0 before and stage 1 after it.
+struct LaunchScope {
+    int kid;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchScope(int k, cudaStream_t s) : kid(k), st(s) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_count[kid]++;
+        if (g_prof_on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, st);
+    }
+    ~LaunchScope() {
+        if (a && b) {
+            cudaEventRecord(b, st);
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_pending.push_back({kid, a, b});
+        }
+    }
+};
+
 }  // namespace
+
+int profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return 0;
+}
+
+int profile_read(mf_profile *out, int reset) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            g_prof_ms[p.kid] += ms;
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_pending.clear();
+    std::memset(out, 0, sizeof *out);
+    for (int i = 0; i < kKernelCount && i < 16; i++) {
+        std::snprintf(out->k[i].name, sizeof out->k[i].name, "%s", kKernelNames[i]);
+        out->k[i].launches = g_prof_count[i];
+        out->k[i].ms = g_prof_ms[i];
+        out->launches += g_prof_count[i];
+    }
+    out->n = kKernelCount;
+    if (reset) {
+        for (int i = 0; i < kKernelCount; i++) {
+            g_prof_ms[i] = 0.0;
+            g_prof_count[i] = 0;
+        }
+    }
+    return 0;
+}
 
 int launch_search(const SearchArgs &a, char *err, size_t errlen) {
     const mf_stack &st = *a.stack;
@@ -509,12 +651,17 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
     int rc = get_encode(err, errlen);
     if (rc) return rc;
 
-    k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(a.sigma, a.mask, H, W, L.pad, L.lam_w, L.lam_h,
-                                                                    lam);
+    {
+        LaunchScope ls(kKLambda, stream);
+        k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(a.sigma, a.mask, H, W, L.pad, L.lam_w,
+                                                                        L.lam_h, lam);
+    }
     MF_CHECK_LAUNCH("k_lambda");
 
     const int64_t nw = T * H * ((W + 3) / 4);
     const int64_t fs = st.frame_stride, rs = st.row_stride;
+    {
+    LaunchScope ls(kKWeight, stream);
     switch (st.dtype) {
         case MF_F32:
             k_weight<float><<<grid_for(nw, 256), 256, 0, stream>>>((const float *)st.data, fs, rs, st.frame_scale,
@@ -529,14 +676,16 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
                                                                     lam, L.pad, L.lam_w, y, T, H, W, L.y_pitch);
             break;
     }
+    }
     MF_CHECK_LAUNCH("k_weight");
 
     {
-        const int tiles_x = (int)((W + kTile - 1) / kTile);
-        const int tiles = tiles_x * (int)((H + kTile - 1) / kTile);
-        dim3 grid((tiles + 3) / 4, tab.K);
-        k_denominator<<<grid, 128, 0, stream>>>(lam, L.lam_w, L.pad, tab.d_segs, tab.d_seg_off, H, W, tiles_x,
-                                                tiles, isd);
+        const int nbx = (int)((W + kDenCols - 1) / kDenCols);
+        const int nby = (int)((H + 7) / 8);
+        dim3 grid((unsigned)(nbx * nby), (unsigned)std::min(tab.K, 65535));
+        LaunchScope ls(kKDenominator, stream);
+        k_denominator<<<grid, 256, 0, stream>>>(lam, L.lam_w, L.pad, tab.d_runs, tab.d_run_off, tab.d_wts, tab.K, H,
+                                                W, nbx, isd);
         MF_CHECK_LAUNCH("k_denominator");
     }
 
@@ -571,36 +720,351 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
         np.G = pl.G;
         np.H = H;
         np.W = W;
-        np.tiles_x = (int)((W - kTileOriginX + kTile - 1) / kTile);
-        const int tiles_y = (int)((H + kTile - 1) / kTile);
+        np.tiles_x = (int)((W - kTileOriginX + pl.tile_w() - 1) / pl.tile_w());
+        const int tiles_y = (int)((H + pl.tile_h() - 1) / pl.tile_h());
         np.S = pl.S;
         np.BH = pl.BH;
-        const size_t smem = numerator_smem(pl);
-        auto kern = k_numerator<kWarpsPerCta, kStages>;
+        np.lockstep = pl.lockstep;
+        const size_t smem = numerator_smem_bytes(pl.S, pl.BH, pl.kt());
+        void (*kern)(const CUtensorMap, const NumParams) = nullptr;
+#define MF_PICK(V)                                                  \
+    switch (pl.shape) {                                             \
+        case 0: kern = k_numerator<16, 1, 1, V>; break;             \
+        case 1: kern = k_numerator<8, 2, 1, V>; break;              \
+        case 2: kern = k_numerator<4, 2, 2, V>; break;              \
+        default: kern = k_numerator<2, 4, 2, V>; break;             \
+    }
+        if (pl.vec == 4) {
+            MF_PICK(4)
+        } else if (pl.vec == 2) {
+            MF_PICK(2)
+        } else {
+            MF_PICK(1)
+        }
+#undef MF_PICK
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
             snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
             return (int)e;
         }
         const long long nblocks = (long long)pl.G * np.tiles_x * tiles_y;
-        kern<<<(unsigned)nblocks, kWarpsPerCta * 32, smem, stream>>>(map, np);
+        LaunchScope ls(kKNumerator, stream);
+        kern<<<(unsigned)nblocks, kWarps * 32, smem, stream>>>(map, np);
         MF_CHECK_LAUNCH("k_numerator");
     }
-    k_finalize<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, a.snr_max, a.argmax);
+    {
+        LaunchScope ls(kKFinalize, stream);
+        k_finalize<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, a.snr_max, a.argmax);
+    }
     MF_CHECK_LAUNCH("k_finalize");
     return 0;
 }
 
-size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top) {
-    (void)H;
-    (void)W;
-    return (size_t)k_top * 64 + 256;
+// ------------------------------------------------------------ rescore ---
+//
+// Candidate list (Section 3.3: scores above a threshold are candidates) and
+// FP64 re-score.  Candidates are ranked by a unique 64-bit key, (order-
+// preserving SNR bits << 32) | (0xFFFFFFFF - flat index): descending key =
+// SNR descending, then flat index ascending.  A 4-pass radix select over 16
+// bits at a time finds the k_top-th largest key, a compaction keeps the keys
+// at or above it, one CTA sorts them, and one warp per candidate recomputes
+// N and D in FP64 from the master stack.
+
+namespace {
+
+struct SelState {
+    unsigned long long prefix;  // selected high bits so far
+    unsigned long long thresh;  // final k_top-th largest key (0: take every valid key)
+    unsigned int need;          // keys still to take at and below the current prefix
+    unsigned int total;         // valid keys
+    unsigned int count;         // compacted keys
+    unsigned int pad;
+};
+
+__global__ void k_sel_keys(const float *__restrict__ snr_max, const int32_t *__restrict__ argmax, int64_t P,
+                           unsigned long long *__restrict__ keys, unsigned int *__restrict__ hist,
+                           SelState *st) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = 0ull;
+        if (argmax[i] >= 0) {
+            uint32_t b = __float_as_uint(snr_max[i]);
+            b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+            key = ((unsigned long long)b << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
+            atomicAdd(&hist[key >> 48], 1u);
+            atomicAdd(&st->total, 1u);
+        }
+        keys[i] = key;
+    }
 }
 
+// Histogram of the next 16 bits among keys that match the selected prefix.
+__global__ void k_sel_hist(const unsigned long long *__restrict__ keys, int64_t P, int pass,
+                           unsigned int *__restrict__ hist, const SelState *st) {
+    const int hi_shift = 64 - 16 * pass;  // bits above this are fixed
+    const unsigned long long prefix = st->prefix;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[i];
+        if (key != 0ull && (key >> hi_shift) == (prefix >> hi_shift))
+            atomicAdd(&hist[(key >> (hi_shift - 16)) & 0xFFFFull], 1u);
+    }
+}
+
+// One CTA: walk the 65536 bins from the top, find the bin holding the
+// `need`-th largest key, extend the prefix, and clear the histogram.
+__global__ void __launch_bounds__(1024) k_sel_pick(unsigned int *__restrict__ hist, int pass, SelState *st,
+                                                   unsigned int k_top) {
+    __shared__ unsigned int part[1024];
+    __shared__ unsigned int chosen_bin, above;
+    const int tid = threadIdx.x;
+    if (pass == 0) {
+        if (tid == 0) {
+            st->need = st->total < k_top ? st->total : k_top;
+            st->prefix = 0ull;
+        }
+        __syncthreads();
+    }
+    const unsigned int need = st->need;
+    // each thread sums 64 consecutive bins; thread 0 holds the highest bins
+    unsigned int sum = 0;
+    for (int j = 0; j < 64; j++) sum += hist[65535 - (tid * 64 + j)];
+    part[tid] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned int acc = 0;
+        int blk = 0;
+        for (; blk < 1024; blk++) {
+            if (acc + part[blk] >= need) break;
+            acc += part[blk];
+        }
+        unsigned int bin = 0;
+        if (blk < 1024) {
+            for (int j = 0; j < 64; j++) {
+                const unsigned int b = 65535 - (blk * 64 + j);
+                if (acc + hist[b] >= need) {
+                    bin = b;
+                    break;
+                }
+                acc += hist[b];
+            }
+        }
+        chosen_bin = bin;
+        above = acc;
+    }
+    __syncthreads();
+    for (int j = tid; j < 65536; j += blockDim.x) hist[j] = 0u;
+    if (tid == 0) {
+        const int shift = 48 - 16 * pass;
+        st->prefix |= (unsigned long long)chosen_bin << shift;
+        st->need = need - above;
+        if (pass == 3) st->thresh = need == 0 ? ~0ull : st->prefix;
+    }
+}
+
+__global__ void k_sel_compact(const unsigned long long *__restrict__ keys, int64_t P,
+                              unsigned long long *__restrict__ out, SelState *st, unsigned int cap) {
+    const unsigned long long th = st->thresh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[i];
+        if (key != 0ull && key >= th) {
+            const unsigned int slot = atomicAdd(&st->count, 1u);
+            if (slot < cap) out[slot] = key;
+        }
+    }
+}
+
+// One CTA bitonic sort (descending) of up to kMaxTop keys in shared memory.
+constexpr int kMaxTop = 16384;
+__global__ void __launch_bounds__(1024) k_sel_sort(unsigned long long *__restrict__ keys, const SelState *st,
+                                                   unsigned int cap) {
+    extern __shared__ unsigned long long sk[];
+    unsigned int n = st->count < cap ? st->count : cap;
+    unsigned int m = 1;
+    while (m < n) m <<= 1;
+    for (unsigned int i = threadIdx.x; i < m; i += blockDim.x) sk[i] = i < n ? keys[i] : 0ull;
+    __syncthreads();
+    for (unsigned int size = 2; size <= m; size <<= 1) {
+        for (unsigned int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (unsigned int i = threadIdx.x; i < m; i += blockDim.x) {
+                const unsigned int j = i ^ stride;
+                if (j > i) {
+                    const bool desc = (i & size) == 0;
+                    const unsigned long long a = sk[i], b = sk[j];
+                    if (desc ? (a < b) : (a > b)) {
+                        sk[i] = b;
+                        sk[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (unsigned int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = sk[i];
+}
+
+template <typename TIn>
+__device__ __forceinline__ double to_f64(TIn v) { return (double)to_f32(v); }
+
+// One warp per candidate: N and D in FP64 from the master stack, the FP64
+// footprints and the FP64 inverse variance.
+template <typename TIn>
+__global__ void k_rescore(const TIn *__restrict__ r, int64_t fstride, int64_t rstride,
+                          const float *__restrict__ scale, const float *__restrict__ sigma,
+                          const uint8_t *__restrict__ mask, const double *__restrict__ taps64,
+                          const int32_t *__restrict__ shifts, const float *__restrict__ snr_max,
+                          const int32_t *__restrict__ argmax, const unsigned long long *__restrict__ keys,
+                          const SelState *st, unsigned int cap, int T, int64_t H, int64_t W,
+                          mf_candidate *__restrict__ out, int32_t *__restrict__ n_out) {
+    const unsigned int n = st->count < cap ? st->count : cap;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp == 0 && lane == 0) *n_out = (int32_t)n;
+    if ((unsigned)warp >= n) return;
+    const unsigned long long key = keys[warp];
+    const int64_t idx = (int64_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+    const int64_t py = idx / W, px = idx % W;
+    const int k = argmax[idx];
+    double num = 0.0, den = 0.0;
+    for (int t = lane; t < T; t += 32) {
+        const size_t kt = (size_t)k * T + t;
+        const int sx = shifts[kt * 2 + 0], sy = shifts[kt * 2 + 1];
+        const double sc = scale ? (double)scale[t] : 1.0;
+        const double *w = taps64 + kt * 25;
+        for (int b = 0; b < 5; b++) {
+            const int64_t qy = py + sy + b - 2;
+            if (qy < 0 || qy >= H) continue;
+            for (int a = 0; a < 5; a++) {
+                const int64_t qx = px + sx + a - 2;
+                if (qx < 0 || qx >= W) continue;
+                const int64_t q = qy * W + qx;
+                const double s = (double)sigma[q];
+                if ((mask && mask[q]) || !(s > 0.0) || !isfinite(s)) continue;
+                const double lam = 1.0 / (s * s);
+                const double wt = w[b * 5 + a];
+                num += wt * lam * (sc * to_f64(r[t * fstride + qy * rstride + qx]));
+                den += wt * wt * lam;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        mf_candidate c;
+        c.y = (int32_t)py;
+        c.x = (int32_t)px;
+        c.k = k;
+        c.reserved = 0;
+        c.snr = den > 0.0 ? num / sqrt(den) : 0.0;
+        c.flux = den > 0.0 ? num / den : 0.0;
+        c.snr_search = snr_max[idx];
+        c.reserved2 = 0.f;
+        out[warp] = c;
+    }
+}
+
+struct RescoreLayout {
+    size_t keys_off, hist_off, st_off, top_off, total;
+};
+
+RescoreLayout rescore_layout(int64_t H, int64_t W, int32_t k_top) {
+    RescoreLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return o;
+    };
+    L.keys_off = take((size_t)H * W * sizeof(unsigned long long));
+    L.hist_off = take(65536 * sizeof(unsigned int));
+    L.st_off = take(sizeof(SelState));
+    L.top_off = take((size_t)k_top * sizeof(unsigned long long));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top) { return rescore_layout(H, W, k_top).total; }
+
 int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
-    (void)a;
-    snprintf(err, errlen, "mf_rescore_topk is not built yet");
-    return (int)cudaErrorNotSupported;
+    const mf_stack &st = *a.stack;
+    const mf_prf_table &tab = *a.tab;
+    cudaStream_t stream = (cudaStream_t)a.stream;
+    const int64_t H = st.H, W = st.W, P = H * W;
+    if (a.k_top > kMaxTop) {
+        snprintf(err, errlen, "k_top above %d", kMaxTop);
+        return (int)cudaErrorInvalidValue;
+    }
+    const RescoreLayout L = rescore_layout(H, W, a.k_top);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
+    unsigned int *hist = reinterpret_cast<unsigned int *>(a.ws + L.hist_off);
+    SelState *sst = reinterpret_cast<SelState *>(a.ws + L.st_off);
+    unsigned long long *top = reinterpret_cast<unsigned long long *>(a.ws + L.top_off);
+    cudaError_t e = cudaMemsetAsync(a.ws + L.hist_off, 0, L.top_off - L.hist_off, stream);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    {
+        LaunchScope ls(kKSelect, stream);
+        k_sel_keys<<<grid_for(P, 256), 256, 0, stream>>>(a.snr_max, a.argmax, P, keys, hist, sst);
+    }
+    MF_CHECK_LAUNCH("k_sel_keys");
+    for (int pass = 0; pass < 4; pass++) {
+        if (pass > 0) {
+            LaunchScope ls(kKSelect, stream);
+            k_sel_hist<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, pass, hist, sst);
+            MF_CHECK_LAUNCH("k_sel_hist");
+        }
+        LaunchScope ls(kKSelect, stream);
+        k_sel_pick<<<1, 1024, 0, stream>>>(hist, pass, sst, (unsigned)a.k_top);
+        MF_CHECK_LAUNCH("k_sel_pick");
+    }
+    {
+        LaunchScope ls(kKCompact, stream);
+        k_sel_compact<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, top, sst, (unsigned)a.k_top);
+    }
+    MF_CHECK_LAUNCH("k_sel_compact");
+    {
+        unsigned int m = 1;
+        while (m < (unsigned)a.k_top) m <<= 1;
+        const size_t smem = (size_t)m * sizeof(unsigned long long);
+        e = cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            snprintf(err, errlen, "cudaFuncSetAttribute(sort): %s", cudaGetErrorString(e));
+            return (int)e;
+        }
+        LaunchScope ls(kKSort, stream);
+        k_sel_sort<<<1, 1024, smem, stream>>>(top, sst, (unsigned)a.k_top);
+    }
+    MF_CHECK_LAUNCH("k_sel_sort");
+    {
+        const int threads = 256;
+        const int blocks = (int)(((int64_t)a.k_top * 32 + threads - 1) / threads);
+        LaunchScope ls(kKRescore, stream);
+        const int64_t fs = st.frame_stride, rs = st.row_stride;
+        switch (st.dtype) {
+            case MF_F32:
+                k_rescore<float><<<blocks, threads, 0, stream>>>(
+                    (const float *)st.data, fs, rs, st.frame_scale, a.sigma, a.mask, tab.d_taps64, tab.d_shifts,
+                    a.snr_max, a.argmax, top, sst, (unsigned)a.k_top, tab.T, H, W, a.out, a.n_out);
+                break;
+            case MF_BF16:
+                k_rescore<__nv_bfloat16><<<blocks, threads, 0, stream>>>(
+                    (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, a.sigma, a.mask, tab.d_taps64,
+                    tab.d_shifts, a.snr_max, a.argmax, top, sst, (unsigned)a.k_top, tab.T, H, W, a.out, a.n_out);
+                break;
+            default:
+                k_rescore<__half><<<blocks, threads, 0, stream>>>(
+                    (const __half *)st.data, fs, rs, st.frame_scale, a.sigma, a.mask, tab.d_taps64, tab.d_shifts,
+                    a.snr_max, a.argmax, top, sst, (unsigned)a.k_top, tab.T, H, W, a.out, a.n_out);
+                break;
+        }
+    }
+    MF_CHECK_LAUNCH("k_rescore");
+    return 0;
 }
 
 int read_device_status(int *status) {

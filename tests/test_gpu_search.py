@@ -158,3 +158,26 @@ def test_deterministic_reruns(mf):
     b = _run(mf, c["res"], c["sigma"], c["mask"], table)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("lockstep", [0, 1])
+@pytest.mark.parametrize("vec", [1, 2, 4])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+def test_every_cta_shape(mf, oracle, shape, vec, lockstep):
+    """Each numerator CTA layout (trajectories x sub-tiles) and shared-memory
+    load width gives the oracle's answer, on a ragged frame that spans several
+    tiles of every layout (odd velocities exercise every window alignment)."""
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 24, 150, 141
+    c = synth.small_case(T, H, W, 40 + shape, mask_frac=0.02, movers=3)
+    vx, vy = synth.velocity_grid(5, 4, -0.25, 0.25)
+    vx = vx + 0.013 * np.arange(vx.size) / vx.size
+    table = mf.prf_table_create(vx, vy, T, shape=shape, vec=vec, lockstep=lockstep)
+    info = table.info()
+    assert info["warps_per_group"] == [16, 8, 4, 2][shape] and info["vec"] == vec
+    assert info["lockstep"] == lockstep
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    check_search(smax, amax, sall, N, D, oracle, label="shape %d" % shape)
