@@ -217,6 +217,25 @@ mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *ma
                     float *snr_all, void *workspace, size_t workspace_bytes,
                     mf_stream stream);
 
+/* mf_search for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this exists for callers such as plug-ins whose host
+ * application owns every device allocation, or real-time loops that may not
+ * call cudaMalloc (it can synchronise the device and stall other streams).
+ * Arguments, outputs, arithmetic and errors are those of mf_search minus the
+ * workspace: the scratch is a static device array of 64 MiB inside libmf,
+ * which every GPU that loads the library holds until the process exits.
+ * A search needing more scratch than that (mf_search_workspace_size) is
+ * rejected with MF_EINVAL and nothing is enqueued.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the previous call's contents (the
+ * search clears what it needs cleared), so calls whose work overlaps on the
+ * GPU (different streams, no ordering between them) race on it: serialise
+ * them.  This entry point itself allocates nothing. */
+mf_status mf_search_noalloc(const mf_stack *stack, const float *sigma, const uint8_t *mask,
+                            const mf_prf_table *table, float *snr_max, int32_t *argmax,
+                            float *snr_all, mf_stream stream);
+
 /* Bytes of workspace mf_rescore_topk needs. */
 mf_status mf_rescore_workspace_size(int64_t H, int64_t W, int32_t k_top, size_t *bytes);
 

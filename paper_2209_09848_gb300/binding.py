@@ -111,6 +111,7 @@ def load():
                              ctypes.POINTER(TableInfo)], ctypes.c_int),
             "mf_search_workspace_size": ([ctypes.POINTER(Stack), P, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_search": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P, SZ, P], ctypes.c_int),
+            "mf_search_noalloc": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P], ctypes.c_int),
             "mf_rescore_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
             "mf_profile_enable": ([I32], ctypes.c_int),
@@ -289,6 +290,23 @@ def search(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torc
     _check(load().mf_search(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
                             _ptr(argmax), _ptr(snr_all), _ptr(ws), ws.numel() * ws.element_size(),
                             _stream_ptr(stream)))
+    return snr_max, argmax, snr_all
+
+
+def search_noalloc(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torch.Tensor | None = None,
+                   frame_scale: torch.Tensor | None = None, want_all: bool = False, out=None, stream=None):
+    """mf_search_noalloc: mf_search with the library's static scratch (no workspace argument)."""
+    st = make_stack(stack, frame_scale)
+    T, H, W = stack.shape
+    dev = stack.device
+    if out is None:
+        snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
+        argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
+        snr_all = torch.empty((table.K, H, W), dtype=torch.float32, device=dev) if want_all else None
+    else:
+        snr_max, argmax, snr_all = out
+    _check(load().mf_search_noalloc(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
+                                    _ptr(argmax), _ptr(snr_all), _stream_ptr(stream)))
     return snr_max, argmax, snr_all
 
 

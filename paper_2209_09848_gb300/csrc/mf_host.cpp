@@ -453,6 +453,8 @@ mf_status check_stack(const mf_stack *st) {
 
 namespace mf {
 
+mf_status set_error(mf_status s, const char *msg) { return fail(s, "%s", msg); }
+
 WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab) {
     WorkspaceLayout L;
     // zero border wide enough for every denominator read: shifts up to

@@ -160,6 +160,9 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen);
 
 int read_device_status(int *status);
 
+// Record an error message for mf_last_error() and return the status.
+mf_status set_error(mf_status s, const char *msg);
+
 // Launch accounting (mf_profile_*).  Kernel ids index kKernelNames.
 enum KernelId { kKLambda = 0, kKWeight, kKDenominator, kKNumerator, kKFinalize, kKSelect, kKRescore,
                 kKCompact, kKSort, kKernelCount };
