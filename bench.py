@@ -244,7 +244,7 @@ def run_ours(args):
 
     T, H, W = args.frames, args.size, args.size
     case = synth.paper_case_gpu(T=T, H=H, W=W, seed=1 + rank, device=dev)
-    vx, vy = synth.velocity_grid(NXG, NYG, -VMAX, VMAX)
+    vx, vy = synth.velocity_grid(NXG, NYG, -args.vmax, args.vmax)
     K = len(vx)
     table = mf.prf_table_create(vx, vy, T)
     info = table.info()
@@ -360,7 +360,7 @@ def run_ours(args):
             "config": {"workload": "paper-shaped search: %d frames x %dx%d px float32, %d trajectories "
                                    "(%dx%d grid, |v|<=%.2f px/frame), sigma log-normal, 1%% star mask, "
                                    "200 movers; search + top-%d FP64 rescore per step" % (
-                                       T, H, W, K, NXG, NYG, VMAX, K_TOP),
+                                       T, H, W, K, NXG, NYG, args.vmax, K_TOP),
                        "frames": T, "height": H, "width": W, "trajectories": K,
                        "l2": "inputs larger than L2 (%.1f GB stack per step)" % (T * H * W * 4 / 1e9),
                        "plan": {k: info[k] for k in ("groups", "warps_per_group", "tile_h", "tile_w",
@@ -393,6 +393,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=T_FR)
     ap.add_argument("--size", type=int, default=HH)
+    ap.add_argument("--vmax", type=float, default=VMAX, help="velocity grid half-range, px/frame")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rescore", action="store_true")

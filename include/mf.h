@@ -278,6 +278,36 @@ mf_status mf_profile_enable(int32_t on);
  * them afterwards. */
 mf_status mf_profile_read(mf_profile *out, int32_t reset);
 
+/* Batched searches (not in the paper).  Many searches -- uneven cutouts,
+ * each with its own stack, noise map, mask, filter bank and outputs -- run as
+ * one CUDA graph: preparation kernels spread over side streams, one
+ * persistent numerator launch per CTA shape present in the batch (one CTA
+ * per SM taking (search, tile, trajectory group) work from a global
+ * counter), then per-search finalisation.  Each search's results equal those
+ * of mf_search on the same inputs (same per-tile code and summation order).
+ *
+ * Usage: mf_batch_create; mf_batch_add per search (pointers are the caller's
+ * and must stay valid while the batch is used); mf_batch_workspace_size;
+ * mf_batch_prepare with a workspace of that size (builds the device
+ * descriptors and a private stream: the only allocations besides the
+ * handle); mf_batch_run on any stream (the first run captures the graph on
+ * the batch's private stream, every run launches it on the given stream:
+ * change inputs in place, not their addresses); mf_batch_destroy.
+ * Errors as mf_search, plus MF_EINVAL for running an unprepared batch or
+ * adding to a prepared one. */
+typedef struct mf_batch mf_batch;
+mf_status mf_batch_create(mf_batch **out);
+mf_status mf_batch_add(mf_batch *batch, const mf_stack *stack, const float *sigma, const uint8_t *mask,
+                       const mf_prf_table *table, float *snr_max, int32_t *argmax, float *snr_all,
+                       int32_t *index);
+mf_status mf_batch_workspace_size(const mf_batch *batch, size_t *bytes);
+mf_status mf_batch_prepare(mf_batch *batch, void *workspace, size_t workspace_bytes);
+mf_status mf_batch_run(mf_batch *batch, mf_stream stream);
+/* Number of searches, of distinct CTA shapes (persistent launches) and
+ * whether the graph has been captured. */
+mf_status mf_batch_info(const mf_batch *batch, int32_t *items, int32_t *shape_groups, int32_t *graph_ready);
+void mf_batch_destroy(mf_batch *batch);
+
 /* Text of the last error on this host thread ("" if none). */
 const char *mf_last_error(void);
 

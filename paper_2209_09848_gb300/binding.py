@@ -116,6 +116,13 @@ def load():
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
             "mf_profile_enable": ([I32], ctypes.c_int),
             "mf_profile_read": ([ctypes.POINTER(Profile), I32], ctypes.c_int),
+            "mf_batch_create": ([pp], ctypes.c_int),
+            "mf_batch_add": ([P, ctypes.POINTER(Stack), P, P, P, P, P, P, ctypes.POINTER(I32)], ctypes.c_int),
+            "mf_batch_workspace_size": ([P, ctypes.POINTER(SZ)], ctypes.c_int),
+            "mf_batch_prepare": ([P, P, SZ], ctypes.c_int),
+            "mf_batch_run": ([P, P], ctypes.c_int),
+            "mf_batch_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
+            "mf_batch_destroy": ([P], None),
             "mf_last_error": ([], ctypes.c_char_p),
             "mf_device_status": ([], ctypes.c_int),
             "mf_version": ([], ctypes.c_char_p),
@@ -353,6 +360,62 @@ def profile_read(reset: bool = True) -> dict:
     out = {p.k[i].name.decode(): (int(p.k[i].launches), float(p.k[i].ms)) for i in range(p.n)}
     out["_launches"] = int(p.launches)
     return out
+
+
+class Batch:
+    """mf_batch: many searches captured into one CUDA graph with a persistent
+    numerator launch.  Keeps every tensor it was given alive."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(load().mf_batch_create(ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+        self.outputs = []
+        self._ws = None
+
+    def add(self, stack, sigma, table, mask=None, frame_scale=None, want_all=False):
+        st = make_stack(stack, frame_scale)
+        T, H, W = stack.shape
+        dev = stack.device
+        snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
+        argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
+        snr_all = torch.empty((table.K, H, W), dtype=torch.float32, device=dev) if want_all else None
+        idx = ctypes.c_int32()
+        _check(load().mf_batch_add(self._h, ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle,
+                                   _ptr(snr_max), _ptr(argmax), _ptr(snr_all), ctypes.byref(idx)))
+        self._keep += [stack, sigma, mask, frame_scale, table]
+        self.outputs.append((snr_max, argmax, snr_all))
+        return idx.value
+
+    def workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load().mf_batch_workspace_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def prepare(self, workspace=None, device="cuda"):
+        n = self.workspace_size()
+        self._ws = workspace if workspace is not None else torch.empty(max(n, 1), dtype=torch.uint8, device=device)
+        _check(load().mf_batch_prepare(self._h, _ptr(self._ws), self._ws.numel() * self._ws.element_size()))
+
+    def run(self, stream=None):
+        _check(load().mf_batch_run(self._h, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().mf_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"items": a.value, "shape_groups": b.value, "graph_ready": bool(c.value)}
+
+    def destroy(self):
+        if self._h:
+            load().mf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def device_status() -> int:

@@ -44,28 +44,31 @@ int64_t floor_div(int64_t a, int64_t b) {
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// Pixel-integrated 1-D Gaussian (PRF kind 0) over pixel [a - 1/2, a + 1/2].
-double pixel_gauss(int a, double phase, double sigma) {
-    const double s = sigma * std::sqrt(2.0);
-    return 0.5 * (std::erf((a + 0.5 - phase) / s) - std::erf((a - 0.5 - phase) / s));
-}
-
 // 5x5 footprint of the PRF for a source at sub-pixel offset (phx, phy) from
 // the base pixel, renormalised to unit sum (Section 2: the PRF shares a point
 // source's flux between neighbouring pixels).
 void footprint(int kind, double sigma, double phx, double phy, double *w) {
     double gx[5], gy[5];
-    double total = 0.0;
-    for (int i = 0; i < 5; i++) {
-        const int d = i - 2;
-        if (kind == 0) {
-            gx[i] = pixel_gauss(d, phx, sigma);
-            gy[i] = pixel_gauss(d, phy, sigma);
-        } else {
+    if (kind == 0) {
+        // pixel d spans [d - 1/2, d + 1/2]: six shared boundaries per axis
+        const double s = sigma * std::sqrt(2.0);
+        double ex[6], ey[6];
+        for (int i = 0; i < 6; i++) {
+            ex[i] = std::erf((i - 2.5 - phx) / s);
+            ey[i] = std::erf((i - 2.5 - phy) / s);
+        }
+        for (int i = 0; i < 5; i++) {
+            gx[i] = 0.5 * (ex[i + 1] - ex[i]);
+            gy[i] = 0.5 * (ey[i + 1] - ey[i]);
+        }
+    } else {
+        for (int i = 0; i < 5; i++) {
+            const int d = i - 2;
             gx[i] = std::exp(-(d - phx) * (d - phx) / (2.0 * sigma * sigma));
             gy[i] = std::exp(-(d - phy) * (d - phy) / (2.0 * sigma * sigma));
         }
     }
+    double total = 0.0;
     for (int b = 0; b < 5; b++)
         for (int a = 0; a < 5; a++) {
             w[b * 5 + a] = gy[b] * gx[a];
@@ -312,25 +315,62 @@ mf_status host_layouts(mf_prf_table *t, HostLayouts &out) {
     std::vector<int32_t> run_off(K + 1, 0);
     std::vector<float> wts;
     int64_t nnz_total = 0;
+    std::vector<double> dense;
     for (int k = 0; k < K; k++) {
         run_off[k] = (int32_t)runs.size();
-        std::map<std::pair<int32_t, int32_t>, double> g;  // (row, column) -> weight
+        // bounding box of G_k's support
+        int32_t x_lo = INT32_MAX, x_hi = INT32_MIN, y_lo = INT32_MAX, y_hi = INT32_MIN;
+        for (int f = 0; f < T; f++) {
+            const size_t kt_ = (size_t)k * T + f;
+            x_lo = std::min(x_lo, t->shifts[kt_ * 2 + 0] - 2);
+            x_hi = std::max(x_hi, t->shifts[kt_ * 2 + 0] + 2);
+            y_lo = std::min(y_lo, t->shifts[kt_ * 2 + 1] - 2);
+            y_hi = std::max(y_hi, t->shifts[kt_ * 2 + 1] + 2);
+        }
+        const int64_t bw = (int64_t)x_hi - x_lo + 1, bh = (int64_t)y_hi - y_lo + 1;
+        std::map<std::pair<int32_t, int32_t>, double> sparse;  // (row, column) -> weight
+        const bool use_dense = bw * bh <= (int64_t)100 * T + 4096;
+        if (use_dense) dense.assign((size_t)(bw * bh), 0.0);
         for (int f = 0; f < T; f++) {
             const size_t kt_ = (size_t)k * T + f;
             const int32_t sx = t->shifts[kt_ * 2 + 0], sy = t->shifts[kt_ * 2 + 1];
             for (int b = 0; b < 5; b++)
                 for (int a = 0; a < 5; a++) {
                     const double w = t->taps[kt_ * 25 + b * 5 + a];
-                    g[{sy + b - 2, sx + a - 2}] += w * w;
+                    if (use_dense)
+                        dense[(size_t)((sy + b - 2 - y_lo) * bw + (sx + a - 2 - x_lo))] += w * w;
+                    else
+                        sparse[{sy + b - 2, sx + a - 2}] += w * w;
                 }
         }
-        nnz_total += (int64_t)g.size();
-        auto it = g.begin();
-        while (it != g.end()) {
+        if (use_dense) {
+            // rows of the box: the support is where some frame's footprint landed
+            std::vector<char> hit((size_t)(bw * bh), 0);
+            for (int f = 0; f < T; f++) {
+                const size_t kt_ = (size_t)k * T + f;
+                const int32_t sx = t->shifts[kt_ * 2 + 0], sy = t->shifts[kt_ * 2 + 1];
+                for (int b = 0; b < 5; b++)
+                    for (int a = 0; a < 5; a++) hit[(size_t)((sy + b - 2 - y_lo) * bw + (sx + a - 2 - x_lo))] = 1;
+            }
+            for (int64_t r = 0; r < bh; r++) {
+                int64_t c0 = -1, c1 = -1;
+                for (int64_t c = 0; c < bw; c++)
+                    if (hit[(size_t)(r * bw + c)]) {
+                        if (c0 < 0) c0 = c;
+                        c1 = c;
+                    }
+                if (c0 < 0) continue;
+                for (int64_t c = c0; c <= c1; c++) sparse[{(int32_t)(r + y_lo), (int32_t)(c + x_lo)}] +=
+                                                        dense[(size_t)(r * bw + c)];
+            }
+        }
+        nnz_total += (int64_t)sparse.size();
+        auto it = sparse.begin();
+        while (it != sparse.end()) {
             const int32_t row = it->first.first;
             auto jt = it;
             int32_t xmax = it->first.second;
-            while (jt != g.end() && jt->first.first == row) {
+            while (jt != sparse.end() && jt->first.first == row) {
                 xmax = jt->first.second;
                 ++jt;
             }
@@ -646,6 +686,173 @@ mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *ma
     const int rc = mf::launch_search(a, err, sizeof err);
     if (rc != 0) return fail(MF_ECUDA, "%s", err);
     return ok();
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- batching ---
+
+struct mf_batch {
+    struct Item {
+        mf_stack stack;
+        const float *sigma;
+        const uint8_t *mask;
+        const mf_prf_table *table;
+        float *snr_max;
+        int32_t *argmax;
+        float *snr_all;
+    };
+    int device = 0;
+    std::vector<Item> items;
+    std::vector<mf::SearchArgs> args;
+    std::vector<mf::WorkspaceLayout> layouts;
+    char *ws = nullptr;
+    mf::BatchDevice *dev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;  // private stream the graph is captured on
+    bool prepared = false;
+};
+
+namespace {
+
+size_t batch_item_offsets(const mf_batch *b, std::vector<size_t> *offs) {
+    size_t off = 0;
+    for (const auto &it : b->items) {
+        if (offs) offs->push_back(off);
+        off += (size_t)round_up((int64_t)mf::search_layout(it.stack.T, it.stack.H, it.stack.W, it.table).total, 256);
+    }
+    return off;
+}
+
+void batch_release(mf_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->capture = nullptr;
+    mf::batch_free(b->dev);
+    b->dev = nullptr;
+    b->prepared = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+mf_status mf_batch_create(mf_batch **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    auto *b = new mf_batch;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return fail(MF_ECUDA, "no current CUDA device");
+    }
+    *out = b;
+    return ok();
+}
+
+mf_status mf_batch_add(mf_batch *b, const mf_stack *stack, const float *sigma, const uint8_t *mask,
+                       const mf_prf_table *table, float *snr_max, int32_t *argmax, float *snr_all,
+                       int32_t *index) {
+    if (!b) return fail(MF_EINVAL, "batch is NULL");
+    if (b->prepared) return fail(MF_EINVAL, "batch already prepared; create a new one to change it");
+    mf_status s = check_stack(stack);
+    if (s != MF_OK) return s;
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (stack->T != table->T) return fail(MF_EINVAL, "stack has T=%lld, table has T=%d", (long long)stack->T,
+                                          table->T);
+    if (stack->H * stack->W == 0) return fail(MF_EINVAL, "empty stack in a batch");
+    if (!sigma || !snr_max || !argmax) return fail(MF_EINVAL, "sigma, snr_max and argmax are required");
+    if (table->device != b->device) return fail(MF_EINVAL, "table and batch live on different devices");
+    b->items.push_back({*stack, sigma, mask, table, snr_max, argmax, snr_all});
+    if (index) *index = (int32_t)b->items.size() - 1;
+    return ok();
+}
+
+mf_status mf_batch_workspace_size(const mf_batch *b, size_t *bytes) {
+    if (!b || !bytes) return fail(MF_EINVAL, "NULL argument");
+    *bytes = batch_item_offsets(b, nullptr);
+    return ok();
+}
+
+mf_status mf_batch_prepare(mf_batch *b, void *workspace, size_t workspace_bytes) {
+    if (!b) return fail(MF_EINVAL, "batch is NULL");
+    if (b->items.empty()) return fail(MF_EINVAL, "batch has no items");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return fail(MF_EINVAL, "batch lives on device %d, current device is %d", b->device, dev);
+    std::vector<size_t> offs;
+    const size_t need = batch_item_offsets(b, &offs);
+    if (!workspace || workspace_bytes < need)
+        return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", need, workspace_bytes);
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    batch_release(b);
+    b->ws = (char *)workspace;
+    b->layouts.clear();
+    b->args.clear();
+    for (const auto &it : b->items) b->layouts.push_back(mf::search_layout(it.stack.T, it.stack.H, it.stack.W, it.table));
+    for (size_t i = 0; i < b->items.size(); i++) {
+        const auto &it = b->items[i];
+        b->args.push_back(mf::SearchArgs{&it.stack, it.sigma, it.mask, it.table, it.snr_max, it.argmax, it.snr_all,
+                                         b->ws + offs[i], b->layouts[i], nullptr});
+    }
+    char err[256] = {0};
+    const int rc = mf::batch_build(b->args.data(), (int)b->args.size(), &b->dev, err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    b->prepared = true;
+    return ok();
+}
+
+mf_status mf_batch_run(mf_batch *b, mf_stream stream) {
+    if (!b) return fail(MF_EINVAL, "batch is NULL");
+    if (!b->prepared) return fail(MF_EINVAL, "call mf_batch_prepare first");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b->exec) {
+        // capture on the batch's own stream (the legacy default stream cannot
+        // be captured); the graph is then launched on the caller's stream
+        char err[256] = {0};
+        cudaStream_t cs = b->capture;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail(MF_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+        const int rc = mf::batch_enqueue(b->dev, b->args.data(), (int)b->args.size(), cs, err, sizeof err);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (rc != 0 || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(MF_ECUDA, "batch capture: %s", rc ? err : cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            b->exec = nullptr;
+            return fail(MF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        b->graph = g;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, st);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+mf_status mf_batch_info(const mf_batch *b, int32_t *items, int32_t *shape_groups, int32_t *graph_ready) {
+    if (!b) return fail(MF_EINVAL, "batch is NULL");
+    if (items) *items = (int32_t)b->items.size();
+    if (shape_groups) {
+        int mask = 0;
+        for (const auto &it : b->items) mask |= 1 << it.table->plan.shape;
+        *shape_groups = __builtin_popcount(mask);
+    }
+    if (graph_ready) *graph_ready = b->exec != nullptr;
+    return ok();
+}
+
+void mf_batch_destroy(mf_batch *b) {
+    if (!b) return;
+    batch_release(b);
+    delete b;
 }
 
 mf_status mf_rescore_workspace_size(int64_t H, int64_t W, int32_t k_top, size_t *bytes) {

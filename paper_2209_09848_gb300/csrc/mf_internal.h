@@ -141,6 +141,14 @@ struct SearchArgs {
 // writes a message into err on failure.
 int launch_search(const SearchArgs &a, char *err, size_t errlen);
 
+// Batched searches: device descriptors for a fixed list of searches (built
+// once), and the enqueue of all of them on a stream (side streams fork and
+// join inside; capturable into a CUDA graph).
+struct BatchDevice;
+int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, size_t errlen);
+int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream, char *err, size_t errlen);
+void batch_free(BatchDevice *b);
+
 struct RescoreArgs {
     const mf_stack *stack;
     const float *sigma;

@@ -81,6 +81,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int cod
     }
 }
 
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -326,16 +330,17 @@ __device__ __forceinline__ void stencil_dispatch(const float *__restrict__ base,
 
 // One CTA: an output tile of (32 TYS) x (32 TXS) start pixels for KT
 // trajectories, kWarps warps, one (trajectory, sub-tile) pair per warp.
+// The work of one CTA on one (output tile, trajectory group): returns false
+// if it gave up (a bounded wait ran out; the device status word says why).
+// `smem` is the CTA's 1024-aligned dynamic shared memory, derived from the
+// extern array so that its loads stay shared-memory loads.
 template <int KT, int TXS, int TYS, int VEC>
-__global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_constant__ CUtensorMap ymap,
-                                                              const NumParams p) {
+__device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const NumParams &p, int g, int tile,
+                                               unsigned char *smem) {
     static_assert(KT * TXS * TYS == kWarps, "one warp per (trajectory, sub-tile)");
     constexpr int NS = kStages;
     constexpr int TH = kTile * TYS, TW = kTile * TXS;
     constexpr uint32_t kBlockBytes = (uint32_t)(sizeof(FrameHdr) + KT * sizeof(SlotRec));
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // keep every pointer derived from smem_raw so that loads stay shared-memory loads
-    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int win_floats = p.BH * p.S;
     float *win = reinterpret_cast<float *>(smem);
     unsigned char *fb = smem + (size_t)NS * win_floats * sizeof(float);  // NS frame blocks
@@ -345,8 +350,6 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_const
     int *bad_flag = last_issued + NS;
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem);  // epilogue reuses the windows
 
-    const int g = (int)(blockIdx.x % (unsigned)p.G);
-    const int tile = (int)(blockIdx.x / (unsigned)p.G);
     const int tile_y0 = (tile / p.tiles_x) * TH;
     const int tile_x0 = (tile % p.tiles_x) * TW + kTileOriginX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_const
         fence_barrier_init();
     }
     __syncthreads();
-    if (*bad_flag != 0) return;  // same value for every thread of the CTA
+    if (*bad_flag != 0) return false;  // same value for every thread of the CTA
 
     // Load frame f into stage s: the rows the group's window needs at frame f
     // (TMA, zero fill outside the frame) and the frame's slot records.
@@ -377,11 +380,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_const
         mbar_expect_tx(bar, nl * row_bytes + kBlockBytes);
         const uint32_t dst = smem_u32(win + (size_t)s * win_floats);
         for (int l = 0; l < nl; l++)
-            tma_load_3d(dst + l * row_bytes, &ymap, tile_x0 + h.rox, tile_y0 + h.roy + l * kLoadRows, f, bar);
+            tma_load_3d(dst + l * row_bytes, ymap, tile_x0 + h.rox, tile_y0 + h.roy + l * kLoadRows, f, bar);
         bulk_load(smem_u32(fb + s * kBlockBytes), gblocks + (size_t)f * kBlockBytes, kBlockBytes, bar);
         last_issued[s] = f;
     };
     if (threadIdx.x == 0) {
+        fence_proxy_async();  // earlier generic writes to these buffers precede the copies
         for (int s = 0; s < NS && s < p.T; s++) issue(s, s, p.hdr[(size_t)g * p.T + s]);
     }
 
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_const
                 if (f >= 0) mbar_wait(smem_u32(&bars[s]), (uint32_t)((f / NS) & 1), 2);
             }
         }
-        return;
+        return false;
     }
 
     // Epilogue: every issued frame has been consumed, so the windows are free
@@ -506,6 +510,64 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_const
         const int64_t py = tile_y0 + ly;
         const int64_t px = tile_x0 + lx + lane_skew<VEC>((ly / kMicroRows) % 8);
         atomicMax(&p.keys[py * p.W + px], key);
+    }
+    // the barriers may be initialised again for this CTA's next tile
+    if (threadIdx.x == 0)
+        for (int s = 0; s < NS; s++) mbar_inval(smem_u32(&bars[s]));
+    return true;
+}
+
+template <int KT, int TXS, int TYS, int VEC>
+__global__ void __launch_bounds__(kWarps * 32, 1) k_numerator(const __grid_constant__ CUtensorMap ymap,
+                                                              const NumParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    numerator_tile<KT, TXS, TYS, VEC>(&ymap, p, (int)(blockIdx.x % (unsigned)p.G),
+                                      (int)(blockIdx.x / (unsigned)p.G), smem);
+}
+
+// One item of a batched search: its numerator parameters, tile count and the
+// first entry of its CTA work in the batch-wide work list.
+struct BatchItem {
+    NumParams p;
+    int tiles_y;
+    int pad;
+    long long cta_begin;
+};
+
+// Persistent numerator over a batch of searches: one CTA per SM takes
+// (item, tile, group) work entries from a global counter until the list is
+// exhausted, running the same per-tile code as k_numerator.
+template <int KT, int TXS, int TYS, int VEC>
+__global__ void __launch_bounds__(kWarps * 32, 1) k_numerator_batch(const CUtensorMap *__restrict__ maps,
+                                                                    const BatchItem *__restrict__ items, int n_items,
+                                                                    long long total,
+                                                                    unsigned long long *counter) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ long long work;
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long w = (long long)atomicAdd(counter, 1ull);
+            int lo = 0, hi = n_items - 1;  // last item whose cta_begin <= w
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (items[mid].cta_begin <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            work = w;
+            item = lo;
+        }
+        __syncthreads();
+        const long long w = work;
+        const int i = item;
+        __syncthreads();
+        if (w >= total) break;
+        const NumParams &p = items[i].p;
+        const long long local = w - items[i].cta_begin;
+        if (!numerator_tile<KT, TXS, TYS, VEC>(maps + i, p, (int)(local % p.G), (int)(local / p.G), smem)) break;
+        __syncthreads();
     }
 }
 
@@ -589,7 +651,10 @@ struct LaunchScope {
     LaunchScope(int k, cudaStream_t s) : kid(k), st(s) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         g_prof_count[kid]++;
-        if (g_prof_on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
+        if (g_prof_on && cs == cudaStreamCaptureStatusNone && cudaEventCreate(&a) == cudaSuccess &&
+            cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, st);
     }
     ~LaunchScope() {
@@ -636,21 +701,18 @@ int profile_read(mf_profile *out, int reset) {
     return 0;
 }
 
-int launch_search(const SearchArgs &a, char *err, size_t errlen) {
+namespace {
+
+// Inverse variance, weighted stack, denominator and a cleared key buffer.
+int enqueue_pre(const SearchArgs &a, cudaStream_t stream, char *err, size_t errlen) {
     const mf_stack &st = *a.stack;
     const mf_prf_table &tab = *a.tab;
-    const Plan &pl = tab.plan;
     const WorkspaceLayout &L = a.L;
-    cudaStream_t stream = (cudaStream_t)a.stream;
     const int64_t T = st.T, H = st.H, W = st.W, P = H * W;
     float *lam = reinterpret_cast<float *>(a.ws + L.lam_off);
     float *y = reinterpret_cast<float *>(a.ws + L.y_off);
     float *isd = reinterpret_cast<float *>(a.ws + L.isd_off);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
-
-    int rc = get_encode(err, errlen);
-    if (rc) return rc;
-
     {
         LaunchScope ls(kKLambda, stream);
         k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(a.sigma, a.mask, H, W, L.pad, L.lam_w,
@@ -661,24 +723,26 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
     const int64_t nw = T * H * ((W + 3) / 4);
     const int64_t fs = st.frame_stride, rs = st.row_stride;
     {
-    LaunchScope ls(kKWeight, stream);
-    switch (st.dtype) {
-        case MF_F32:
-            k_weight<float><<<grid_for(nw, 256), 256, 0, stream>>>((const float *)st.data, fs, rs, st.frame_scale,
-                                                                   lam, L.pad, L.lam_w, y, T, H, W, L.y_pitch);
-            break;
-        case MF_BF16:
-            k_weight<__nv_bfloat16><<<grid_for(nw, 256), 256, 0, stream>>>(
-                (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, lam, L.pad, L.lam_w, y, T, H, W, L.y_pitch);
-            break;
-        default:
-            k_weight<__half><<<grid_for(nw, 256), 256, 0, stream>>>((const __half *)st.data, fs, rs, st.frame_scale,
-                                                                    lam, L.pad, L.lam_w, y, T, H, W, L.y_pitch);
-            break;
-    }
+        LaunchScope ls(kKWeight, stream);
+        switch (st.dtype) {
+            case MF_F32:
+                k_weight<float><<<grid_for(nw, 256), 256, 0, stream>>>((const float *)st.data, fs, rs,
+                                                                       st.frame_scale, lam, L.pad, L.lam_w, y, T,
+                                                                       H, W, L.y_pitch);
+                break;
+            case MF_BF16:
+                k_weight<__nv_bfloat16><<<grid_for(nw, 256), 256, 0, stream>>>(
+                    (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, lam, L.pad, L.lam_w, y, T, H, W,
+                    L.y_pitch);
+                break;
+            default:
+                k_weight<__half><<<grid_for(nw, 256), 256, 0, stream>>>((const __half *)st.data, fs, rs,
+                                                                        st.frame_scale, lam, L.pad, L.lam_w, y,
+                                                                        T, H, W, L.y_pitch);
+                break;
+        }
     }
     MF_CHECK_LAUNCH("k_weight");
-
     {
         const int nbx = (int)((W + kDenCols - 1) / kDenCols);
         const int nby = (int)((H + 7) / 8);
@@ -688,61 +752,110 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
                                                 W, nbx, isd);
         MF_CHECK_LAUNCH("k_denominator");
     }
-
     cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)P * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) {
         snprintf(err, errlen, "cudaMemsetAsync: %s", cudaGetErrorString(e));
         return (int)e;
     }
+    return 0;
+}
 
-    CUtensorMap map;
-    {
-        cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
-        cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * 4, (cuuint64_t)(H * L.y_pitch * 4)};
-        cuuint32_t box[3] = {(cuuint32_t)pl.S, (cuuint32_t)kLoadRows, 1};
-        cuuint32_t estr[3] = {1, 1, 1};
-        CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr != CUDA_SUCCESS) {
-            snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-            return (int)cudaErrorInvalidValue;
-        }
+// Tensor map over the weighted stack and the numerator's parameters.
+int numerator_params(const SearchArgs &a, CUtensorMap *map, NumParams *np, int *tiles_y, char *err,
+                     size_t errlen) {
+    const mf_stack &st = *a.stack;
+    const mf_prf_table &tab = *a.tab;
+    const Plan &pl = tab.plan;
+    const WorkspaceLayout &L = a.L;
+    const int64_t T = st.T, H = st.H, W = st.W;
+    int rc = get_encode(err, errlen);
+    if (rc) return rc;
+    float *y = reinterpret_cast<float *>(a.ws + L.y_off);
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
+    cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * 4, (cuuint64_t)(H * L.y_pitch * 4)};
+    cuuint32_t box[3] = {(cuuint32_t)pl.S, (cuuint32_t)kLoadRows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+        return (int)cudaErrorInvalidValue;
     }
-    {
-        NumParams np;
-        np.blocks = tab.d_blocks;
-        np.hdr = tab.d_hdr;
-        np.isd = isd;
-        np.keys = keys;
-        np.snr_all = a.snr_all;
-        np.T = (int)T;
-        np.G = pl.G;
-        np.H = H;
-        np.W = W;
-        np.tiles_x = (int)((W - kTileOriginX + pl.tile_w() - 1) / pl.tile_w());
-        const int tiles_y = (int)((H + pl.tile_h() - 1) / pl.tile_h());
-        np.S = pl.S;
-        np.BH = pl.BH;
-        np.lockstep = pl.lockstep;
-        const size_t smem = numerator_smem_bytes(pl.S, pl.BH, pl.kt());
-        void (*kern)(const CUtensorMap, const NumParams) = nullptr;
-#define MF_PICK(V)                                                  \
-    switch (pl.shape) {                                             \
-        case 0: kern = k_numerator<16, 1, 1, V>; break;             \
-        case 1: kern = k_numerator<8, 2, 1, V>; break;              \
-        case 2: kern = k_numerator<4, 2, 2, V>; break;              \
-        default: kern = k_numerator<2, 4, 2, V>; break;             \
+    np->blocks = tab.d_blocks;
+    np->hdr = tab.d_hdr;
+    np->isd = reinterpret_cast<float *>(a.ws + L.isd_off);
+    np->keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
+    np->snr_all = a.snr_all;
+    np->T = (int)T;
+    np->G = pl.G;
+    np->H = H;
+    np->W = W;
+    np->tiles_x = (int)((W - kTileOriginX + pl.tile_w() - 1) / pl.tile_w());
+    np->S = pl.S;
+    np->BH = pl.BH;
+    np->lockstep = pl.lockstep;
+    *tiles_y = (int)((H + pl.tile_h() - 1) / pl.tile_h());
+    return 0;
+}
+
+typedef void (*NumKernel)(const CUtensorMap, const NumParams);
+typedef void (*NumBatchKernel)(const CUtensorMap *, const BatchItem *, int, long long, unsigned long long *);
+
+NumKernel pick_numerator(int shape, int vec) {
+#define MF_PICK(V)                                       \
+    switch (shape) {                                     \
+        case 0: return k_numerator<16, 1, 1, V>;         \
+        case 1: return k_numerator<8, 2, 1, V>;          \
+        case 2: return k_numerator<4, 2, 2, V>;          \
+        default: return k_numerator<2, 4, 2, V>;         \
     }
-        if (pl.vec == 4) {
-            MF_PICK(4)
-        } else if (pl.vec == 2) {
-            MF_PICK(2)
-        } else {
-            MF_PICK(1)
-        }
+    if (vec == 4) {
+        MF_PICK(4)
+    } else if (vec == 2) {
+        MF_PICK(2)
+    } else {
+        MF_PICK(1)
+    }
 #undef MF_PICK
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+NumBatchKernel pick_numerator_batch(int shape) {
+    switch (shape) {
+        case 0: return k_numerator_batch<16, 1, 1, 2>;
+        case 1: return k_numerator_batch<8, 2, 1, 2>;
+        case 2: return k_numerator_batch<4, 2, 2, 2>;
+        default: return k_numerator_batch<2, 4, 2, 2>;
+    }
+}
+
+int enqueue_finalize(const SearchArgs &a, cudaStream_t stream, char *err, size_t errlen) {
+    const int64_t P = a.stack->H * a.stack->W;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + a.L.keys_off);
+    {
+        LaunchScope ls(kKFinalize, stream);
+        k_finalize<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, a.snr_max, a.argmax);
+    }
+    MF_CHECK_LAUNCH("k_finalize");
+    return 0;
+}
+
+}  // namespace
+
+int launch_search(const SearchArgs &a, char *err, size_t errlen) {
+    cudaStream_t stream = (cudaStream_t)a.stream;
+    const Plan &pl = a.tab->plan;
+    int rc = enqueue_pre(a, stream, err, errlen);
+    if (rc) return rc;
+    CUtensorMap map;
+    NumParams np;
+    int tiles_y = 0;
+    rc = numerator_params(a, &map, &np, &tiles_y, err, errlen);
+    if (rc) return rc;
+    {
+        const size_t smem = numerator_smem_bytes(pl.S, pl.BH, pl.kt());
+        NumKernel kern = pick_numerator(pl.shape, pl.vec);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
             snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
             return (int)e;
@@ -752,11 +865,139 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
         kern<<<(unsigned)nblocks, kWarps * 32, smem, stream>>>(map, np);
         MF_CHECK_LAUNCH("k_numerator");
     }
-    {
-        LaunchScope ls(kKFinalize, stream);
-        k_finalize<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, a.snr_max, a.argmax);
+    return enqueue_finalize(a, stream, err, errlen);
+}
+
+// ------------------------------------------------------------ batching ---
+//
+// A batch of searches (uneven cutouts, each with its own filter bank) runs as
+// per-item preparation kernels spread over side streams, one persistent
+// numerator launch per CTA shape in the batch (usually one), and per-item
+// finalisation.  The descriptors the persistent kernel reads (tensor maps,
+// parameters, work-list offsets) live in device memory owned by the batch.
+
+struct BatchDevice {
+    struct Group {
+        int shape = 0;
+        int first = 0, count = 0;  // range in the device arrays
+        long long total = 0;       // CTA work entries
+        size_t smem = 0;
+    };
+    std::vector<Group> groups;
+    std::vector<int> order;  // device-array position -> item
+    CUtensorMap *d_maps = nullptr;
+    BatchItem *d_items = nullptr;
+    unsigned long long *d_counters = nullptr;
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
+    int sms = 0;
+};
+
+void batch_free(BatchDevice *b) {
+    if (!b) return;
+    cudaFree(b->d_maps);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counters);
+    for (int i = 0; i < BatchDevice::kSide; i++) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
     }
-    MF_CHECK_LAUNCH("k_finalize");
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, size_t errlen) {
+    auto *b = new BatchDevice;
+    std::vector<CUtensorMap> maps;
+    std::vector<BatchItem> bitems;
+    for (int shape = 0; shape < kNumShapes; shape++) {
+        BatchDevice::Group grp;
+        grp.shape = shape;
+        grp.first = (int)bitems.size();
+        for (int i = 0; i < n; i++) {
+            const Plan &pl = items[i].tab->plan;
+            if (pl.shape != shape) continue;
+            CUtensorMap m;
+            BatchItem bi;
+            std::memset(&bi, 0, sizeof bi);
+            int rc = numerator_params(items[i], &m, &bi.p, &bi.tiles_y, err, errlen);
+            if (rc) {
+                batch_free(b);
+                return rc;
+            }
+            bi.cta_begin = grp.total;
+            grp.total += (long long)pl.G * bi.p.tiles_x * bi.tiles_y;
+            grp.smem = std::max(grp.smem, numerator_smem_bytes(pl.S, pl.BH, pl.kt()));
+            maps.push_back(m);
+            bitems.push_back(bi);
+            b->order.push_back(i);
+        }
+        grp.count = (int)bitems.size() - grp.first;
+        if (grp.count > 0) b->groups.push_back(grp);
+    }
+    cudaError_t e = cudaSuccess;
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && !maps.empty()) e = cudaMalloc((void **)&b->d_maps, maps.size() * sizeof(CUtensorMap));
+    if (e == cudaSuccess && !bitems.empty()) e = cudaMalloc((void **)&b->d_items, bitems.size() * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counters, kNumShapes * sizeof(unsigned long long));
+    if (e == cudaSuccess && !maps.empty())
+        e = cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !bitems.empty())
+        e = cudaMemcpy(b->d_items, bitems.data(), bitems.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    for (int i = 0; i < BatchDevice::kSide && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (const auto &grp : b->groups) {
+        if (e != cudaSuccess) break;
+        e = cudaFuncSetAttribute(pick_numerator_batch(grp.shape), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)grp.smem);
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "batch set-up: %s", cudaGetErrorString(e));
+        batch_free(b);
+        return (int)e;
+    }
+    *out = b;
+    return 0;
+}
+
+int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream_v, char *err, size_t errlen) {
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    cudaError_t e = cudaEventRecord(b->fork, stream);
+    for (int s = 0; s < BatchDevice::kSide && e == cudaSuccess; s++) e = cudaStreamWaitEvent(b->side[s], b->fork, 0);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "batch fork: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    for (int i = 0; i < n; i++) {
+        int rc = enqueue_pre(items[i], b->side[i % BatchDevice::kSide], err, errlen);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < BatchDevice::kSide && e == cudaSuccess; s++) {
+        e = cudaEventRecord(b->join[s], b->side[s]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->join[s], 0);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, kNumShapes * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "batch join: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    for (const auto &grp : b->groups) {
+        const int grid = (int)std::min<long long>(grp.total, (long long)b->sms);
+        LaunchScope ls(kKNumerator, stream);
+        pick_numerator_batch(grp.shape)<<<grid, kWarps * 32, grp.smem, stream>>>(
+            b->d_maps + grp.first, b->d_items + grp.first, grp.count, grp.total, b->d_counters + grp.shape);
+        MF_CHECK_LAUNCH("k_numerator_batch");
+    }
+    for (int i = 0; i < n; i++) {
+        int rc = enqueue_finalize(items[i], stream, err, errlen);
+        if (rc) return rc;
+    }
     return 0;
 }
 

@@ -1,0 +1,93 @@
+"""Batched searches (one CUDA graph, persistent numerator): every search in a
+batch of uneven cutouts gives exactly the maps mf_search gives for it alone
+(same per-tile code and summation order), on the first run and on graph
+replays; one search is also checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from _util import check_search
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2209_09848_gb300 as m
+    assert torch.cuda.is_available()
+    m.load()
+    return m
+
+
+def _items(mf):
+    from paper_2209_09848_gb300 import synth
+    specs = [  # T, H, W, grid, vmax, dtype, mask, shape
+        (24, 96, 130, (3, 3), 0.3, torch.float32, 0.02, None),
+        (9, 64, 64, (2, 2), 0.5, torch.bfloat16, 0.0, None),
+        (31, 150, 90, (4, 2), 0.2, torch.float32, 0.01, 0),
+        (16, 70, 200, (5, 3), 0.25, torch.float16, 0.02, 3),
+        (5, 33, 47, (1, 1), 0.1, torch.float32, 0.0, None),
+        (40, 128, 128, (3, 4), 0.15, torch.float32, 0.01, 1),
+    ]
+    out = []
+    for i, (T, H, W, (nx, ny), vm, dt, mfrac, shape) in enumerate(specs):
+        c = synth.small_case(T, H, W, 200 + i, mask_frac=mfrac, movers=2)
+        vx, vy = synth.velocity_grid(nx, ny, -vm, vm)
+        table = mf.prf_table_create(vx, vy, T, shape=shape)
+        scale = None
+        if dt == torch.float16:
+            scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14).astype(np.float32)
+            data = torch.from_numpy(c["res"] / scale[:, None, None]).to(dt).cuda()
+            scale = torch.from_numpy(scale).cuda()
+        else:
+            data = torch.from_numpy(c["res"]).to(dt).cuda()
+        s = torch.from_numpy(c["sigma"]).cuda()
+        m = None if c["mask"] is None else torch.from_numpy(c["mask"]).cuda()
+        out.append(dict(c=c, vx=vx, vy=vy, table=table, data=data, sigma=s, mask=m, scale=scale))
+    return out
+
+
+def test_batch_equals_individual_searches(mf, oracle):
+    items = _items(mf)
+    b = mf.Batch()
+    for it in items:
+        b.add(it["data"], it["sigma"], it["table"], mask=it["mask"], frame_scale=it["scale"], want_all=True)
+    b.prepare()
+    info = b.info()
+    assert info["items"] == len(items) and info["shape_groups"] >= 2 and not info["graph_ready"]
+    alone = [mf.search(it["data"], it["sigma"], it["table"], mask=it["mask"], frame_scale=it["scale"],
+                       want_all=True) for it in items]
+    torch.cuda.synchronize()
+    for run in range(3):
+        for o in b.outputs:  # scribble over the outputs: every replay must rewrite them
+            o[0].fill_(-7.0)
+            o[1].fill_(-7)
+            o[2].fill_(-7.0)
+        b.run()
+        torch.cuda.synchronize()
+        assert mf.device_status() == 0
+        assert b.info()["graph_ready"]
+        for (gm, ga, gall), (am, aa, aall) in zip(b.outputs, alone):
+            assert torch.equal(gm, am) and torch.equal(ga, aa) and torch.equal(gall, aall)
+    # and one of them against the FP64 oracle
+    it = items[0]
+    sh, tp = oracle.trajectory_table(it["vx"], it["vy"], it["data"].shape[0])
+    lam = oracle.inverse_variance(it["c"]["sigma"], it["c"]["mask"])
+    N, D = oracle.search_full(it["c"]["res"], lam, sh, tp)
+    gm, ga, gall = b.outputs[0]
+    check_search(gm.cpu().numpy(), ga.cpu().numpy(), gall.cpu().numpy(), N, D, oracle, label="batch item 0")
+    b.destroy()
+
+
+def test_batch_argument_errors(mf):
+    b = mf.Batch()
+    with pytest.raises(mf.MFError):
+        b.run()  # not prepared
+    with pytest.raises(mf.MFError):
+        b.prepare()  # no items
+    T = 4
+    table = mf.prf_table_create([0.1], [0.0], T)
+    r = torch.zeros((T + 1, 8, 8), device="cuda")
+    with pytest.raises(mf.MFError):
+        b.add(r, torch.ones((8, 8), device="cuda"), table)  # T mismatch
+    b.destroy()
