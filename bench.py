@@ -20,6 +20,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -385,6 +387,151 @@ def run_ours(args):
     return 0
 
 
+def _cutout(rng, dev, side, T, K, dtype, seed):
+    """One cutout of the batched / serving workloads: config-2 statistics
+    scaled to the cutout (movers in proportion to its area, at least 1)."""
+    import torch
+
+    from paper_2209_09848_gb300 import synth
+    n_mov = max(1, int(round(200 * side * side / (2048 * 2048))))
+    case = synth.paper_case_gpu(T=T, H=side, W=side, n_movers=n_mov, seed=seed, device=dev)
+    nx = max(1, int(round(np.sqrt(K))))
+    ny = max(1, int(round(K / nx)))
+    vx, vy = synth.velocity_grid(nx, ny, -VMAX, VMAX)
+    res = case["res"]
+    if dtype == "bf16":
+        res = res.to(torch.bfloat16)
+    return dict(res=res, sigma=case["sigma"], mask=case["mask"], vx=vx, vy=vy, T=T, side=side)
+
+
+def run_batch(args):
+    """Batched form: uneven cutouts in one graph-captured persistent launch,
+    layouts picked by the autotuner, against the same searches launched one
+    at a time."""
+    import torch
+
+    import paper_2209_09848_gb300 as mf
+    from paper_2209_09848_gb300 import _build, autotune
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(4)
+    items = []
+    for i in range(args.items):
+        side = int(rng.choice([256, 512, 768, 1024]))
+        T = int(rng.integers(300, 1301))
+        K = int(rng.integers(50, 401))
+        dt = "bf16" if rng.random() < 0.5 else "f32"
+        items.append(_cutout(rng, dev, side, T, K, dt, 100 + i))
+    units = sum(len(it["vx"]) * it["T"] * it["side"] ** 2 for it in items)
+    t0 = time.perf_counter()
+    for it in items:
+        dtype = it["res"].dtype
+        it["table"] = autotune.tuned_table(it["vx"], it["vy"], it["T"], it["side"], it["side"], dtype=dtype,
+                                           crop=256, reps=1)
+    tune_s = time.perf_counter() - t0
+    b = mf.Batch()
+    for it in items:
+        b.add(it["res"], it["sigma"], it["table"], mask=it["mask"])
+    b.prepare(device=dev)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    # the same searches, one launch sequence per cutout
+    e0.record()
+    for it in items:
+        mf.search(it["res"], it["sigma"], it["table"], mask=it["mask"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    ok = all(torch.equal(o[0], mf.search(it["res"], it["sigma"], it["table"], mask=it["mask"])[0])
+             for o, it in list(zip(b.outputs, items))[:4])
+    line = {"metric": "traj*pixel*frame/s, %d uneven cutouts in one graph-captured persistent launch" % len(items),
+            "value": units / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 and bf16 storage, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": "batched form: sides {256,512,768,1024}^2, frames 300-1300, 50-400 "
+                                   "trajectories each, fp32 or bf16 (coin flip), sigma/mask/movers as the "
+                                   "paper-shaped stack", "items": len(items), "units": units,
+                       "autotune_s": tune_s, "info": b.info()},
+            "one_launch_per_cutout": {"value": units / (ms_seq * 1e-3), "ms": ms_seq},
+            "speedup_vs_one_launch_per_cutout": ms_seq / ms_batch,
+            "batch_equals_single_search": bool(ok)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving form: Poisson request stream, admission by footprint against
+    a memory budget, continuous batching on several streams; p50/p99 latency
+    and throughput, against the same stream served one request at a time."""
+    import torch
+
+    from paper_2209_09848_gb300 import _build
+    from paper_2209_09848_gb300.serve import Request, Server, percentile
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(5)
+    pool = []
+    for i in range(args.pool):
+        side = int(rng.choice([256, 512, 768, 1024]))
+        T = int(rng.integers(300, 1301))
+        K = int(rng.integers(10, 201))
+        dt = "bf16" if rng.random() < 0.5 else "f32"
+        c = _cutout(rng, dev, side, T, K, dt, 500 + i)
+        req = Request(stack=c["res"].cpu().pin_memory(), sigma=c["sigma"].cpu().pin_memory(),
+                      vx=c["vx"], vy=c["vy"], mask=c["mask"].cpu().pin_memory(), k_top=64,
+                      tag=(len(c["vx"]) * T * side * side))
+        pool.append(req)
+        del c
+    torch.cuda.empty_cache()
+    n_req = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    picks = rng.integers(0, len(pool), n_req)
+
+    def serve(streams):
+        srv = Server(budget_bytes=int(args.budget_gb * 1e9), streams=streams, planners=8, device=dev)
+        # warm the planners and the allocator on one request
+        srv.submit(pool[0]).result()
+        futs = []
+        t0 = time.perf_counter()
+        for t_arr, k in zip(arrivals, picks):
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            futs.append(srv.submit(pool[k]))
+        res = [f.result() for f in futs]
+        srv.close()
+        lat = [r.latency * 1e3 for r in res]
+        span = max(r.done for r in res) - min(r.arrival for r in res)
+        units = sum(r.tag for r in res)
+        return {"p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "mean_ms": float(np.mean(lat)),
+                "throughput": units / span, "requests": len(res), "span_s": span,
+                "peak_bytes": srv.peak}
+
+    mix = serve(args.streams)
+    one = serve(1)
+    line = {"metric": "serve p50/p99 latency (ms) and traj*pixel*frame/s under a Poisson request stream",
+            "value": mix["throughput"], "unit": UNIT, "n_gpus": 1, "steps": mix["requests"],
+            "warmup": 1, "ms_per_step": mix["mean_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 and bf16 storage, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": "serving form: Poisson %.0f req/s for %.0f s, cutouts as the batched form with "
+                                   "10-200 trajectories, top-64 FP64 rescore each, budget %.0f GB, %d streams"
+                                   % (args.rate, args.duration, args.budget_gb, args.streams),
+                       "distinct_requests": len(pool)},
+            "serve": mix, "one_request_at_a_time": one}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,11 +545,23 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rescore", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--workload", choices=["search", "batch", "serve"], default="search",
+                    help="search: the paper-shaped search (default); batch / serve: the batched and serving forms")
+    ap.add_argument("--items", type=int, default=64, help="batch: cutouts in the batch")
+    ap.add_argument("--pool", type=int, default=16, help="serve: distinct pregenerated requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: admission budget")
+    ap.add_argument("--streams", type=int, default=4, help="serve: searches in flight")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 
