@@ -162,7 +162,8 @@ bool measure(mf::Plan &p, const mf_prf_table &t) {
         const int aw = active * sh.txs * sh.tys;
         const double issue = mf::kWarps * 950.0 / 4.0;
         for (int f = 0; f < t.T; f++) {
-            const double smem = aw * 105.0 + rows[(size_t)g * t.T + f] * (double)p.S / 32.0;
+            // the kernel stages the whole BH x S window every frame
+            const double smem = aw * 105.0 + p.BH * (double)p.S / 32.0;
             cyc += std::max(issue, smem);
         }
     }

@@ -23,7 +23,7 @@ constexpr int kMicroCols = 8;
 constexpr int kTileOriginX = -8;     // first tile column (covers the skewed rows at x = 0)
 constexpr int kWarps = 16;           // warps per numerator CTA
 constexpr int kStages = 3;           // frame windows in flight per CTA
-constexpr int kLoadRows = 8;         // rows per TMA box
+constexpr int kLoadRows = 8;         // window rows are a multiple of this
 constexpr int kFrameBlock = 16;      // frames per FP32 partial sum in the numerator
 constexpr int kDenTaps = 256;        // denominator taps per FP32 partial before the FP64 add
 constexpr int kDenCols = 256;        // denominator: start pixels per warp (one row)
@@ -51,7 +51,7 @@ static_assert(sizeof(SlotRec) == 128, "SlotRec is 128 bytes");
 struct alignas(16) FrameHdr {
     int32_t roy;    // min_k s_y - 2
     int32_t rox;    // floor4(min_k s_x - 2)
-    int32_t nrows;  // rows to load, a multiple of kLoadRows
+    int32_t nrows;  // rows the group's window needs at this frame (the kernel loads all BH)
     int32_t pad;
 };
 
@@ -59,6 +59,10 @@ struct alignas(16) FrameHdr {
 // t + kStages (the frame the issuing warp loads next into this stage) followed
 // by kt slot records of frame t.
 inline size_t frame_block_bytes(int kt) { return sizeof(FrameHdr) + (size_t)kt * sizeof(SlotRec); }
+
+// Frame blocks arrive in chunks of kRecordChunk consecutive frames (one bulk
+// copy per chunk, double-buffered); at least kStages frames per chunk.
+constexpr int kRecordChunk = 4;
 
 // One row of the collapsed denominator kernel G_k: weights for columns
 // x0 .. x0 + 8 * nch - 1 (x0 a multiple of 4) of row offset dy.
@@ -84,7 +88,7 @@ struct Plan {
 // Dynamic shared memory of the numerator kernel: windows (the key tile of the
 // epilogue reuses them), frame blocks, barriers and counters, alignment slack.
 inline size_t numerator_smem_bytes(int S, int BH, int kt) {
-    return 1024 + (size_t)kStages * BH * S * sizeof(float) + (size_t)kStages * frame_block_bytes(kt) +
+    return 1024 + (size_t)kStages * BH * S * sizeof(float) + 2 * (size_t)kRecordChunk * frame_block_bytes(kt) +
            (size_t)kStages * sizeof(uint64_t) + 3 * kStages * sizeof(int) + sizeof(int) + 64;
 }
 

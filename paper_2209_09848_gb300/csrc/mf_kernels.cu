@@ -63,6 +63,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking check of a phase (acquire on success).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ int status_now() { return *(volatile int *)&g_status; }
 
 // Wait for a phase of an mbarrier, giving up after kWaitCycles or as soon as
@@ -341,10 +354,12 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
     constexpr int NS = kStages;
     constexpr int TH = kTile * TYS, TW = kTile * TXS;
     constexpr uint32_t kBlockBytes = (uint32_t)(sizeof(FrameHdr) + KT * sizeof(SlotRec));
+    constexpr int R = kRecordChunk;  // frames per record chunk
+    static_assert(R >= NS, "a record chunk must outlive the frames in flight");
     const int win_floats = p.BH * p.S;
     float *win = reinterpret_cast<float *>(smem);
     unsigned char *fb = smem + (size_t)NS * win_floats * sizeof(float);  // NS frame blocks
-    uint64_t *bars = reinterpret_cast<uint64_t *>(fb + NS * kBlockBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(fb + 2 * R * kBlockBytes);  // fb: 2 chunks of R blocks
     int *cnt = reinterpret_cast<int *>(bars + NS);
     int *last_issued = cnt + NS;
     int *bad_flag = last_issued + NS;
@@ -374,14 +389,17 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
     // Load frame f into stage s: the rows the group's window needs at frame f
     // (TMA, zero fill outside the frame) and the frame's slot records.
     auto issue = [&](int f, int s, FrameHdr h) {
+        // one box of the whole window (BH x S): every TMA operation costs the
+        // CTA's shared-memory pipeline more than the rows it would save
         const uint32_t bar = smem_u32(&bars[s]);
-        const int nl = h.nrows / kLoadRows;
-        const uint32_t row_bytes = (uint32_t)kLoadRows * p.S * 4;
-        mbar_expect_tx(bar, nl * row_bytes + kBlockBytes);
-        const uint32_t dst = smem_u32(win + (size_t)s * win_floats);
-        for (int l = 0; l < nl; l++)
-            tma_load_3d(dst + l * row_bytes, ymap, tile_x0 + h.rox, tile_y0 + h.roy + l * kLoadRows, f, bar);
-        bulk_load(smem_u32(fb + s * kBlockBytes), gblocks + (size_t)f * kBlockBytes, kBlockBytes, bar);
+        // the first frame of a chunk also brings the records of the chunk's
+        // frames (its buffer last held chunk f / R - 2, long released)
+        const int nrec = (f % R == 0) ? min(R, p.T - f) : 0;
+        mbar_expect_tx(bar, (uint32_t)win_floats * 4 + (uint32_t)nrec * kBlockBytes);
+        tma_load_3d(smem_u32(win + (size_t)s * win_floats), ymap, tile_x0 + h.rox, tile_y0 + h.roy, f, bar);
+        if (nrec)
+            bulk_load(smem_u32(fb + ((f / R) & 1) * R * kBlockBytes), gblocks + (size_t)f * kBlockBytes,
+                      (uint32_t)nrec * kBlockBytes, bar);
         last_issued[s] = f;
     };
     if (threadIdx.x == 0) {
@@ -403,15 +421,21 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
         }
     int kk = -1;
     bool bad = false;
+    bool next_ready = false;  // frame t's data already seen complete during frame t - 1
     for (int t = 0; t < p.T; t++) {
         const int s = t % NS;
-        const bool ready = mbar_wait(smem_u32(&bars[s]), (uint32_t)((t / NS) & 1), 1);
+        const bool ready = next_ready || mbar_wait(smem_u32(&bars[s]), (uint32_t)((t / NS) & 1), 1);
         if (!ready && !p.lockstep) {
             bad = true;
             break;
         }
-        const SlotRec *rec = reinterpret_cast<const SlotRec *>(fb + s * kBlockBytes + sizeof(FrameHdr)) + slot;
+        const unsigned char *fblk = fb + (((t / R) & 1) * R + t % R) * kBlockBytes;  // frame t's block
+        const SlotRec *rec = reinterpret_cast<const SlotRec *>(fblk + sizeof(FrameHdr)) + slot;
         kk = rec->k;
+        // Look at the next frame's barrier now: the check's latency then hides
+        // behind this frame's arithmetic instead of stalling the next frame.
+        next_ready = !p.lockstep && t + 1 < p.T &&
+                     mbar_test_wait(smem_u32(&bars[(t + 1) % NS]), (uint32_t)(((t + 1) / NS) & 1));
         if (ready && kk >= 0 && inside) {
             float w[28];
             const float4 *w4 = reinterpret_cast<const float4 *>(rec->taps);
@@ -446,7 +470,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
                 break;
             }
             if (threadIdx.x == 0 && t + NS < p.T) {
-                const FrameHdr h = *reinterpret_cast<const FrameHdr *>(fb + s * kBlockBytes);
+                const FrameHdr h = *reinterpret_cast<const FrameHdr *>(fblk);
                 fence_proxy_async();
                 issue(t + NS, s, h);
             }
@@ -460,7 +484,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
             if (prev == kWarps - 1) {
                 cnt[s] = 0;
                 if (t + NS < p.T) {
-                    const FrameHdr h = *reinterpret_cast<const FrameHdr *>(fb + s * kBlockBytes);
+                    const FrameHdr h = *reinterpret_cast<const FrameHdr *>(fblk);
                     fence_proxy_async();
                     issue(t + NS, s, h);
                 }
@@ -773,7 +797,7 @@ int numerator_params(const SearchArgs &a, CUtensorMap *map, NumParams *np, int *
     float *y = reinterpret_cast<float *>(a.ws + L.y_off);
     cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
     cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * 4, (cuuint64_t)(H * L.y_pitch * 4)};
-    cuuint32_t box[3] = {(cuuint32_t)pl.S, (cuuint32_t)kLoadRows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)pl.S, (cuuint32_t)pl.BH, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
