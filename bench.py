@@ -117,6 +117,23 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(x: float, dist=None, device=None) -> float:
+    """Max of a per-rank number over all ranks (the slowest rank sets the
+    whole job's time); identity without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Weak scaling: every rank processes its own units; the job's throughput
+    is all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def _traffic_from_profiles():
     """DRAM bytes per numerator launch from the committed ncu summary, if any."""
     path = os.path.join(ROOT, "profiles", "k_numerator_paper_shaped.md")
@@ -288,13 +305,9 @@ def run_ours(args):
     clocks = sampler.stop()
     prof = mf.profile_read(reset=True)
     mf.profile_enable(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, dev)
     units_rank = K * T * H * W
-    value = units_rank * ws / (ms * 1e-3)
+    value = job_throughput(units_rank, ws, ms * 1e-3)
 
     peaks, peak_src = _peaks()
     num_launches, num_ms_total = prof["k_numerator"]
@@ -328,12 +341,8 @@ def run_ours(args):
             out_max.copy_(snr_max, non_blocking=True)
             out_arg.copy_(argmax, non_blocking=True)
             torch.cuda.synchronize(dev)
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": units_rank * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
+        e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dist, dev)
+        e2e = {"value": job_throughput(units_rank, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
                "d2h_bytes_per_step": H * W * 8, "steps": e2e_steps}
         del host
 
