@@ -541,6 +541,94 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """Precision form: the paper-shaped stack stored as FP32, BF16 (scale 1)
+    and FP16 (per-frame scale max|r_t| / 2^14), 1000 trajectories (40 x 25
+    grid), FP32 accumulation; each form timed and its SNR error against the
+    FP64 oracle (evaluated on the FP32 master) reported on sampled pixels, plus
+    the error of the FP64 re-score of the top candidates."""
+    import torch
+
+    import oracle
+    import paper_2209_09848_gb300 as mf
+    from paper_2209_09848_gb300 import _build, synth
+    _build.build()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    T, H, W = args.frames, args.size, args.size
+    case = synth.paper_case_gpu(T=T, H=H, W=W, seed=3, device=dev)
+    vx, vy = synth.velocity_grid(40, 25, -args.vmax, args.vmax)
+    K = len(vx)
+    table = mf.prf_table_create(vx, vy, T)
+    master = case["res"]
+    scale16 = (master.abs().amax(dim=(1, 2)) / 2.0 ** 14).float().contiguous()
+    forms = {"f32": (master, None), "bf16": (master.to(torch.bfloat16), None),
+             "f16": ((master / scale16[:, None, None]).to(torch.float16), scale16)}
+    rng = np.random.default_rng(11)
+    n_px = args.sample_px
+    ys = rng.integers(0, H, n_px).astype(np.int32)
+    xs = rng.integers(0, W, n_px).astype(np.int32)
+    res_host = master.cpu().numpy()
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(case["sigma_np"], case["mask_np"])
+    t0 = time.perf_counter()
+    N, D = oracle.search_points(res_host, lam, sh, tp, np.repeat(ys, K), np.repeat(xs, K),
+                                np.tile(np.arange(K, dtype=np.int32), n_px))
+    oracle_s = time.perf_counter() - t0
+    N = N.reshape(n_px, K)
+    D = D.reshape(n_px, K)
+    o_snr = np.where(D > 0, N / np.sqrt(np.where(D > 0, D, 1.0)), 0.0)
+    o_max = np.where(D > 0, o_snr, -np.inf).max(axis=1)
+    ws = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
+    out = {}
+    peaks, _ = _peaks()
+    peak_tf = _fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    units = K * T * H * W
+    mf.profile_enable(True)
+    for name, (stack, fs) in forms.items():
+        smax = torch.empty((H, W), device=dev)
+        amax = torch.empty((H, W), dtype=torch.int32, device=dev)
+        mf.search(stack, case["sigma"], table, mask=case["mask"], frame_scale=fs, workspace=ws, out=(smax, amax, None))
+        torch.cuda.synchronize()
+        mf.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            mf.search(stack, case["sigma"], table, mask=case["mask"], frame_scale=fs, workspace=ws,
+                      out=(smax, amax, None))
+            raw, n = mf.rescore_topk(master, case["sigma"], table, smax, amax, K_TOP, mask=case["mask"])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        prof = mf.profile_read(reset=True)
+        num_ms = prof["k_numerator"][1] / max(1, prof["k_numerator"][0])
+        g_max = smax.cpu().numpy()[ys, xs].astype(np.float64)
+        err = np.abs(g_max - o_max) / np.maximum(1.0, np.abs(o_max))
+        cands = mf.decode_candidates(raw, int(n.item()))
+        top = cands[:64]
+        Nc, Dc = oracle.search_points(res_host, lam, sh, tp, top["y"], top["x"], top["k"])
+        rerr = np.abs(top["snr"] - Nc / np.sqrt(Dc)) / np.maximum(1.0, np.abs(Nc / np.sqrt(Dc)))
+        serr = np.abs(top["snr_search"] - Nc / np.sqrt(Dc)) / np.maximum(1.0, np.abs(Nc / np.sqrt(Dc)))
+        out[name] = {"value": units / (ms * 1e-3), "ms_per_step": ms, "numerator_ms": num_ms,
+                     "frac": units * FLOP_PER_UNIT / (num_ms * 1e-3) / 1e12 / peak_tf,
+                     "stack_gb": stack.numel() * stack.element_size() / 1e9,
+                     "snr_max_rel_err_vs_fp64_oracle": {"max": float(err.max()), "median": float(np.median(err))},
+                     "search_snr_of_top64_rel_err": float(serr.max()),
+                     "fp64_rescore_of_top64_rel_err": float(rerr.max())}
+    line = {"metric": "traj*pixel*frame/s, precision forms at %dx%d^2x%d traj" % (T, H, K), "value": out["bf16"]["value"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": out["bf16"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 storage (f32 and f16 alongside), f32 arithmetic", "data": "synthetic",
+            "config": {"workload": "precision form: %d frames x %dx%d, %d trajectories (40x25 grid), "
+                                   "search + top-%d FP64 rescore from the FP32 master" % (T, H, W, K, K_TOP),
+                       "error_sample": "%d random start pixels x all trajectories, FP64 oracle on the FP32 master "
+                                       "(%.1f s)" % (n_px, oracle_s)},
+            "forms": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,7 +642,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rescore", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["search", "batch", "serve"], default="search",
+    ap.add_argument("--workload", choices=["search", "batch", "serve", "precision"], default="search",
                     help="search: the paper-shaped search (default); batch / serve: the batched and serving forms")
     ap.add_argument("--items", type=int, default=64, help="batch: cutouts in the batch")
     ap.add_argument("--pool", type=int, default=16, help="serve: distinct pregenerated requests")
@@ -562,6 +650,7 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: admission budget")
     ap.add_argument("--streams", type=int, default=4, help="serve: searches in flight")
+    ap.add_argument("--sample-px", type=int, default=256, help="precision: start pixels checked against the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -571,6 +660,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 

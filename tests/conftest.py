@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
-    config.addinivalue_line("markers", "slow: long-running check")
+    config.addinivalue_line("markers", "slow: long-running check (full paper-shaped size)")
 
 
 @pytest.fixture(scope="session")
