@@ -221,18 +221,31 @@ __global__ void __launch_bounds__(256) k_denominator(const float *__restrict__ l
                 v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
                 v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
             }
-            for (int ch = 0; ch < rr.nch; ch++) {
-                const float4 p2 = __ldg(row + 2 * ch + 2), p3 = __ldg(row + 2 * ch + 3);
-                v[8] = p2.x; v[9] = p2.y; v[10] = p2.z; v[11] = p2.w;
-                v[12] = p3.x; v[13] = p3.y; v[14] = p3.z; v[15] = p3.w;
-                const float4 w0 = __ldg(wp + 2 * ch), w1 = __ldg(wp + 2 * ch + 1);
-                const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            // two chunks per step with the halves of v swapping roles, so the
+            // sliding window needs no register moves
+            for (int ch = 0; ch < rr.nch; ch += 2) {
+                {
+                    const float4 p2 = __ldg(row + 2 * ch + 2), p3 = __ldg(row + 2 * ch + 3);
+                    v[8] = p2.x; v[9] = p2.y; v[10] = p2.z; v[11] = p2.w;
+                    v[12] = p3.x; v[13] = p3.y; v[14] = p3.z; v[15] = p3.w;
+                    const float4 w0 = __ldg(wp + 2 * ch), w1 = __ldg(wp + 2 * ch + 1);
+                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-                for (int i = 0; i < 8; i++)
+                    for (int i = 0; i < 8; i++)
 #pragma unroll
-                    for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[i + c], a[c]);
+                        for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[i + c], a[c]);
+                }
+                if (ch + 1 < rr.nch) {
+                    const float4 p2 = __ldg(row + 2 * ch + 4), p3 = __ldg(row + 2 * ch + 5);
+                    v[0] = p2.x; v[1] = p2.y; v[2] = p2.z; v[3] = p2.w;
+                    v[4] = p3.x; v[5] = p3.y; v[6] = p3.z; v[7] = p3.w;
+                    const float4 w0 = __ldg(wp + 2 * ch + 2), w1 = __ldg(wp + 2 * ch + 3);
+                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-                for (int c = 0; c < 8; c++) v[c] = v[c + 8];
+                    for (int i = 0; i < 8; i++)
+#pragma unroll
+                        for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[(8 + i + c) & 15], a[c]);
+                }
             }
             taps += rr.nch * 8;
             if (taps >= kDenTaps) {
@@ -422,9 +435,14 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
     int kk = -1;
     bool bad = false;
     bool next_ready = false;  // frame t's data already seen complete during frame t - 1
+    // lane's offset in a window; stage and barrier phase advance incrementally
+    const int lane_off = (kTile * sty + kMicroRows * ty) * p.S + kTile * stx + kMicroCols * tx + skew;
+    int s = 0;
+    uint32_t par = 0;
     for (int t = 0; t < p.T; t++) {
-        const int s = t % NS;
-        const bool ready = next_ready || mbar_wait(smem_u32(&bars[s]), (uint32_t)((t / NS) & 1), 1);
+        const int s1 = (s + 1 == NS) ? 0 : s + 1;            // stage and phase of frame t + 1
+        const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
+        const bool ready = next_ready || mbar_wait(smem_u32(&bars[s]), par, 1);
         if (!ready && !p.lockstep) {
             bad = true;
             break;
@@ -434,8 +452,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
         kk = rec->k;
         // Look at the next frame's barrier now: the check's latency then hides
         // behind this frame's arithmetic instead of stalling the next frame.
-        next_ready = !p.lockstep && t + 1 < p.T &&
-                     mbar_test_wait(smem_u32(&bars[(t + 1) % NS]), (uint32_t)(((t + 1) / NS) & 1));
+        next_ready = !p.lockstep && t + 1 < p.T && mbar_test_wait(smem_u32(&bars[s1]), par1);
         if (ready && kk >= 0 && inside) {
             float w[28];
             const float4 *w4 = reinterpret_cast<const float4 *>(rec->taps);
@@ -449,9 +466,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
             }
             const int offy = __float_as_int(w[25]);
             const int offx = __float_as_int(w[26]);
-            const float *base = win + (size_t)s * win_floats +
-                                (offy + kTile * sty + kMicroRows * ty) * p.S + offx + kTile * stx +
-                                kMicroCols * tx + skew;
+            const float *base = win + (size_t)s * win_floats + offy * p.S + offx + lane_off;
             stencil_dispatch<VEC>(base, offx & (VEC - 1), p.S, w, blk);
         }
         if ((t + 1) % kFrameBlock == 0) {
@@ -474,6 +489,8 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
                 fence_proxy_async();
                 issue(t + NS, s, h);
             }
+            s = s1;
+            par = par1;
             continue;
         }
         // Release stage s; the last warp to release it loads frame t + NS.
@@ -490,6 +507,8 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
                 }
             }
         }
+        s = s1;
+        par = par1;
     }
     if (bad) atomicExch(bad_flag, 1);
     __syncthreads();
