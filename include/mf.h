@@ -117,18 +117,38 @@ typedef struct mf_prf_table mf_prf_table;
 mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy,
                               int32_t K, int32_t T, mf_prf_table **out);
 
-/* Kernel-layout choices for a table (not in the paper).  shape selects how a
- * numerator CTA's 16 warps split between trajectories and 32 x 32 sub-tiles:
- * 0: 16 trajectories x 1 sub-tile, 1: 8 x (1 x 2), 2: 4 x (2 x 2),
- * 3: 2 x (2 x 4) (rows x columns of sub-tiles); -1 lets the planner's cost
- * model choose.
- * An autotuner times several shapes and keeps the fastest. */
+/* Kernel-layout choices for a table (not in the paper).
+ *
+ * kernel selects the numerator: 1 = the general kernel, 25 FMAs per
+ * (trajectory, pixel, frame), for any footprint; 2 = the factored kernel for
+ * separable footprints W(a, b) = u_x(a) u_y(b) (every table built by
+ * mf_prf_table_create is separable): a 5-tap pass along rows, shared by the
+ * trajectories of a CTA that have the same v_x, then a 5-tap pass down
+ * columns per trajectory; 0 = automatic (factored whenever the table is
+ * separable and the frame windows fit).  Both give the same sums up to FP32
+ * rounding.
+ *
+ * General kernel: shape selects how a CTA's 16 warps split between
+ * trajectories and 32 x 32 sub-tiles: 0: 16 trajectories x 1 sub-tile,
+ * 1: 8 x (1 x 2), 2: 4 x (2 x 2), 3: 2 x (2 x 4) (rows x columns of
+ * sub-tiles); -1 lets the planner's cost model choose.  A shape >= 0 with
+ * kernel = 0 selects the general kernel.
+ *
+ * Factored kernel: group = trajectories per CTA (all with one v_x), tile_h a
+ * multiple of 32, tile_w 32 or 64, with group * tile_h / 32 * tile_w / 32 <= 16
+ * warps; stages = frame windows in flight (2..6); 0 = planner's choice.
+ * An autotuner times several layouts and keeps the fastest. */
 typedef struct {
     int32_t shape;
-    int32_t vec;         /* floats per shared-memory load in the numerator: 1, 2, 4; 0 = default */
-    int32_t lockstep;    /* numerator frame hand-off: 1 = CTA barrier per frame, 0 = last warp
-                            out refills the stage, -1 = default */
-    int32_t reserved[5];
+    int32_t vec;         /* floats per shared-memory load in the general numerator: 1, 2, 4;
+                            0 = default */
+    int32_t lockstep;    /* general numerator frame hand-off: 1 = CTA barrier per frame, 0 = last
+                            warp out refills the stage, -1 = default */
+    int32_t kernel;      /* 0 automatic, 1 general, 2 factored */
+    int32_t group;       /* factored: trajectories per CTA, 0 = automatic */
+    int32_t tile_h;      /* factored: output rows per CTA, 0 = automatic */
+    int32_t tile_w;      /* factored: output columns per CTA, 0 = automatic */
+    int32_t stages;      /* factored: frame windows in flight, 0 = automatic */
 } mf_plan_opts;
 
 /* mf_prf_table_create with layout options (opts NULL = automatic).
@@ -177,6 +197,8 @@ typedef struct {
     double cost;              /* planner's estimate, SM cycles per start pixel */
     int32_t vec;              /* floats per shared-memory load in the numerator */
     int32_t lockstep;         /* numerator frame hand-off (see mf_plan_opts) */
+    int32_t kernel;           /* numerator: 1 general, 2 factored (see mf_plan_opts) */
+    int32_t stages;           /* frame windows in flight per CTA */
 } mf_table_info;
 
 /* Layout of an existing table. */

@@ -1,4 +1,4 @@
-"""Build libmf.so in-tree with nvcc for sm_103a (no cmake, two translation
+"""Build libmf.so in-tree with nvcc for sm_103a (no cmake, the translation
 units compiled in parallel).  Used by ``__graft_entry__.build()``."""
 from __future__ import annotations
 
@@ -11,7 +11,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmf.so")
-SOURCES = ["mf_kernels.cu", "mf_host.cpp", "mf_noalloc.cu"]
+SOURCES = ["mf_kernels.cu", "mf_factored.cu", "mf_host.cpp", "mf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -24,7 +24,7 @@ def nvcc() -> str:
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "mf_internal.h"), os.path.join(PKG, "..", "include", "mf.h")]
+    files += [os.path.join(CSRC, "mf_internal.h"), os.path.join(CSRC, "mf_device.cuh"), os.path.join(PKG, "..", "include", "mf.h")]
     return files
 
 

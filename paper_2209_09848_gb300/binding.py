@@ -48,16 +48,23 @@ CANDIDATE_BYTES = ctypes.sizeof(Candidate)
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("vec", ctypes.c_int32), ("lockstep", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("kernel", ctypes.c_int32), ("group", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
-def _opts(shape=None, vec=None, lockstep=None):
-    if shape is None and vec is None and lockstep is None:
+_LAYOUT_KEYS = ("shape", "vec", "lockstep", "kernel", "group", "tile_h", "tile_w", "stages")
+
+
+def _opts(**kw):
+    """mf_plan_opts from keyword layout options; None when all are None."""
+    if all(kw.get(k) is None for k in _LAYOUT_KEYS):
         return None
     o = PlanOpts()
-    o.shape = -1 if shape is None else int(shape)
-    o.vec = 0 if vec is None else int(vec)
-    o.lockstep = -1 if lockstep is None else int(lockstep)
+    o.shape = -1 if kw.get("shape") is None else int(kw["shape"])
+    o.vec = 0 if kw.get("vec") is None else int(kw["vec"])
+    o.lockstep = -1 if kw.get("lockstep") is None else int(kw["lockstep"])
+    for k in ("kernel", "group", "tile_h", "tile_w", "stages"):
+        setattr(o, k, 0 if kw.get(k) is None else int(kw[k]))
     return ctypes.byref(o)
 
 
@@ -68,7 +75,7 @@ class TableInfo(ctypes.Structure):
                 ("window_rows", ctypes.c_int32), ("segments", ctypes.c_int32),
                 ("max_abs_shift", ctypes.c_int32), ("g_nnz", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("cost", ctypes.c_double), ("vec", ctypes.c_int32),
-                ("lockstep", ctypes.c_int32)]
+                ("lockstep", ctypes.c_int32), ("kernel", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -196,35 +203,45 @@ class PrfTable:
             pass
 
 
-def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, shape=None, vec=None, lockstep=None) -> PrfTable:
-    """mf_prf_table_create / mf_prf_table_create_ex (shape = CTA layout, None = automatic)."""
+def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> PrfTable:
+    """mf_prf_table_create, or mf_prf_table_create_ex when layout options are
+    given: shape, vec, lockstep (general numerator), kernel (1 general,
+    2 factored), group, tile_h, tile_w, stages (factored numerator); None or
+    absent = automatic."""
     import numpy as np
+    bad = set(layout) - set(_LAYOUT_KEYS)
+    if bad:
+        raise TypeError("unknown layout option(s) %s" % sorted(bad))
     vx = np.ascontiguousarray(vx, np.float64)
     vy = np.ascontiguousarray(vy, np.float64)
     if vx.shape != vy.shape or vx.ndim != 1:
         raise ValueError("vx and vy must be 1-D of equal length")
     prm = PrfParams(int(kind), 0, float(sigma_px))
     h = ctypes.c_void_p()
-    if shape is None and vec is None and lockstep is None:
+    opts = _opts(**layout)
+    if opts is None:
         _check(load().mf_prf_table_create(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
                                           vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
                                           ctypes.byref(h)))
     else:
         _check(load().mf_prf_table_create_ex(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
                                              vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
-                                             _opts(shape, vec, lockstep), ctypes.byref(h)))
+                                             opts, ctypes.byref(h)))
     return PrfTable(h)
 
 
-def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, shape=None, vec=None, lockstep=None) -> dict:
+def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> dict:
     """mf_prf_plan: host-only layout of a Gaussian-PRF filter bank (no GPU needed)."""
     import numpy as np
+    bad = set(layout) - set(_LAYOUT_KEYS)
+    if bad:
+        raise TypeError("unknown layout option(s) %s" % sorted(bad))
     vx = np.ascontiguousarray(vx, np.float64)
     vy = np.ascontiguousarray(vy, np.float64)
     prm = PrfParams(int(kind), 0, float(sigma_px))
     inf = TableInfo()
     _check(load().mf_prf_plan(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                              vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T), _opts(shape, vec, lockstep),
+                              vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T), _opts(**layout),
                               ctypes.byref(inf)))
     return inf.as_dict()
 

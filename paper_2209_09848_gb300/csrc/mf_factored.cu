@@ -1,0 +1,240 @@
+// Factored numerator of the matched filter (Section 3.2, Eq. 5) for
+// separable footprints, sm_103a.
+//
+// N_k(p) = sum_t sum_{a,b} u_x(a) u_y(b) y_t(p + s_{k,t} + (a, b)) is computed
+// per frame as a row pass H(i, c) = sum_a u_x(a) R(i, c + a) over the staged
+// window R, then a column pass N += sum_b u_y(b) H(i + b, c).  The row pass
+// depends on the trajectory only through s_x and u_x, which every trajectory
+// of a CTA shares (they have one v_x), so it is made once per frame for the
+// whole CTA; the column pass is per trajectory.  Per (trajectory, pixel,
+// frame) this costs 5 FMAs plus the row pass's share, against 25 FMAs for the
+// general 5 x 5 stencil; the arithmetic is the same sum regrouped.
+//
+// Per frame: every thread waits for the frame's window (TMA box, mbarrier
+// with a bounded wait), the CTA's threads split the row pass into items of 12
+// outputs, one CTA barrier, thread 0 refills the window's stage with frame
+// t + stages, and each warp runs the column pass of its (trajectory slot,
+// 32 x 32 sub-tile).  The row-pass buffer is double-buffered, so one barrier
+// per frame orders both its writes and its reuse.  FP32 throughout, with the
+// blocked accumulation of the general kernel (partials over 16 frames).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "mf_device.cuh"
+#include "mf_internal.h"
+
+namespace mf {
+namespace {
+
+using namespace dev;
+
+template <int TW>
+__global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant__ CUtensorMap ymap,
+                                                          const FacParams p) {
+    constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / 12;
+    constexpr int R = kFacRecordChunk;
+    constexpr int NSUBX = TW / 32;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+
+    const int NS = p.ns, BH = p.bh, KT = p.kt;
+    const int g = (int)(blockIdx.x % (unsigned)p.G), tile = (int)(blockIdx.x / (unsigned)p.G);
+    const int tile_y0 = (tile / p.tiles_x) * p.th;
+    const int tile_x0 = (tile % p.tiles_x) * TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nsub = (p.th / 32) * NSUBX;
+    // a slot's warps are consecutive, so they spread over the SM's four
+    // schedulers and an empty slot leaves every scheduler the same work
+    const int slot = warp / nsub, sub = warp % nsub;
+    const int sub_y = sub / NSUBX, sub_x = sub % NSUBX;
+    const uint32_t kBB = (uint32_t)fac_block_bytes(KT);
+
+    const int SF = fac_stage_floats(TW, BH);                              // stage stride, 128-byte multiple
+    float *rwin = reinterpret_cast<float *>(smem);                       // [NS][SF] windows of BH x RP
+    float *hbuf = rwin + (size_t)NS * SF;                                 // [2][BH][HP]
+    unsigned char *fb = reinterpret_cast<unsigned char *>(hbuf + (size_t)2 * BH * HP);  // [2][R] blocks
+    uint64_t *bars = reinterpret_cast<uint64_t *>(fb + 2 * R * kBB);
+    int *last_issued = reinterpret_cast<int *>(bars + NS);
+    int *bad_flag = last_issued + NS;
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem);  // epilogue reuses the windows
+
+    const unsigned char *gblocks = p.blocks + (size_t)g * p.T * kBB;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            last_issued[s] = -1;
+        }
+        *bad_flag = status_now(p.status);  // an earlier CTA gave up: do not start
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (*bad_flag != 0) return;  // same value for every thread of the CTA
+
+    const uint32_t box_bytes = (uint32_t)BH * RP * 4;
+    auto issue = [&](int f, int s, int roy, int rox) {
+        const uint32_t bar = smem_u32(&bars[s]);
+        const int nrec = (f % R == 0) ? min(R, p.T - f) : 0;  // the chunk's records ride on its first frame
+        mbar_expect_tx(bar, box_bytes + (uint32_t)nrec * kBB);
+        tma_load_3d(smem_u32(rwin + (size_t)s * SF), &ymap, tile_x0 + rox, tile_y0 + roy, f, bar);
+        if (nrec)
+            bulk_load(smem_u32(fb + ((f / R) & 1) * R * kBB), gblocks + (size_t)f * kBB, (uint32_t)nrec * kBB, bar);
+        last_issued[s] = f;
+    };
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        for (int s = 0; s < NS && s < p.T; s++) {
+            const FrameHdr h = p.hdr[(size_t)g * p.T + s];
+            issue(s, s, h.roy, h.rox);
+        }
+    }
+
+    const int kk = p.members[(size_t)g * KT + slot];
+    const bool active = kk >= 0 && tile_y0 + 32 * sub_y < p.H && tile_x0 + 32 * sub_x < p.W;
+    float acc[32], blk[32];
+#pragma unroll
+    for (int r = 0; r < 32; r++) {
+        acc[r] = 0.f;
+        blk[r] = 0.f;
+    }
+    bool bad = false;
+    int s = 0;
+    uint32_t par = 0;
+    for (int t = 0; t < p.T; t++) {
+        const bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
+        const unsigned char *fblk = fb + (((t / R) & 1) * R + t % R) * kBB;
+        const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
+        float *hb = hbuf + (size_t)(t & 1) * BH * HP;
+        if (ready) {
+            // row pass: item (row, m) -> 12 outputs H(row, 12m .. 12m + 11);
+            // consecutive threads take consecutive rows
+            const int nrows = fh->nrows;
+            const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
+            const float *rs = rwin + (size_t)s * SF;
+            for (int it = threadIdx.x; it < nrows * NI; it += blockDim.x) {
+                const int m = it / nrows, row = it - m * nrows;
+                const float4 *src = reinterpret_cast<const float4 *>(rs + row * RP + 12 * m);
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float4 x = src[q];
+                    v[4 * q] = x.x;
+                    v[4 * q + 1] = x.y;
+                    v[4 * q + 2] = x.z;
+                    v[4 * q + 3] = x.w;
+                }
+                float o[12];
+#pragma unroll
+                for (int c = 0; c < 12; c++) {
+                    float h = ux0 * v[c];
+                    h = fmaf(ux1, v[c + 1], h);
+                    h = fmaf(ux2, v[c + 2], h);
+                    h = fmaf(ux3, v[c + 3], h);
+                    o[c] = fmaf(ux4, v[c + 4], h);
+                }
+                float4 *dst = reinterpret_cast<float4 *>(hb + row * HP + 12 * m);
+#pragma unroll
+                for (int q = 0; q < 3; q++) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            }
+        }
+        if (__syncthreads_or(!ready)) {
+            bad = true;
+            break;
+        }
+        // every thread is done with stage s: refill it with frame t + NS
+        if (threadIdx.x == 0 && t + NS < p.T) {
+            fence_proxy_async();
+            issue(t + NS, s, fh->next_roy, fh->next_rox);
+        }
+        if (active) {
+            const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
+            const float uy0 = fs->uy[0], uy1 = fs->uy[1], uy2 = fs->uy[2], uy3 = fs->uy[3], uy4 = fs->uy[4];
+            const float *col = hb + (32 * sub_y + fs->oy) * HP + 32 * sub_x + lane + fh->cofs;
+#pragma unroll
+            for (int i = 0; i < 36; i++) {
+                const float h = col[i * HP];
+                if (i < 32) blk[i] = fmaf(uy0, h, blk[i]);
+                if (i >= 1 && i - 1 < 32) blk[i - 1] = fmaf(uy1, h, blk[i - 1]);
+                if (i >= 2 && i - 2 < 32) blk[i - 2] = fmaf(uy2, h, blk[i - 2]);
+                if (i >= 3 && i - 3 < 32) blk[i - 3] = fmaf(uy3, h, blk[i - 3]);
+                if (i >= 4) blk[i - 4] = fmaf(uy4, h, blk[i - 4]);
+            }
+        }
+        if ((t + 1) % kFrameBlock == 0) {
+#pragma unroll
+            for (int r = 0; r < 32; r++) {
+                acc[r] += blk[r];
+                blk[r] = 0.f;
+            }
+        }
+        if (++s == NS) {
+            s = 0;
+            par ^= 1u;
+        }
+    }
+    if (bad) {
+        // let any copy still in flight land before the CTA's shared memory goes away
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < NS; q++) {
+                const int f = last_issued[q];
+                if (f >= 0) mbar_wait(smem_u32(&bars[q]), (uint32_t)((f / NS) & 1), 2, p.status);
+            }
+        }
+        return;
+    }
+
+    // Epilogue: SNR = N / sqrt(D); max over the CTA's trajectories in a tile
+    // of packed (SNR, k) keys, then one atomicMax per pixel.
+    const int TH = p.th;
+    for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) red[i] = 0ull;
+    __syncthreads();
+    const int64_t P = p.H * p.W;
+    const int64_t px = tile_x0 + 32 * sub_x + lane;
+    if (kk >= 0 && px < p.W) {
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            const int64_t py = tile_y0 + 32 * sub_y + r;
+            if (py < p.H) {
+                const int64_t q = py * p.W + px;
+                const float isd = p.isd[(int64_t)kk * P + q];
+                const float snr = (acc[r] + blk[r]) * isd;
+                if (p.snr_all) p.snr_all[(int64_t)kk * P + q] = isd > 0.f ? snr : 0.f;
+                if (isd > 0.f) atomicMax(&red[(32 * sub_y + r) * TW + 32 * sub_x + lane], pack_key(snr, kk));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
+        const unsigned long long key = red[i];
+        if (key == 0ull) continue;
+        const int64_t py = tile_y0 + i / TW, qx = tile_x0 + i % TW;
+        atomicMax(&p.keys[py * p.W + qx], key);
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NS; q++) mbar_inval(smem_u32(&bars[q]));
+}
+
+}  // namespace
+
+int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int warps, size_t smem, long long nblocks,
+                void *stream, char *err, size_t errlen) {
+    const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(tensor_map);
+    void (*kern)(const CUtensorMap, const FacParams) =
+        tw == 64 ? k_numerator_fac<64> : k_numerator_fac<32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
+        return (int)e;
+    }
+    if (nblocks <= 0) return 0;
+    kern<<<(unsigned)nblocks, warps * 32, smem, (cudaStream_t)stream>>>(map, p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "k_numerator_fac: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    return 0;
+}
+
+}  // namespace mf

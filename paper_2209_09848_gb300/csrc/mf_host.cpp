@@ -47,7 +47,11 @@ int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // 5x5 footprint of the PRF for a source at sub-pixel offset (phx, phy) from
 // the base pixel, renormalised to unit sum (Section 2: the PRF shares a point
 // source's flux between neighbouring pixels).
-void footprint(int kind, double sigma, double phx, double phy, double *w) {
+// When fx / fy are given they receive the normalised 1-D factors: w[b * 5 +
+// a] = fy[b] * fx[a] up to rounding (the 5 x 5 sum is the product of the two
+// 1-D sums).
+void footprint(int kind, double sigma, double phx, double phy, double *w, double *fx = nullptr,
+               double *fy = nullptr) {
     double gx[5], gy[5];
     if (kind == 0) {
         // pixel d spans [d - 1/2, d + 1/2]: six shared boundaries per axis
@@ -75,6 +79,17 @@ void footprint(int kind, double sigma, double phx, double phy, double *w) {
             total += w[b * 5 + a];
         }
     for (int i = 0; i < 25; i++) w[i] /= total;
+    if (fx && fy) {
+        double sx = 0.0, sy = 0.0;
+        for (int i = 0; i < 5; i++) {
+            sx += gx[i];
+            sy += gy[i];
+        }
+        for (int i = 0; i < 5; i++) {
+            fx[i] = gx[i] / sx;
+            fy[i] = gy[i] / sy;
+        }
+    }
 }
 
 // Balanced k-d split of the velocity set into `groups` parts of at most `cap`
@@ -230,6 +245,116 @@ mf_status plan_groups(mf_prf_table &t) {
     return MF_OK;
 }
 
+// Factored numerator: trajectories with the same v_x form a class (they
+// share s_x and u_x at every frame); each class, sorted by v_y, is split into
+// groups of consecutive members, one group per CTA.  For each candidate CTA
+// geometry (trajectories per CTA, tile) the window rows BH follow from the
+// largest s_y spread of a group, the stages from the shared-memory budget,
+// and the cost from a per-frame model of one CTA in SM cycles: FP32 FMAs of
+// both passes at 128 per cycle, or the shared-memory bytes they move at 128
+// per cycle, whichever is larger, plus a fixed cost for the frame barrier.
+// Returns false if the table is not separable or no geometry fits.
+bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
+    if (t.fx.empty() || t.vx.size() != (size_t)t.K) return false;
+    const int K = t.K, T = t.T;
+    std::map<double, std::vector<int>> cls;
+    for (int k = 0; k < K; k++) cls[t.vx[k]].push_back(k);
+    std::vector<std::vector<int>> classes;
+    for (auto &c : cls) {
+        std::vector<int> v = c.second;
+        std::sort(v.begin(), v.end(), [&](int a, int b) { return t.vy[a] != t.vy[b] ? t.vy[a] < t.vy[b] : a < b; });
+        classes.push_back(std::move(v));
+    }
+    struct Geo {
+        int kt, th, tw;
+    };
+    std::vector<Geo> geos;
+    for (int tw : {32, 64}) {
+        if (t.forced_tw && tw != t.forced_tw) continue;
+        for (int kt = 1; kt <= 16; kt++) {
+            if (t.forced_group && kt != t.forced_group) continue;
+            const int per = kt * (tw / 32);  // warps per 32 rows of tile
+            if (per > 16) continue;
+            if (t.forced_th) {
+                if (t.forced_th / 32 * per <= 16) geos.push_back({kt, t.forced_th, tw});
+            } else {
+                for (int th = std::min(224, 32 * (16 / per)); th >= 32; th -= 32) geos.push_back({kt, th, tw});
+            }
+        }
+    }
+    bool have = false;
+    for (const Geo &geo : geos) {
+        mf::Plan p;
+        p.kernel = 2;
+        p.f_kt = geo.kt;
+        p.f_th = geo.th;
+        p.f_tw = geo.tw;
+        std::vector<std::vector<int>> groups;
+        for (const auto &c : classes) {
+            const int n = (int)c.size();
+            const int ng = (n + geo.kt - 1) / geo.kt;
+            for (int g = 0, i = 0; g < ng; g++) {
+                const int sz = n / ng + (g < n % ng ? 1 : 0);
+                groups.emplace_back(c.begin() + i, c.begin() + i + sz);
+                i += sz;
+            }
+        }
+        // rows of each (group, frame) and the window height
+        std::vector<int> nrows(groups.size() * (size_t)T);
+        int bh = 0;
+        for (size_t g = 0; g < groups.size(); g++)
+            for (int f = 0; f < T; f++) {
+                int mn = INT32_MAX, mx = INT32_MIN;
+                for (int k : groups[g]) {
+                    const int sy = t.shifts[((size_t)k * T + f) * 2 + 1];
+                    mn = std::min(mn, sy);
+                    mx = std::max(mx, sy);
+                }
+                nrows[g * T + f] = geo.th + 4 + (mx - mn);
+                bh = std::max(bh, nrows[g * T + f]);
+            }
+        if (bh > 256) continue;
+        int ns = 0;
+        for (int c = t.forced_stages ? t.forced_stages : mf::kFacMaxStages; c >= 2; c--) {
+            if (mf::fac_smem_bytes(geo.tw, bh, c, geo.kt) <= (size_t)mf::kSmemBudget &&
+                (size_t)c * mf::fac_stage_floats(geo.tw, bh) * 4 >= (size_t)geo.th * geo.tw * 8) {
+                ns = c;
+                break;
+            }
+            if (t.forced_stages) break;
+        }
+        if (ns == 0) continue;
+        p.f_ns = ns;
+        p.f_bh = bh;
+        const double hc = mf::fac_hcols(geo.tw), rp = mf::fac_rpitch(geo.tw);
+        const double sub = (geo.th / 32) * (geo.tw / 32);
+        double cyc = 0.0;
+        for (size_t g = 0; g < groups.size(); g++) {
+            const double n = (double)groups[g].size();
+            for (int f = 0; f < T; f++) {
+                const double nr = nrows[g * T + f];
+                const double fma = (n * geo.th * geo.tw * 5.0 + nr * hc * 5.0) / 128.0;
+                const double sm = (n * sub * 36.0 * 128.0 + nr * (hc / 12.0) * 112.0 + bh * rp * 4.0) / 128.0;
+                cyc += std::max(fma, sm) / 0.8 + 200.0;
+            }
+        }
+        p.cost = cyc / ((double)geo.th * geo.tw);
+        p.G = (int)groups.size();
+        p.members.assign((size_t)p.G * geo.kt, -1);
+        for (size_t g = 0; g < groups.size(); g++)
+            for (size_t i = 0; i < groups[g].size(); i++) p.members[g * geo.kt + i] = groups[g][i];
+        if (!have || p.cost < out.cost) {
+            out = std::move(p);
+            have = true;
+        }
+    }
+    if (!have) return false;
+    int mx = 0;
+    for (size_t i = 0; i < t.shifts.size(); i++) mx = std::max(mx, std::abs(t.shifts[i]));
+    out.max_abs_shift = mx;
+    return true;
+}
+
 template <class T>
 mf_status upload(T **dst, const T *src, size_t n) {
     if (n == 0) {
@@ -252,17 +377,45 @@ struct HostLayouts {
 };
 
 size_t layout_bytes(const mf_prf_table *t, const HostLayouts &h) {
-    return h.blocks.size() + h.hdr.size() * sizeof(mf::FrameHdr) + h.runs.size() * sizeof(mf::RunRec) +
+    return h.blocks.size() + h.hdr.size() * sizeof(mf::FrameHdr) + t->plan.members.size() * sizeof(int32_t) +
+           h.runs.size() * sizeof(mf::RunRec) +
            h.run_off.size() * sizeof(int32_t) + h.wts.size() * sizeof(float) + t->taps.size() * sizeof(double) +
            t->shifts.size() * sizeof(int32_t);
 }
 
+void general_layouts(mf_prf_table *t, HostLayouts &out);
+void fac_layouts(mf_prf_table *t, HostLayouts &out);
+void denominator_layouts(mf_prf_table *t, HostLayouts &out);
+
 // Plan the groups and build the layouts the kernels read: frame headers and
-// blocks (numerator), constant-shift runs (denominator).
+// blocks (numerator), constant-shift runs (denominator).  The factored
+// numerator is used whenever the table is separable and a layout fits,
+// unless the options ask for the general one.
 mf_status host_layouts(mf_prf_table *t, HostLayouts &out) {
-    mf_status s = plan_groups(*t);
-    if (s != MF_OK) return s;
-    const int K = t->K, T = t->T;
+    bool factored = false;
+    if (t->forced_kernel != 1) {
+        mf::Plan fp;
+        factored = plan_factored(*t, fp);
+        if (factored) t->plan = std::move(fp);
+        else if (t->forced_kernel == 2)
+            return fail(t->fx.empty() ? MF_EINVAL : MF_EUNSUPPORTED,
+                        t->fx.empty() ? "the factored numerator needs a separable (Gaussian PRF) table"
+                                      : "no factored layout holds these trajectories' frame windows");
+    }
+    if (factored) {
+        fac_layouts(t, out);
+    } else {
+        mf_status s = plan_groups(*t);
+        if (s != MF_OK) return s;
+        general_layouts(t, out);
+    }
+    denominator_layouts(t, out);
+    return MF_OK;
+}
+
+// Frame headers and blocks of the general numerator.
+void general_layouts(mf_prf_table *t, HostLayouts &out) {
+    const int T = t->T;
     const mf::Plan &p = t->plan;
     const int kt = p.kt();
     std::vector<mf::FrameHdr> hdr((size_t)p.G * T);
@@ -307,6 +460,74 @@ mf_status host_layouts(mf_prf_table *t, HostLayouts &out) {
             }
         }
     }
+    out.hdr = std::move(hdr);
+    out.blocks = std::move(blocks);
+}
+
+// Frame headers and blocks of the factored numerator: per (group, frame) the
+// window origin (rows from min s_y - 2, columns from s_x - 2 rounded down to
+// a multiple of 4 for the TMA box), the row-pass rows, u_x, and per slot u_y
+// and the slot's row offset in the row-pass buffer.
+void fac_layouts(mf_prf_table *t, HostLayouts &out) {
+    const int T = t->T;
+    const mf::Plan &p = t->plan;
+    const int kt = p.f_kt;
+    std::vector<mf::FrameHdr> hdr((size_t)p.G * T);
+    for (int g = 0; g < p.G; g++) {
+        const int k0 = p.members[(size_t)g * kt];
+        for (int f = 0; f < T; f++) {
+            int mny = INT32_MAX, mxy = INT32_MIN;
+            for (int w = 0; w < kt; w++) {
+                const int k = p.members[(size_t)g * kt + w];
+                if (k < 0) continue;
+                mny = std::min(mny, t->shifts[((size_t)k * T + f) * 2 + 1]);
+                mxy = std::max(mxy, t->shifts[((size_t)k * T + f) * 2 + 1]);
+            }
+            const int64_t sx = t->shifts[((size_t)k0 * T + f) * 2 + 0];
+            mf::FrameHdr &h = hdr[(size_t)g * T + f];
+            h.roy = mny - 2;
+            h.rox = (int32_t)(4 * floor_div(sx - 2, 4));
+            h.nrows = p.f_th + 4 + (mxy - mny);
+            h.pad = (int32_t)(sx - 2 - h.rox);  // column phase
+        }
+    }
+    const size_t bb = mf::fac_block_bytes(kt);
+    std::vector<unsigned char> blocks((size_t)p.G * T * bb, 0);
+    for (int g = 0; g < p.G; g++) {
+        const int k0 = p.members[(size_t)g * kt];
+        for (int f = 0; f < T; f++) {
+            unsigned char *b = blocks.data() + ((size_t)g * T + f) * bb;
+            const mf::FrameHdr &h = hdr[(size_t)g * T + f];
+            mf::FacHdr fh;
+            std::memset(&fh, 0, sizeof fh);
+            if (f + p.f_ns < T) {
+                fh.next_roy = hdr[(size_t)g * T + f + p.f_ns].roy;
+                fh.next_rox = hdr[(size_t)g * T + f + p.f_ns].rox;
+            }
+            fh.cofs = h.pad;
+            fh.nrows = h.nrows;
+            for (int a = 0; a < 5; a++) fh.ux[a] = (float)t->fx[((size_t)k0 * T + f) * 5 + a];
+            std::memcpy(b, &fh, sizeof fh);
+            for (int w = 0; w < kt; w++) {
+                const int k = p.members[(size_t)g * kt + w];
+                mf::FacSlot fs;
+                std::memset(&fs, 0, sizeof fs);
+                if (k >= 0) {
+                    const size_t ktf = (size_t)k * T + f;
+                    for (int c = 0; c < 5; c++) fs.uy[c] = (float)t->fy[ktf * 5 + c];
+                    fs.oy = t->shifts[ktf * 2 + 1] - 2 - h.roy;
+                }
+                std::memcpy(b + sizeof fh + (size_t)w * sizeof fs, &fs, sizeof fs);
+            }
+        }
+    }
+    out.hdr = std::move(hdr);
+    out.blocks = std::move(blocks);
+}
+
+// Denominator layout: constant-shift runs of the collapsed kernels.
+void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
+    const int K = t->K, T = t->T;
     // Denominator: lambda does not depend on t, so D_k(p) = sum_u G_k(u)
     // lambda(p + u) with the collapsed kernel G_k(u) = sum over (t, a, b)
     // with s_{k,t} + (a, b) = u of W_{k,t}(a, b)^2, summed here in FP64.
@@ -393,12 +614,9 @@ mf_status host_layouts(mf_prf_table *t, HostLayouts &out) {
     run_off[K] = (int32_t)runs.size();
     t->n_seg = (int)runs.size();
     t->g_nnz = nnz_total;
-    out.hdr = std::move(hdr);
-    out.blocks = std::move(blocks);
     out.runs = std::move(runs);
     out.run_off = std::move(run_off);
     out.wts = std::move(wts);
-    return MF_OK;
 }
 
 mf_status finish_table(mf_prf_table *t) {
@@ -407,6 +625,7 @@ mf_status finish_table(mf_prf_table *t) {
     if (s != MF_OK) return s;
     if ((s = upload(&t->d_blocks, h.blocks.data(), h.blocks.size())) != MF_OK) return s;
     if ((s = upload(&t->d_hdr, h.hdr.data(), h.hdr.size())) != MF_OK) return s;
+    if ((s = upload(&t->d_members, t->plan.members.data(), t->plan.members.size())) != MF_OK) return s;
     if ((s = upload(&t->d_runs, h.runs.data(), h.runs.size())) != MF_OK) return s;
     if ((s = upload(&t->d_run_off, h.run_off.data(), h.run_off.size())) != MF_OK) return s;
     if ((s = upload(&t->d_wts, h.wts.data(), h.wts.size())) != MF_OK) return s;
@@ -424,21 +643,25 @@ void fill_info(const mf_prf_table *t, mf_table_info *info) {
     info->warps_per_group = t->plan.kt();
     info->tile_h = t->plan.tile_h();
     info->tile_w = t->plan.tile_w();
-    info->window_pitch = t->plan.S;
-    info->window_rows = t->plan.BH;
+    const bool fac = t->plan.kernel == 2;
+    info->window_pitch = fac ? mf::fac_rpitch(t->plan.f_tw) : t->plan.S;
+    info->window_rows = fac ? t->plan.f_bh : t->plan.BH;
     info->segments = t->n_seg;
     info->g_nnz = t->g_nnz;
     info->max_abs_shift = t->plan.max_abs_shift;
-    info->smem_bytes = (int64_t)mf::numerator_smem_bytes(t->plan.S, t->plan.BH, t->plan.kt());
+    info->smem_bytes = (int64_t)t->plan.smem();
     info->cost = t->plan.cost;
-    info->vec = t->plan.vec;
-    info->lockstep = t->plan.lockstep;
+    info->vec = fac ? 1 : t->plan.vec;
+    info->lockstep = fac ? 1 : t->plan.lockstep;
+    info->kernel = t->plan.kernel;
+    info->stages = fac ? t->plan.f_ns : mf::kStages;
     info->device_bytes = (int64_t)t->device_bytes;
 }
 
 void free_device(mf_prf_table *t) {
     cudaFree(t->d_blocks);
     cudaFree(t->d_hdr);
+    cudaFree(t->d_members);
     cudaFree(t->d_runs);
     cudaFree(t->d_run_off);
     cudaFree(t->d_wts);
@@ -446,6 +669,7 @@ void free_device(mf_prf_table *t) {
     cudaFree(t->d_shifts);
     t->d_blocks = nullptr;
     t->d_hdr = nullptr;
+    t->d_members = nullptr;
     t->d_runs = nullptr;
     t->d_run_off = nullptr;
     t->d_wts = nullptr;
@@ -540,6 +764,10 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
     t->T = T;
     t->shifts.resize((size_t)K * T * 2);
     t->taps.resize((size_t)K * T * 25);
+    t->fx.resize((size_t)K * T * 5);
+    t->fy.resize((size_t)K * T * 5);
+    t->vx.assign(vx, vx + K);
+    t->vy.assign(vy, vy + K);
     for (int k = 0; k < K; k++) {
         for (int f = 0; f < T; f++) {
             // position after f frames, base pixel floor(c + 1/2), phase c - s
@@ -550,7 +778,8 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
             const size_t kt = (size_t)k * T + f;
             t->shifts[kt * 2 + 0] = (int32_t)sx;
             t->shifts[kt * 2 + 1] = (int32_t)sy;
-            footprint(prf->kind, prf->sigma_px, cx - sx, cy - sy, &t->taps[kt * 25]);
+            footprint(prf->kind, prf->sigma_px, cx - sx, cy - sy, &t->taps[kt * 25], &t->fx[kt * 5],
+                      &t->fy[kt * 5]);
         }
     }
     *out_t = t;
@@ -567,9 +796,26 @@ static mf_status apply_opts(mf_prf_table *t, const mf_plan_opts *opts) {
         delete t;
         return fail(MF_EINVAL, "vec %d must be 0, 1, 2 or 4", opts->vec);
     }
+    if (opts->kernel < 0 || opts->kernel > 2) {
+        delete t;
+        return fail(MF_EINVAL, "kernel %d must be 0, 1 or 2", opts->kernel);
+    }
+    if (opts->group < 0 || opts->group > 16 || opts->tile_h < 0 || opts->tile_h % 32 != 0 ||
+        (opts->tile_w != 0 && opts->tile_w != 32 && opts->tile_w != 64) || opts->stages < 0 ||
+        opts->stages == 1 || opts->stages > mf::kFacMaxStages) {
+        delete t;
+        return fail(MF_EINVAL, "factored layout group=%d tile_h=%d tile_w=%d stages=%d out of range", opts->group,
+                    opts->tile_h, opts->tile_w, opts->stages);
+    }
     t->forced_shape = opts->shape;
     t->forced_vec = opts->vec;
     t->forced_lockstep = opts->lockstep;
+    t->forced_kernel = opts->kernel;
+    if (opts->kernel == 0 && opts->shape >= 0) t->forced_kernel = 1;
+    t->forced_group = opts->group;
+    t->forced_th = opts->tile_h;
+    t->forced_tw = opts->tile_w;
+    t->forced_stages = opts->stages;
     return MF_OK;
 }
 

@@ -70,7 +70,59 @@ struct alignas(16) RunRec {
     int32_t dy, x0, nch, woff;  // woff: index of the first weight (multiple of 4)
 };
 
+// ------------------------------------------------ factored numerator ---
+// When every footprint factors as W(a, b) = u_x(a) u_y(b) (the Gaussian PRF
+// tables do: the pixel-integrated Gaussian is a product of two erf
+// differences, and so is its 5 x 5 renormalisation), the numerator runs as a
+// 5-tap pass along rows with u_x into a row-pass buffer H, then a 5-tap pass
+// down columns of H with u_y.  Trajectories with the same v_x have the same
+// s_x and u_x at every frame, so a CTA holding several of them (different
+// v_y) makes the row pass once per frame for all of them.
+//
+// CTA: (slots per CTA) x (tile_h / 32) x (tile_w / 32) warps, each warp one
+// (trajectory slot, 32 x 32 sub-tile); lane = output column, 32 rows per
+// lane.  The staged window R of a frame is a TMA box of fac_rpitch(tile_w)
+// columns (the box is as wide as the row pitch) and BH rows.
+struct alignas(16) FacHdr {
+    int32_t next_roy, next_rox;  // window origin of frame t + stages, relative to the tile origin
+    int32_t cofs;                // row-pass column of output column 0 (0..3)
+    int32_t nrows;               // row-pass rows this frame needs
+    float ux[5];                 // u_x(a), a = -2..2
+    int32_t pad[3];
+};
+static_assert(sizeof(FacHdr) == 48, "FacHdr is 48 bytes");
+struct alignas(16) FacSlot {
+    float uy[5];  // u_y(b), b = -2..2
+    int32_t oy;   // row-pass row of (tile row 0 + s_y - 2)
+    int32_t pad[2];
+};
+static_assert(sizeof(FacSlot) == 32, "FacSlot is 32 bytes");
+__host__ __device__ inline size_t fac_block_bytes(int kt) { return sizeof(FacHdr) + (size_t)kt * sizeof(FacSlot); }
+// Row-pass outputs per row: tile_w + 4 (column phase 0..3 plus footprint),
+// in items of 12; each item reads 16 window values.  Both pitches are odd
+// multiples of 4 floats, so 8 lanes on 8 consecutive rows hit 8 distinct
+// 16-byte bank groups with 128-bit accesses.
+__host__ __device__ constexpr int fac_hcols(int tw) { return (tw + 4 + 11) / 12 * 12; }
+__host__ __device__ constexpr int fac_odd4(int n) { return (n / 4) % 2 ? n : n + 4; }
+__host__ __device__ constexpr int fac_hpitch(int tw) { return fac_odd4(fac_hcols(tw)); }
+__host__ __device__ constexpr int fac_rpitch(int tw) { return fac_odd4(fac_hcols(tw) + 4); }
+constexpr int kFacMaxStages = 6;
+// Frame records arrive in chunks of kFacRecordChunk frames (one bulk copy per
+// chunk, two chunk buffers); a chunk buffer is refilled while frame t + stages
+// is issued, so kFacRecordChunk >= kFacMaxStages keeps frame t's chunk intact.
+constexpr int kFacRecordChunk = 8;
+static_assert(kFacRecordChunk >= kFacMaxStages, "record chunks must outlive the frames in flight");
+// Floats of one window stage, rounded to 128 bytes (TMA destination alignment).
+__host__ __device__ constexpr int fac_stage_floats(int tw, int bh) { return (bh * fac_rpitch(tw) + 31) / 32 * 32; }
+inline size_t fac_smem_bytes(int tw, int bh, int ns, int kt) {
+    return 1024 + (size_t)ns * fac_stage_floats(tw, bh) * sizeof(float) +
+           2 * (size_t)bh * fac_hpitch(tw) * sizeof(float) + 2 * (size_t)kFacRecordChunk * fac_block_bytes(kt) +
+           (size_t)ns * (sizeof(uint64_t) + sizeof(int)) + sizeof(int) + 64;
+}
+
 struct Plan {
+    int kernel = 1;       // 1: general 5 x 5 numerator, 2: factored numerator
+    int f_kt = 0, f_th = 0, f_tw = 0, f_ns = 0, f_bh = 0;  // factored numerator geometry
     int shape = 0;        // index into kShapes
     int vec = 2;          // width of the numerator's shared-memory loads (1, 2 or 4 floats)
     int lockstep = 0;     // numerator frame hand-off: 1 = CTA barrier per frame
@@ -80,9 +132,11 @@ struct Plan {
     int max_abs_shift = 0;
     double cost = 0.0;    // planner estimate, cycles per output pixel
     std::vector<int32_t> members;  // G * kt original k, or -1
-    int kt() const { return kShapes[shape].kt; }
-    int tile_h() const { return kTile * kShapes[shape].tys; }
-    int tile_w() const { return kTile * kShapes[shape].txs; }
+    int kt() const { return kernel == 2 ? f_kt : kShapes[shape].kt; }
+    int tile_h() const { return kernel == 2 ? f_th : kTile * kShapes[shape].tys; }
+    int tile_w() const { return kernel == 2 ? f_tw : kTile * kShapes[shape].txs; }
+    int warps() const { return kernel == 2 ? f_kt * (f_th / 32) * (f_tw / 32) : kWarps; }
+    size_t smem() const;
 };
 
 // Dynamic shared memory of the numerator kernel: windows (the key tile of the
@@ -92,6 +146,10 @@ inline size_t numerator_smem_bytes(int S, int BH, int kt) {
            (size_t)kStages * sizeof(uint64_t) + 3 * kStages * sizeof(int) + sizeof(int) + 64;
 }
 
+inline size_t Plan::smem() const {
+    return kernel == 2 ? fac_smem_bytes(f_tw, f_bh, f_ns, f_kt) : numerator_smem_bytes(S, BH, kt());
+}
+
 }  // namespace mf
 
 struct mf_prf_table {
@@ -99,7 +157,14 @@ struct mf_prf_table {
     int device = 0;
     std::vector<int32_t> shifts;  // K*T*2, (s_x, s_y)
     std::vector<double> taps;     // K*T*25
+    // factors of separable footprints, W(a, b) = fx(a) fy(b) (empty when the
+    // table was given as explicit footprints), and the velocities that group
+    // trajectories sharing the row pass
+    std::vector<double> fx, fy;   // K*T*5
+    std::vector<double> vx, vy;   // K
     mf::Plan plan;
+    int forced_kernel = 0;  // 0: automatic, 1: general, 2: factored
+    int forced_group = 0, forced_th = 0, forced_tw = 0, forced_stages = 0;  // factored geometry, 0: automatic
     int forced_shape = -1;  // -1: cost model
     int forced_vec = 0;     // 0: default
     int forced_lockstep = -1;
@@ -107,7 +172,8 @@ struct mf_prf_table {
     int64_t g_nnz = 0;      // nonzero weights of the collapsed kernels
     size_t device_bytes = 0;
     // device copies
-    unsigned char *d_blocks = nullptr;   // [G][T] frame blocks of frame_block_bytes(kt)
+    unsigned char *d_blocks = nullptr;   // [G][T] frame blocks (frame_block_bytes or fac_block_bytes)
+    int32_t *d_members = nullptr;        // [G][kt] trajectory of each slot, -1 for none
     mf::FrameHdr *d_hdr = nullptr;       // [G][T]
     mf::RunRec *d_runs = nullptr;        // [n_seg]
     int32_t *d_run_off = nullptr;        // [K + 1]
@@ -171,6 +237,26 @@ size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top);
 int launch_rescore(const RescoreArgs &a, char *err, size_t errlen);
 
 int read_device_status(int *status);
+
+// Device address of the status word that bounded waits write on giving up.
+int *status_word(char *err, size_t errlen);
+
+// Factored numerator (mf_factored.cu).  The tensor map covers the weighted
+// stack y [T][H][y_pitch] with a box of fac_rpitch(tile_w) x f_bh x 1.
+struct FacParams {
+    const unsigned char *blocks;  // [G][T] blocks of fac_block_bytes(kt)
+    const FrameHdr *hdr;          // [G][T] window origins (pad = column phase)
+    const int32_t *members;       // [G][kt] trajectory of each slot, -1 for none
+    const float *isd;             // [K][H][W] 1 / sqrt(D)
+    unsigned long long *keys;     // [H][W] packed (SNR, k)
+    float *snr_all;               // [K][H][W] or null
+    int *status;                  // device status word
+    int T, G, kt, th, bh, ns;
+    int64_t H, W;
+    int tiles_x;
+};
+int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int warps, size_t smem, long long nblocks,
+                void *stream, char *err, size_t errlen);
 
 // Record an error message for mf_last_error() and return the status.
 mf_status set_error(mf_status s, const char *msg);

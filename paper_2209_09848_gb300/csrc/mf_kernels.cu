@@ -28,6 +28,7 @@
 #include <mutex>
 #include <vector>
 
+#include "mf_device.cuh"
 #include "mf_internal.h"
 
 namespace mf {
@@ -37,97 +38,12 @@ __device__ int g_status;
 
 namespace {
 
-constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
+using namespace dev;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ int status_now() { return dev::status_now(&g_status); }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Non-blocking check of a phase (acquire on success).
-__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ int status_now() { return *(volatile int *)&g_status; }
-
-// Wait for a phase of an mbarrier, giving up after kWaitCycles or as soon as
-// another CTA has recorded a failure; on giving up the device status word
-// records `code` (if nothing was recorded before).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (unsigned it = 1;; it++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && status_now() != 0) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            atomicCAS(&g_status, 0, code);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_inval(uint32_t bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-// Order-preserving 64-bit key: larger SNR first, then smaller k.  Any valid
-// key is nonzero, so 0 means "no filter with D > 0".
-__device__ __forceinline__ unsigned long long pack_key(float snr, int k) {
-    uint32_t b = __float_as_uint(snr);
-    b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-    return ((unsigned long long)b << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)k);
+    return dev::mbar_wait(bar, parity, code, &g_status);
 }
 
 template <typename T>
@@ -842,6 +758,50 @@ int numerator_params(const SearchArgs &a, CUtensorMap *map, NumParams *np, int *
     return 0;
 }
 
+// Tensor map and parameters of the factored numerator; *nblocks = CTAs.
+int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *nblocks, char *err,
+               size_t errlen) {
+    const mf_stack &st = *a.stack;
+    const mf_prf_table &tab = *a.tab;
+    const Plan &pl = tab.plan;
+    const WorkspaceLayout &L = a.L;
+    const int64_t T = st.T, H = st.H, W = st.W;
+    int rc = get_encode(err, errlen);
+    if (rc) return rc;
+    int *status = status_word(err, errlen);
+    if (!status) return (int)cudaErrorInvalidSymbol;
+    float *y = reinterpret_cast<float *>(a.ws + L.y_off);
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
+    cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * 4, (cuuint64_t)(H * L.y_pitch * 4)};
+    cuuint32_t box[3] = {(cuuint32_t)fac_rpitch(pl.f_tw), (cuuint32_t)pl.f_bh, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+        return (int)cudaErrorInvalidValue;
+    }
+    fp->blocks = tab.d_blocks;
+    fp->hdr = tab.d_hdr;
+    fp->members = tab.d_members;
+    fp->isd = reinterpret_cast<float *>(a.ws + L.isd_off);
+    fp->keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
+    fp->snr_all = a.snr_all;
+    fp->status = status;
+    fp->T = (int)T;
+    fp->G = pl.G;
+    fp->kt = pl.f_kt;
+    fp->th = pl.f_th;
+    fp->bh = pl.f_bh;
+    fp->ns = pl.f_ns;
+    fp->H = H;
+    fp->W = W;
+    fp->tiles_x = (int)((W + pl.f_tw - 1) / pl.f_tw);
+    *nblocks = (long long)pl.G * fp->tiles_x * ((H + pl.f_th - 1) / pl.f_th);
+    return 0;
+}
+
 typedef void (*NumKernel)(const CUtensorMap, const NumParams);
 typedef void (*NumBatchKernel)(const CUtensorMap *, const BatchItem *, int, long long, unsigned long long *);
 
@@ -891,6 +851,16 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
     int rc = enqueue_pre(a, stream, err, errlen);
     if (rc) return rc;
     CUtensorMap map;
+    if (pl.kernel == 2) {
+        FacParams fp;
+        long long nblocks = 0;
+        rc = fac_params(a, &map, &fp, &nblocks, err, errlen);
+        if (rc) return rc;
+        LaunchScope ls(kKNumerator, stream);
+        rc = fac_enqueue(&map, fp, pl.f_tw, pl.warps(), pl.smem(), nblocks, stream, err, errlen);
+        if (rc) return rc;
+        return enqueue_finalize(a, stream, err, errlen);
+    }
     NumParams np;
     int tiles_y = 0;
     rc = numerator_params(a, &map, &np, &tiles_y, err, errlen);
@@ -928,6 +898,13 @@ struct BatchDevice {
     };
     std::vector<Group> groups;
     std::vector<int> order;  // device-array position -> item
+    struct FacLaunch {
+        int item = 0;
+        CUtensorMap map;
+        FacParams p;
+        long long nblocks = 0;
+    };
+    std::vector<FacLaunch> fac;  // items with a factored numerator, one launch each
     CUtensorMap *d_maps = nullptr;
     BatchItem *d_items = nullptr;
     unsigned long long *d_counters = nullptr;
@@ -960,7 +937,7 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         grp.first = (int)bitems.size();
         for (int i = 0; i < n; i++) {
             const Plan &pl = items[i].tab->plan;
-            if (pl.shape != shape) continue;
+            if (pl.kernel != 1 || pl.shape != shape) continue;
             CUtensorMap m;
             BatchItem bi;
             std::memset(&bi, 0, sizeof bi);
@@ -978,6 +955,17 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         }
         grp.count = (int)bitems.size() - grp.first;
         if (grp.count > 0) b->groups.push_back(grp);
+    }
+    for (int i = 0; i < n; i++) {
+        if (items[i].tab->plan.kernel != 2) continue;
+        BatchDevice::FacLaunch fl;
+        fl.item = i;
+        int rc = fac_params(items[i], &fl.map, &fl.p, &fl.nblocks, err, errlen);
+        if (rc) {
+            batch_free(b);
+            return rc;
+        }
+        b->fac.push_back(fl);
     }
     cudaError_t e = cudaSuccess;
     int dev = 0;
@@ -1036,6 +1024,12 @@ int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream_v
         pick_numerator_batch(grp.shape)<<<grid, kWarps * 32, grp.smem, stream>>>(
             b->d_maps + grp.first, b->d_items + grp.first, grp.count, grp.total, b->d_counters + grp.shape);
         MF_CHECK_LAUNCH("k_numerator_batch");
+    }
+    for (const auto &fl : b->fac) {
+        const Plan &pl = items[fl.item].tab->plan;
+        LaunchScope ls(kKNumerator, stream);
+        int rc = fac_enqueue(&fl.map, fl.p, pl.f_tw, pl.warps(), pl.smem(), fl.nblocks, stream, err, errlen);
+        if (rc) return rc;
     }
     for (int i = 0; i < n; i++) {
         int rc = enqueue_finalize(items[i], stream, err, errlen);
@@ -1349,6 +1343,29 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
     }
     MF_CHECK_LAUNCH("k_rescore");
     return 0;
+}
+
+int *status_word(char *err, size_t errlen) {
+    static std::mutex mu;
+    static std::vector<int *> addr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "cudaGetDevice: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_status);
+        if (e != cudaSuccess) {
+            snprintf(err, errlen, "cudaGetSymbolAddress(status word): %s", cudaGetErrorString(e));
+            return nullptr;
+        }
+        addr[dev] = static_cast<int *>(p);
+    }
+    return addr[dev];
 }
 
 int read_device_status(int *status) {

@@ -181,3 +181,77 @@ def test_every_cta_shape(mf, oracle, shape, vec, lockstep):
     N, D = oracle.search_full(c["res"], lam, sh, tp)
     smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
     check_search(smax, amax, sall, N, D, oracle, label="shape %d" % shape)
+
+
+FACTORED = [
+    # group, tile_h, tile_w, stages (0 = planner's choice)
+    (1, 0, 32, 0),
+    (1, 0, 64, 0),
+    (2, 0, 64, 2),
+    (3, 0, 32, 0),
+    (4, 128, 32, 4),
+    (5, 96, 32, 6),
+    (6, 64, 32, 5),
+    (8, 64, 32, 3),
+    (16, 32, 32, 2),
+    (2, 32, 64, 0),
+]
+
+
+@pytest.mark.parametrize("group,tile_h,tile_w,stages", FACTORED)
+def test_factored_layouts(mf, oracle, group, tile_h, tile_w, stages):
+    """The factored numerator (row pass shared by the trajectories of one v_x,
+    column pass per trajectory) gives the oracle's answer for every CTA
+    geometry and stage count, on a ragged frame spanning several tiles, with
+    more frames than a record chunk and a frame block, and a grid whose v_y
+    spread makes the window rows differ from frame to frame."""
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 40, 203, 157
+    c = synth.small_case(T, H, W, 60 + group, mask_frac=0.02, movers=3)
+    gx = np.array([-0.61, -0.2, 0.05, 0.33, 0.9])
+    gy = np.linspace(-0.8, 0.7, 7)
+    vx = np.repeat(gx, gy.size)
+    vy = np.tile(gy, gx.size)
+    table = mf.prf_table_create(vx, vy, T, kernel=2, group=group, tile_h=tile_h or None, tile_w=tile_w,
+                                stages=stages or None)
+    info = table.info()
+    assert info["kernel"] == 2 and info["warps_per_group"] == group and info["tile_w"] == tile_w
+    if tile_h:
+        assert info["tile_h"] == tile_h
+    if stages:
+        assert info["stages"] == stages
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    check_search(smax, amax, sall, N, D, oracle, label="factored %s" % ((group, tile_h, tile_w, stages),))
+
+
+def test_factored_is_default_and_matches_general(mf):
+    """Tables built from velocities use the factored numerator by default; the
+    general kernel on the same table gives the same SNR up to FP32 rounding
+    and the same argmax."""
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 30, 130, 170
+    c = synth.small_case(T, H, W, 77, mask_frac=0.01, movers=4)
+    vx, vy = synth.velocity_grid(6, 5, -0.3, 0.3)
+    fac = mf.prf_table_create(vx, vy, T)
+    gen = mf.prf_table_create(vx, vy, T, kernel=1)
+    assert fac.info()["kernel"] == 2 and gen.info()["kernel"] == 1
+    a = _run(mf, c["res"], c["sigma"], c["mask"], fac)
+    b = _run(mf, c["res"], c["sigma"], c["mask"], gen)
+    assert np.all(np.abs(a[0] - b[0]) <= 2e-5 * np.maximum(1, np.abs(b[0])))
+    assert np.all(np.abs(a[2] - b[2]) <= 2e-5 * np.maximum(1, np.abs(b[2])))
+    top2 = np.sort(b[2], axis=0)[-2:]
+    clear = (top2[1] - top2[0]) > 1e-3
+    assert np.array_equal(a[1][clear], b[1][clear])
+
+
+def test_factored_needs_separable_table(mf):
+    g = np.random.default_rng(5)
+    sh = g.integers(-3, 4, size=(3, 4, 2)).astype(np.int32)
+    tp = g.uniform(0, 1, size=(3, 4, 5, 5))
+    t = mf.prf_table_create_custom(sh, tp)
+    assert t.info()["kernel"] == 1
+    with pytest.raises(mf.MFError):
+        mf.prf_table_create(np.zeros(2), np.zeros(2), 4, kernel=2, group=17)

@@ -1,0 +1,78 @@
+"""Host-only planning of filter-bank layouts (mf_prf_plan: no GPU needed).
+
+The factored numerator needs separable footprints and groups trajectories
+that share v_x; these tests check the planner's choices and its limits."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2209_09848_gb300 as m
+    m.load()
+    return m
+
+
+def _grid(nx, ny, lo=-0.1, hi=0.1):
+    from paper_2209_09848_gb300 import synth
+    return synth.velocity_grid(nx, ny, lo, hi)
+
+
+def test_paper_grid_plans_factored(mf):
+    vx, vy = _grid(10, 10)
+    info = mf.prf_plan(vx, vy, 1000)
+    assert info["kernel"] == 2
+    kt, th, tw = info["warps_per_group"], info["tile_h"], info["tile_w"]
+    assert kt * (th // 32) * (tw // 32) <= 16 and th % 32 == 0 and tw in (32, 64)
+    # groups never mix v_x: each of the 10 columns of the grid splits on its own
+    assert info["groups"] == 10 * -(-10 // kt)
+    assert info["window_rows"] <= 256 and info["smem_bytes"] <= 227 * 1024
+    assert 2 <= info["stages"] <= 6
+
+
+def test_general_kernel_on_request(mf):
+    vx, vy = _grid(10, 10)
+    info = mf.prf_plan(vx, vy, 1000, kernel=1)
+    assert info["kernel"] == 1 and info["warps_per_group"] in (16, 8, 4, 2)
+    info = mf.prf_plan(vx, vy, 1000, shape=2)
+    assert info["kernel"] == 1 and info["warps_per_group"] == 4
+
+
+def test_distinct_vx_gives_single_trajectory_groups(mf):
+    g = np.random.default_rng(3)
+    vx = g.uniform(-0.1, 0.1, 40)
+    vy = g.uniform(-0.1, 0.1, 40)
+    info = mf.prf_plan(vx, vy, 500)
+    assert info["kernel"] == 2 and info["groups"] == 40  # one trajectory per CTA
+
+
+def test_forced_geometry_is_reported(mf):
+    vx, vy = _grid(10, 10)
+    info = mf.prf_plan(vx, vy, 1000, kernel=2, group=4, tile_h=128, tile_w=32, stages=3)
+    assert (info["warps_per_group"], info["tile_h"], info["tile_w"], info["stages"]) == (4, 128, 32, 3)
+    assert info["groups"] == 30
+    # rows: tile + footprint + the largest s_y spread of a group; the 10 v_y
+    # of a column split into groups of 4, 3 and 3 consecutive values
+    gy = np.linspace(-0.1, 0.1, 10)
+    s_last = np.floor(gy * 999 + 0.5)
+    spread = max(s_last[j - 1] - s_last[i] for i, j in ((0, 4), (4, 7), (7, 10)))
+    assert info["window_rows"] == 128 + 4 + spread
+
+
+@pytest.mark.parametrize("opts", [dict(kernel=3), dict(kernel=2, group=17), dict(kernel=2, tile_h=48),
+                                  dict(kernel=2, tile_w=96), dict(kernel=2, stages=1), dict(kernel=2, stages=7)])
+def test_invalid_layout_options(mf, opts):
+    vx, vy = _grid(3, 3)
+    with pytest.raises(mf.MFError) as e:
+        mf.prf_plan(vx, vy, 10, **opts)
+    assert e.value.status == 1
+
+
+def test_window_too_tall_is_unsupported(mf):
+    # 10 v_y spanning 2 px/frame over 140 frames: no group of 10 fits 256 rows
+    vx, vy = _grid(2, 10, -1.0, 1.0)
+    with pytest.raises(mf.MFError) as e:
+        mf.prf_plan(vx, vy, 140, kernel=2, group=10)
+    assert e.value.status == 5
+    info = mf.prf_plan(vx, vy, 140)  # the planner splits the columns instead
+    assert info["kernel"] == 2 and info["window_rows"] <= 256
