@@ -37,7 +37,7 @@ METRIC = "traj*pixel*frame/s at 1000x2048^2x100 traj"
 UNIT = "traj*pixel*frame/s"
 T_FR, HH, WW, NXG, NYG, VMAX = 1000, 2048, 2048, 10, 10, 0.1
 K_TOP = 4096
-FLOP_PER_UNIT = 50  # 25 FP32 FMAs per (trajectory, pixel, frame): the general 5x5 footprint
+FLOP_PER_UNIT_GENERAL = 50  # 25 FP32 FMAs per (trajectory, pixel, frame): the general 5x5 footprint
 SM_COUNT, FP32_LANES = 152, 128
 
 
@@ -134,9 +134,26 @@ def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> flo
     return units_per_rank * world / seconds_max
 
 
-def _traffic_from_profiles():
-    """DRAM bytes per numerator launch from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "k_numerator_paper_shaped.md")
+def flop_per_unit(kernel: int, vx) -> float:
+    """Algorithmic FP32 flops per (trajectory, pixel, frame) of the numerator
+    form the plan uses.  General 5 x 5 footprint: 25 FMAs.  Factored form
+    (separable footprint): a 5-tap column pass per trajectory, plus a 5-tap
+    row pass shared by all trajectories with the same v_x, i.e. 5 * C / K
+    FMAs per unit for C distinct v_x among K trajectories (halo rows and
+    columns, and classes split over several CTAs, are overhead, not
+    algorithmic work)."""
+    if kernel != 2:
+        return float(FLOP_PER_UNIT_GENERAL)
+    K = len(vx)
+    C = len(set(float(v) for v in vx))
+    return 2.0 * (5.0 + 5.0 * C / K)
+
+
+def _traffic_from_profiles(kernel: int = 2):
+    """DRAM bytes per numerator launch from the committed ncu summary of the
+    kernel the plan uses, if any."""
+    name = "k_numerator_fac_paper_shaped.md" if kernel == 2 else "k_numerator_paper_shaped.md"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             for line in f:
@@ -265,7 +282,7 @@ def run_ours(args):
     case = synth.paper_case_gpu(T=T, H=H, W=W, seed=1 + rank, device=dev)
     vx, vy = synth.velocity_grid(NXG, NYG, -args.vmax, args.vmax)
     K = len(vx)
-    table = mf.prf_table_create(vx, vy, T)
+    table = mf.prf_table_create(vx, vy, T, kernel=args.kernel or None)
     info = table.info()
     res, sigma, mask = case["res"], case["sigma"], case["mask"]
     ws_search = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
@@ -313,8 +330,9 @@ def run_ours(args):
     num_launches, num_ms_total = prof["k_numerator"]
     num_ms = num_ms_total / max(1, num_launches)
     peak_tf = _fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-    achieved_tf = units_rank * FLOP_PER_UNIT / (num_ms * 1e-3) / 1e12
-    traffic = _traffic_from_profiles()
+    fpu = flop_per_unit(info["kernel"], vx)
+    achieved_tf = units_rank * fpu / (num_ms * 1e-3) / 1e12
+    traffic = _traffic_from_profiles(info["kernel"])
     kernel_ms = {k: round(v[1] / max(1, v[0]), 3) for k, v in prof.items() if k != "_launches" and v[0]}
     launches = int(prof["_launches"])
 
@@ -374,14 +392,15 @@ def run_ours(args):
                                        T, H, W, K, NXG, NYG, args.vmax, K_TOP),
                        "frames": T, "height": H, "width": W, "trajectories": K,
                        "l2": "inputs larger than L2 (%.1f GB stack per step)" % (T * H * W * 4 / 1e9),
-                       "plan": {k: info[k] for k in ("groups", "warps_per_group", "tile_h", "tile_w",
-                                                      "window_pitch", "window_rows", "vec")},
+                       "plan": {k: info[k] for k in ("kernel", "groups", "warps_per_group", "tile_h", "tile_w",
+                                                      "window_pitch", "window_rows", "stages")},
                        "parallelism": "weak scaling: independent stack per GPU" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_numerator", "achieved": achieved_tf, "peak": peak_tf,
+            "roofline": {"bound": "alu", "kernel": "k_numerator_fac" if info["kernel"] == 2 else "k_numerator",
+                         "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s)" % (
                              float(peaks.get("sm_max_mhz", 2070.0)), peak_src),
-                         "flop_per_unit": FLOP_PER_UNIT, "avg_launch_ms": num_ms},
+                         "flop_per_unit": fpu, "avg_launch_ms": num_ms},
             "kernel_ms": kernel_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -611,7 +630,7 @@ def run_precision(args):
         rerr = np.abs(top["snr"] - Nc / np.sqrt(Dc)) / np.maximum(1.0, np.abs(Nc / np.sqrt(Dc)))
         serr = np.abs(top["snr_search"] - Nc / np.sqrt(Dc)) / np.maximum(1.0, np.abs(Nc / np.sqrt(Dc)))
         out[name] = {"value": units / (ms * 1e-3), "ms_per_step": ms, "numerator_ms": num_ms,
-                     "frac": units * FLOP_PER_UNIT / (num_ms * 1e-3) / 1e12 / peak_tf,
+                     "frac": units * flop_per_unit(table.info()["kernel"], vx) / (num_ms * 1e-3) / 1e12 / peak_tf,
                      "stack_gb": stack.numel() * stack.element_size() / 1e9,
                      "snr_max_rel_err_vs_fp64_oracle": {"max": float(err.max()), "median": float(np.median(err))},
                      "search_snr_of_top64_rel_err": float(serr.max()),
@@ -642,6 +661,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rescore", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
+                    help="numerator: 0 planner's choice, 1 general 5x5, 2 factored")
     ap.add_argument("--workload", choices=["search", "batch", "serve", "precision"], default="search",
                     help="search: the paper-shaped search (default); batch / serve: the batched and serving forms")
     ap.add_argument("--items", type=int, default=64, help="batch: cutouts in the batch")

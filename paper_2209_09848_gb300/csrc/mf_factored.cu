@@ -112,8 +112,9 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
             const int nrows = fh->nrows;
             const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
             const float *rs = rwin + (size_t)s * SF;
+            const float rn = 1.0f / (float)nrows;  // m = floor((it + 1/2) / nrows): exact, it < 2^16
             for (int it = threadIdx.x; it < nrows * NI; it += blockDim.x) {
-                const int m = it / nrows, row = it - m * nrows;
+                const int m = (int)(((float)it + 0.5f) * rn), row = it - m * nrows;
                 const float4 *src = reinterpret_cast<const float4 *>(rs + row * RP + 12 * m);
                 float v[16];
 #pragma unroll
