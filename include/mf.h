@@ -325,8 +325,9 @@ mf_status mf_batch_add(mf_batch *batch, const mf_stack *stack, const float *sigm
 mf_status mf_batch_workspace_size(const mf_batch *batch, size_t *bytes);
 mf_status mf_batch_prepare(mf_batch *batch, void *workspace, size_t workspace_bytes);
 mf_status mf_batch_run(mf_batch *batch, mf_stream stream);
-/* Number of searches, of distinct CTA shapes (persistent launches) and
- * whether the graph has been captured. */
+/* Number of searches, of persistent numerator launches (one per general
+ * CTA shape and one per factored tile width present) and whether the graph
+ * has been captured. */
 mf_status mf_batch_info(const mf_batch *batch, int32_t *items, int32_t *shape_groups, int32_t *graph_ready);
 void mf_batch_destroy(mf_batch *batch);
 

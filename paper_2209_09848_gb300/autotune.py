@@ -1,11 +1,12 @@
-"""Autotuner for the numerator's CTA layout (not in the paper).
+"""Autotuner for the numerator's layout (not in the paper).
 
-For a filter bank and a cutout size it times every layout the library can
-hold in shared memory -- CTA shape (trajectories per CTA x 32 x 32 sub-tiles)
-and frame hand-off (last-warp refill or CTA barrier) -- on a sample stack of
-the same frame count and dtype, and keeps the fastest.  Results are cached
-per (frames, sample size, trajectories, dtype, velocity span) bucket, so a
-stream of similar requests is tuned once.  Timing uses CUDA events around
+For a filter bank and a cutout size it times candidate layouts the library
+can hold in shared memory -- the factored numerator with the planner's
+geometry and with each tile width, and the general numerator with the
+planner's CTA shape and with each frame hand-off -- on a sample stack of the
+same frame count and dtype, and keeps the fastest.  Results are cached per
+(frames, sample size, trajectories, dtype, velocity span) bucket, so a stream
+of similar requests is tuned once.  Timing uses CUDA events around
 mf_search; every candidate runs the library's kernels.
 """
 from __future__ import annotations
@@ -17,7 +18,13 @@ import torch
 
 from . import binding as mf
 
-CANDIDATES = [(shape, lock) for shape in (0, 1, 2, 3) for lock in (0, 1)]
+CANDIDATES = [
+    {"kernel": 2},
+    {"kernel": 2, "tile_w": 32},
+    {"kernel": 2, "tile_w": 64},
+    {"kernel": 1, "lockstep": 0},
+    {"kernel": 1, "lockstep": 1},
+]
 _cache: dict = {}
 _lock = threading.Lock()
 
@@ -29,8 +36,9 @@ def _key(vx, vy, T, H, W, dtype, crop):
 
 
 def tune(vx, vy, T, H, W, dtype=torch.float32, crop=512, reps=2, sigma_px=0.7, device="cuda", verbose=False):
-    """Return (best options dict, timings {(shape, lockstep): ms}) for this
-    bank and cutout size; cached by bucket."""
+    """Return (best layout options, timings {candidate index: ms}) for this
+    bank and cutout size; cached by bucket.  The options are keyword
+    arguments of prf_table_create."""
     key = _key(vx, vy, T, H, W, dtype, crop)
     with _lock:
         if key in _cache:
@@ -41,11 +49,17 @@ def tune(vx, vy, T, H, W, dtype=torch.float32, crop=512, reps=2, sigma_px=0.7, d
     stack = torch.randn((T, h, w), generator=g, device=device).to(dtype)
     sigma = torch.ones((h, w), device=device)
     timings = {}
-    for shape, lock in CANDIDATES:
+    seen = set()
+    for i, opts in enumerate(CANDIDATES):
         try:
-            table = mf.prf_table_create(vx, vy, T, sigma_px=sigma_px, shape=shape, lockstep=lock)
+            table = mf.prf_table_create(vx, vy, T, sigma_px=sigma_px, **opts)
         except mf.MFError:
             continue  # this layout cannot hold the windows
+        inf = table.info()
+        sig = (inf["kernel"], inf["warps_per_group"], inf["tile_h"], inf["tile_w"], inf["lockstep"], inf["stages"])
+        if sig in seen:
+            continue  # the same layout as an earlier candidate
+        seen.add(sig)
         ws = torch.empty(mf.search_workspace_size((T, h, w), table), dtype=torch.uint8, device=device)
         out = (torch.empty((h, w), device=device), torch.empty((h, w), dtype=torch.int32, device=device), None)
         mf.search(stack, sigma, table, workspace=ws, out=out)
@@ -55,14 +69,14 @@ def tune(vx, vy, T, H, W, dtype=torch.float32, crop=512, reps=2, sigma_px=0.7, d
             mf.search(stack, sigma, table, workspace=ws, out=out)
         e1.record()
         torch.cuda.synchronize()
-        timings[(shape, lock)] = e0.elapsed_time(e1) / reps
+        timings[i] = e0.elapsed_time(e1) / reps
         del table, ws
     if not timings:
         raise mf.MFError(5, "no numerator layout fits this filter bank")
     best = min(timings, key=timings.get)
-    res = ({"shape": best[0], "lockstep": best[1]}, timings)
+    res = (dict(CANDIDATES[best]), timings)
     if verbose:
-        print("autotune", key, "->", best, {k: round(v, 3) for k, v in timings.items()})
+        print("autotune", key, "->", CANDIDATES[best], {i: round(v, 3) for i, v in timings.items()})
     with _lock:
         _cache[key] = res
     return res
@@ -71,7 +85,7 @@ def tune(vx, vy, T, H, W, dtype=torch.float32, crop=512, reps=2, sigma_px=0.7, d
 def tuned_table(vx, vy, T, H, W, dtype=torch.float32, sigma_px=0.7, **kw):
     """Filter bank built with the layout the autotuner picked."""
     opts, _ = tune(vx, vy, T, H, W, dtype=dtype, sigma_px=sigma_px, **kw)
-    return mf.prf_table_create(vx, vy, T, sigma_px=sigma_px, shape=opts["shape"], lockstep=opts["lockstep"])
+    return mf.prf_table_create(vx, vy, T, sigma_px=sigma_px, **opts)
 
 
 def clear_cache():

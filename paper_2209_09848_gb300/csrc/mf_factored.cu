@@ -30,17 +30,19 @@ namespace {
 
 using namespace dev;
 
+// The work of one CTA on one (output tile, trajectory group) of one search;
+// false if it gave up (a bounded wait ran out; the device status word says
+// why).  The CTA may have more warps than the search's layout uses (batched
+// searches share one launch): the extra warps take part in the row pass and
+// the barriers only.  `smem` is the CTA's 1024-aligned dynamic shared memory.
 template <int TW>
-__global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant__ CUtensorMap ymap,
-                                                          const FacParams p) {
+__device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParams &p, int g, int tile,
+                                         unsigned char *smem) {
     constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / 12;
     constexpr int R = kFacRecordChunk;
     constexpr int NSUBX = TW / 32;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
 
     const int NS = p.ns, BH = p.bh, KT = p.kt;
-    const int g = (int)(blockIdx.x % (unsigned)p.G), tile = (int)(blockIdx.x / (unsigned)p.G);
     const int tile_y0 = (tile / p.tiles_x) * p.th;
     const int tile_x0 = (tile % p.tiles_x) * TW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
         fence_barrier_init();
     }
     __syncthreads();
-    if (*bad_flag != 0) return;  // same value for every thread of the CTA
+    if (*bad_flag != 0) return false;  // same value for every thread of the CTA
 
     const uint32_t box_bytes = (uint32_t)BH * RP * 4;
     auto issue = [&](int f, int s, int roy, int rox) {
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
         }
     }
 
-    const int kk = p.members[(size_t)g * KT + slot];
+    const int kk = warp < p.warps ? p.members[(size_t)g * KT + slot] : -1;
     const bool active = kk >= 0 && tile_y0 + 32 * sub_y < p.H && tile_x0 + 32 * sub_x < p.W;
     float acc[32], blk[32];
 #pragma unroll
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
                 if (f >= 0) mbar_wait(smem_u32(&bars[q]), (uint32_t)((f / NS) & 1), 2, p.status);
             }
         }
-        return;
+        return false;
     }
 
     // Epilogue: SNR = N / sqrt(D); max over the CTA's trajectories in a tile
@@ -212,11 +214,84 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
         const int64_t py = tile_y0 + i / TW, qx = tile_x0 + i % TW;
         atomicMax(&p.keys[py * p.W + qx], key);
     }
+    // the barriers may be initialised again for this CTA's next tile
     if (threadIdx.x == 0)
         for (int q = 0; q < NS; q++) mbar_inval(smem_u32(&bars[q]));
+    return true;
+}
+
+template <int TW>
+__global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant__ CUtensorMap ymap,
+                                                          const FacParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    fac_tile<TW>(ymap, p, (int)(blockIdx.x % (unsigned)p.G), (int)(blockIdx.x / (unsigned)p.G), smem);
+}
+
+// Persistent factored numerator over a batch of searches: one CTA per SM
+// takes (search, tile, group) work entries from a global counter until the
+// list is exhausted, running the same per-tile code as k_numerator_fac.
+template <int TW>
+__global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMap *__restrict__ maps,
+                                                                const FacBatchItem *__restrict__ items,
+                                                                int n_items, long long total,
+                                                                unsigned long long *counter) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ long long work;
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long w = (long long)atomicAdd(counter, 1ull);
+            int lo = 0, hi = n_items - 1;  // last item whose cta_begin <= w
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (items[mid].cta_begin <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            work = w;
+            item = lo;
+        }
+        __syncthreads();
+        const long long w = work;
+        const int i = item;
+        __syncthreads();
+        if (w >= total) break;
+        const FacParams &p = items[i].p;
+        const long long local = w - items[i].cta_begin;
+        if (!fac_tile<TW>(maps[i], p, (int)(local % p.G), (int)(local / p.G), smem)) break;
+        __syncthreads();
+    }
 }
 
 }  // namespace
+
+int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen) {
+    cudaError_t e = cudaFuncSetAttribute(tw == 64 ? k_numerator_fac_batch<64> : k_numerator_fac_batch<32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
+        return (int)e;
+    }
+    return 0;
+}
+
+int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, long long total,
+                      unsigned long long *counter, int tw, int warps, size_t smem, int grid, void *stream, char *err,
+                      size_t errlen) {
+    void (*kern)(const CUtensorMap *, const FacBatchItem *, int, long long, unsigned long long *) =
+        tw == 64 ? k_numerator_fac_batch<64> : k_numerator_fac_batch<32>;
+    cudaError_t e;
+    if (total <= 0 || grid <= 0) return 0;
+    kern<<<grid, warps * 32, smem, (cudaStream_t)stream>>>(reinterpret_cast<const CUtensorMap *>(maps), items,
+                                                           n_items, total, counter);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "k_numerator_fac_batch: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    return 0;
+}
 
 int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int warps, size_t smem, long long nblocks,
                 void *stream, char *err, size_t errlen) {

@@ -1088,9 +1088,14 @@ mf_status mf_batch_info(const mf_batch *b, int32_t *items, int32_t *shape_groups
     if (!b) return fail(MF_EINVAL, "batch is NULL");
     if (items) *items = (int32_t)b->items.size();
     if (shape_groups) {
-        int mask = 0;
-        for (const auto &it : b->items) mask |= 1 << it.table->plan.shape;
-        *shape_groups = __builtin_popcount(mask);
+        int mask = 0;  // bits 0..3: general shapes, 4..5: factored tile widths 32 and 64
+        for (const auto &it : b->items) {
+            const mf::Plan &pl = it.table->plan;
+            mask |= pl.kernel == 2 ? 1 << (3 + pl.f_tw / 32) : 1 << pl.shape;
+        }
+        int n = 0;
+        for (int i = 0; i < 6; i++) n += (mask >> i) & 1;
+        *shape_groups = n;
     }
     if (graph_ready) *graph_ready = b->exec != nullptr;
     return ok();

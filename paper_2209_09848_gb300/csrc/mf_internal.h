@@ -252,9 +252,19 @@ struct FacParams {
     float *snr_all;               // [K][H][W] or null
     int *status;                  // device status word
     int T, G, kt, th, bh, ns;
+    int warps;                    // warps of the layout (a batched launch may have more)
     int64_t H, W;
     int tiles_x;
 };
+struct FacBatchItem {
+    FacParams p;
+    long long cta_begin;  // first entry of this search in the batch's work list
+};
+// Shared-memory limit of the persistent kernel (set once, outside capture).
+int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen);
+int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, long long total,
+                      unsigned long long *counter, int tw, int warps, size_t smem, int grid, void *stream, char *err,
+                      size_t errlen);
 int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int warps, size_t smem, long long nblocks,
                 void *stream, char *err, size_t errlen);
 

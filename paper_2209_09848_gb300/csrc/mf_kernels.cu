@@ -795,6 +795,7 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     fp->th = pl.f_th;
     fp->bh = pl.f_bh;
     fp->ns = pl.f_ns;
+    fp->warps = pl.warps();
     fp->H = H;
     fp->W = W;
     fp->tiles_x = (int)((W + pl.f_tw - 1) / pl.f_tw);
@@ -898,13 +899,20 @@ struct BatchDevice {
     };
     std::vector<Group> groups;
     std::vector<int> order;  // device-array position -> item
-    struct FacLaunch {
-        int item = 0;
-        CUtensorMap map;
-        FacParams p;
-        long long nblocks = 0;
+    // searches with a factored numerator: one persistent launch per tile
+    // width, with as many warps and as much shared memory as its largest
+    // layout needs
+    struct FacGroup {
+        int tw = 32;
+        int first = 0, count = 0;  // range in d_fmaps / d_fitems
+        long long total = 0;       // CTA work entries
+        size_t smem = 0;
+        int warps = 0;
     };
-    std::vector<FacLaunch> fac;  // items with a factored numerator, one launch each
+    std::vector<FacGroup> fac;
+    CUtensorMap *d_fmaps = nullptr;
+    FacBatchItem *d_fitems = nullptr;
+    unsigned long long *d_fcounters = nullptr;  // one per group
     CUtensorMap *d_maps = nullptr;
     BatchItem *d_items = nullptr;
     unsigned long long *d_counters = nullptr;
@@ -919,6 +927,9 @@ void batch_free(BatchDevice *b) {
     cudaFree(b->d_maps);
     cudaFree(b->d_items);
     cudaFree(b->d_counters);
+    cudaFree(b->d_fmaps);
+    cudaFree(b->d_fitems);
+    cudaFree(b->d_fcounters);
     for (int i = 0; i < BatchDevice::kSide; i++) {
         if (b->side[i]) cudaStreamDestroy(b->side[i]);
         if (b->join[i]) cudaEventDestroy(b->join[i]);
@@ -956,18 +967,43 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         grp.count = (int)bitems.size() - grp.first;
         if (grp.count > 0) b->groups.push_back(grp);
     }
-    for (int i = 0; i < n; i++) {
-        if (items[i].tab->plan.kernel != 2) continue;
-        BatchDevice::FacLaunch fl;
-        fl.item = i;
-        int rc = fac_params(items[i], &fl.map, &fl.p, &fl.nblocks, err, errlen);
-        if (rc) {
-            batch_free(b);
-            return rc;
+    std::vector<CUtensorMap> fmaps;
+    std::vector<FacBatchItem> fitems;
+    for (int tw : {32, 64}) {
+        BatchDevice::FacGroup grp;
+        grp.tw = tw;
+        grp.first = (int)fitems.size();
+        for (int i = 0; i < n; i++) {
+            const Plan &pl = items[i].tab->plan;
+            if (pl.kernel != 2 || pl.f_tw != tw) continue;
+            CUtensorMap m;
+            FacBatchItem fi;
+            std::memset(&fi, 0, sizeof fi);
+            long long nblocks = 0;
+            int rc = fac_params(items[i], &m, &fi.p, &nblocks, err, errlen);
+            if (rc) {
+                batch_free(b);
+                return rc;
+            }
+            fi.cta_begin = grp.total;
+            grp.total += nblocks;
+            grp.smem = std::max(grp.smem, pl.smem());
+            grp.warps = std::max(grp.warps, pl.warps());
+            fmaps.push_back(m);
+            fitems.push_back(fi);
         }
-        b->fac.push_back(fl);
+        grp.count = (int)fitems.size() - grp.first;
+        if (grp.count > 0) b->fac.push_back(grp);
     }
     cudaError_t e = cudaSuccess;
+    if (!fitems.empty()) e = cudaMalloc((void **)&b->d_fmaps, fmaps.size() * sizeof(CUtensorMap));
+    if (e == cudaSuccess && !fitems.empty()) e = cudaMalloc((void **)&b->d_fitems, fitems.size() * sizeof(FacBatchItem));
+    if (e == cudaSuccess && !fitems.empty())
+        e = cudaMalloc((void **)&b->d_fcounters, b->fac.size() * sizeof(unsigned long long));
+    if (e == cudaSuccess && !fitems.empty())
+        e = cudaMemcpy(b->d_fmaps, fmaps.data(), fmaps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !fitems.empty())
+        e = cudaMemcpy(b->d_fitems, fitems.data(), fitems.size() * sizeof(FacBatchItem), cudaMemcpyHostToDevice);
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -992,6 +1028,13 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         snprintf(err, errlen, "batch set-up: %s", cudaGetErrorString(e));
         batch_free(b);
         return (int)e;
+    }
+    for (const auto &grp : b->fac) {
+        const int rc = fac_batch_attr(grp.tw, grp.smem, err, errlen);
+        if (rc) {
+            batch_free(b);
+            return rc;
+        }
     }
     *out = b;
     return 0;
@@ -1025,10 +1068,19 @@ int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream_v
             b->d_maps + grp.first, b->d_items + grp.first, grp.count, grp.total, b->d_counters + grp.shape);
         MF_CHECK_LAUNCH("k_numerator_batch");
     }
-    for (const auto &fl : b->fac) {
-        const Plan &pl = items[fl.item].tab->plan;
+    if (!b->fac.empty()) {
+        e = cudaMemsetAsync(b->d_fcounters, 0, b->fac.size() * sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) {
+            snprintf(err, errlen, "batch counters: %s", cudaGetErrorString(e));
+            return (int)e;
+        }
+    }
+    for (size_t gi = 0; gi < b->fac.size(); gi++) {
+        const auto &grp = b->fac[gi];
+        const int grid = (int)std::min<long long>(grp.total, (long long)b->sms);
         LaunchScope ls(kKNumerator, stream);
-        int rc = fac_enqueue(&fl.map, fl.p, pl.f_tw, pl.warps(), pl.smem(), fl.nblocks, stream, err, errlen);
+        int rc = fac_batch_enqueue(b->d_fmaps + grp.first, b->d_fitems + grp.first, grp.count, grp.total,
+                                   b->d_fcounters + gi, grp.tw, grp.warps, grp.smem, grid, stream, err, errlen);
         if (rc) return rc;
     }
     for (int i = 0; i < n; i++) {

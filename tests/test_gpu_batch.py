@@ -21,19 +21,24 @@ def mf():
 
 def _items(mf):
     from paper_2209_09848_gb300 import synth
-    specs = [  # T, H, W, grid, vmax, dtype, mask, shape
+    # T, H, W, grid, vmax, dtype, mask, layout (None: planner; shape: general
+    # kernel; factored layouts of different warp counts share one launch)
+    specs = [
         (24, 96, 130, (3, 3), 0.3, torch.float32, 0.02, None),
         (9, 64, 64, (2, 2), 0.5, torch.bfloat16, 0.0, None),
-        (31, 150, 90, (4, 2), 0.2, torch.float32, 0.01, 0),
-        (16, 70, 200, (5, 3), 0.25, torch.float16, 0.02, 3),
+        (31, 150, 90, (4, 2), 0.2, torch.float32, 0.01, dict(shape=0)),
+        (16, 70, 200, (5, 3), 0.25, torch.float16, 0.02, dict(shape=3)),
         (5, 33, 47, (1, 1), 0.1, torch.float32, 0.0, None),
-        (40, 128, 128, (3, 4), 0.15, torch.float32, 0.01, 1),
+        (40, 128, 128, (3, 4), 0.15, torch.float32, 0.01, dict(shape=1)),
+        (20, 77, 140, (2, 5), 0.4, torch.float32, 0.01, dict(kernel=2, group=5, tile_h=64, tile_w=32)),
+        (12, 100, 61, (3, 3), 0.3, torch.float32, 0.0, dict(kernel=2, group=1, tile_h=32, tile_w=32)),
+        (18, 90, 150, (2, 3), 0.3, torch.float32, 0.02, dict(kernel=2, group=3, tile_w=64)),
     ]
     out = []
-    for i, (T, H, W, (nx, ny), vm, dt, mfrac, shape) in enumerate(specs):
+    for i, (T, H, W, (nx, ny), vm, dt, mfrac, layout) in enumerate(specs):
         c = synth.small_case(T, H, W, 200 + i, mask_frac=mfrac, movers=2)
         vx, vy = synth.velocity_grid(nx, ny, -vm, vm)
-        table = mf.prf_table_create(vx, vy, T, shape=shape)
+        table = mf.prf_table_create(vx, vy, T, **(layout or {}))
         scale = None
         if dt == torch.float16:
             scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14).astype(np.float32)
@@ -54,7 +59,8 @@ def test_batch_equals_individual_searches(mf, oracle):
         b.add(it["data"], it["sigma"], it["table"], mask=it["mask"], frame_scale=it["scale"], want_all=True)
     b.prepare()
     info = b.info()
-    assert info["items"] == len(items) and info["shape_groups"] >= 2 and not info["graph_ready"]
+    assert info["items"] == len(items) and info["shape_groups"] >= 4 and not info["graph_ready"]
+    assert {it["table"].info()["kernel"] for it in items} == {1, 2}
     alone = [mf.search(it["data"], it["sigma"], it["table"], mask=it["mask"], frame_scale=it["scale"],
                        want_all=True) for it in items]
     torch.cuda.synchronize()
@@ -91,3 +97,25 @@ def test_batch_argument_errors(mf):
     with pytest.raises(mf.MFError):
         b.add(r, torch.ones((8, 8), device="cuda"), table)  # T mismatch
     b.destroy()
+
+
+def test_autotuner_picks_a_timed_layout(mf, oracle):
+    """The autotuner times the factored and general layouts, caches the
+    winner per bucket, and the tuned table searches correctly."""
+    from paper_2209_09848_gb300 import autotune, synth
+    autotune.clear_cache()
+    T, H, W = 20, 120, 140
+    vx, vy = synth.velocity_grid(3, 4, -0.3, 0.3)
+    opts, timings = autotune.tune(vx, vy, T, H, W, crop=128)
+    assert timings and opts in autotune.CANDIDATES
+    assert {autotune.CANDIDATES[i]["kernel"] for i in timings} == {1, 2}
+    assert autotune.tune(vx, vy, T, H, W, crop=128)[0] is not None  # cached
+    table = autotune.tuned_table(vx, vy, T, H, W, crop=128)
+    c = synth.small_case(T, H, W, 31, mask_frac=0.01, movers=2)
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    smax, amax, sall = mf.search(torch.from_numpy(c["res"]).cuda(), torch.from_numpy(c["sigma"]).cuda(), table,
+                                 mask=torch.from_numpy(c["mask"]).cuda(), want_all=True)
+    torch.cuda.synchronize()
+    check_search(smax.cpu().numpy(), amax.cpu().numpy(), sall.cpu().numpy(), N, D, oracle, label="tuned")
