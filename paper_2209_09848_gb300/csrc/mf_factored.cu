@@ -11,10 +11,12 @@
 // general 5 x 5 stencil; the arithmetic is the same sum regrouped.
 //
 // Per frame: every thread waits for the frame's window (TMA box, mbarrier
-// with a bounded wait), the CTA's threads split the row pass into items of 12
-// outputs, one CTA barrier, thread 0 refills the window's stage with frame
-// t + stages, and each warp runs the column pass of its (trajectory slot,
-// 32 x 32 sub-tile).  The row-pass buffer is double-buffered, so one barrier
+// with a bounded wait), the CTA's threads split the row pass into items of 16
+// outputs (at most one per thread for the usual layouts; the column phase is
+// applied as the item reads the window, so the row-pass buffer holds exactly
+// the tile's columns), one CTA barrier, thread 0 refills the window's stage
+// with frame t + stages, and each warp runs the column pass of its
+// (trajectory slot, 32 x 32 sub-tile).  The row-pass buffer is double-buffered, so one barrier
 // per frame orders both its writes and its reuse.  FP32 throughout, with the
 // blocked accumulation of the general kernel (partials over 16 frames).
 #include <cuda.h>
@@ -35,10 +37,40 @@ using namespace dev;
 // why).  The CTA may have more warps than the search's layout uses (batched
 // searches share one launch): the extra warps take part in the row pass and
 // the barriers only.  `smem` is the CTA's 1024-aligned dynamic shared memory.
+// One row-pass item: H(row, c0 .. c0 + 15) = sum_a u_x(a) R(row, c0 + M + c + a)
+// for a column phase M known at compile time; src = R(row, c0), 16-aligned,
+// dst = H(row, c0).
+template <int M>
+__device__ __forceinline__ void row_item(const float *__restrict__ src, float *__restrict__ dst, float ux0,
+                                         float ux1, float ux2, float ux3, float ux4) {
+    constexpr int NL = (kFacItem + 4 + M + 3) / 4;  // 128-bit loads covering the inputs
+    float v[4 * NL];
+#pragma unroll
+    for (int q = 0; q < NL; q++) {
+        const float4 x = reinterpret_cast<const float4 *>(src)[q];
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+    }
+    float o[kFacItem];
+#pragma unroll
+    for (int c = 0; c < kFacItem; c++) {
+        float h = ux0 * v[M + c];
+        h = fmaf(ux1, v[M + c + 1], h);
+        h = fmaf(ux2, v[M + c + 2], h);
+        h = fmaf(ux3, v[M + c + 3], h);
+        o[c] = fmaf(ux4, v[M + c + 4], h);
+    }
+#pragma unroll
+    for (int q = 0; q < kFacItem / 4; q++)
+        reinterpret_cast<float4 *>(dst)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+}
+
 template <int TW>
 __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParams &p, int g, int tile,
                                          unsigned char *smem) {
-    constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / 12;
+    constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / kFacItem;
     constexpr int R = kFacRecordChunk;
     constexpr int NSUBX = TW / 32;
 
@@ -107,38 +139,24 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         const bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
         const unsigned char *fblk = fb + (((t / R) & 1) * R + t % R) * kBB;
         const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
-        float *hb = hbuf + (size_t)(t & 1) * BH * HP;
         if (ready) {
-            // row pass: item (row, m) -> 12 outputs H(row, 12m .. 12m + 11);
+            // row pass: item (row, m) -> 16 outputs H(row, 16m .. 16m + 15);
             // consecutive threads take consecutive rows
-            const int nrows = fh->nrows;
+            const int nrows = fh->nrows, cofs = fh->cofs;
             const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
             const float *rs = rwin + (size_t)s * SF;
+            float *hb = hbuf + (size_t)(t & 1) * BH * HP;
             const float rn = 1.0f / (float)nrows;  // m = floor((it + 1/2) / nrows): exact, it < 2^16
             for (int it = threadIdx.x; it < nrows * NI; it += blockDim.x) {
                 const int m = (int)(((float)it + 0.5f) * rn), row = it - m * nrows;
-                const float4 *src = reinterpret_cast<const float4 *>(rs + row * RP + 12 * m);
-                float v[16];
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const float4 x = src[q];
-                    v[4 * q] = x.x;
-                    v[4 * q + 1] = x.y;
-                    v[4 * q + 2] = x.z;
-                    v[4 * q + 3] = x.w;
+                const float *src = rs + row * RP + kFacItem * m;
+                float *dst = hb + row * HP + kFacItem * m;
+                switch (cofs) {
+                    case 0: row_item<0>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 1: row_item<1>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 2: row_item<2>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    default: row_item<3>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
                 }
-                float o[12];
-#pragma unroll
-                for (int c = 0; c < 12; c++) {
-                    float h = ux0 * v[c];
-                    h = fmaf(ux1, v[c + 1], h);
-                    h = fmaf(ux2, v[c + 2], h);
-                    h = fmaf(ux3, v[c + 3], h);
-                    o[c] = fmaf(ux4, v[c + 4], h);
-                }
-                float4 *dst = reinterpret_cast<float4 *>(hb + row * HP + 12 * m);
-#pragma unroll
-                for (int q = 0; q < 3; q++) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
             }
         }
         if (__syncthreads_or(!ready)) {
@@ -153,7 +171,7 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         if (active) {
             const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
             const float uy0 = fs->uy[0], uy1 = fs->uy[1], uy2 = fs->uy[2], uy3 = fs->uy[3], uy4 = fs->uy[4];
-            const float *col = hb + (32 * sub_y + fs->oy) * HP + 32 * sub_x + lane + fh->cofs;
+            const float *col = hbuf + (size_t)(t & 1) * BH * HP + (32 * sub_y + fs->oy) * HP + 32 * sub_x + lane;
 #pragma unroll
             for (int i = 0; i < 36; i++) {
                 const float h = col[i * HP];

@@ -334,7 +334,7 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
             for (int f = 0; f < T; f++) {
                 const double nr = nrows[g * T + f];
                 const double fma = (n * geo.th * geo.tw * 5.0 + nr * hc * 5.0) / 128.0;
-                const double sm = (n * sub * 36.0 * 128.0 + nr * (hc / 12.0) * 112.0 + bh * rp * 4.0) / 128.0;
+                const double sm = (n * sub * 36.0 * 128.0 + nr * (hc / 16.0) * 160.0 + bh * rp * 4.0) / 128.0;
                 cyc += std::max(fma, sm) / 0.8 + 200.0;
             }
         }

@@ -98,14 +98,16 @@ struct alignas(16) FacSlot {
 };
 static_assert(sizeof(FacSlot) == 32, "FacSlot is 32 bytes");
 __host__ __device__ inline size_t fac_block_bytes(int kt) { return sizeof(FacHdr) + (size_t)kt * sizeof(FacSlot); }
-// Row-pass outputs per row: tile_w + 4 (column phase 0..3 plus footprint),
-// in items of 12; each item reads 16 window values.  Both pitches are odd
-// multiples of 4 floats, so 8 lanes on 8 consecutive rows hit 8 distinct
-// 16-byte bank groups with 128-bit accesses.
-__host__ __device__ constexpr int fac_hcols(int tw) { return (tw + 4 + 11) / 12 * 12; }
+// Row-pass outputs per row: tile_w, in items of 16 (the column phase 0..3
+// is applied when the row pass reads the window, so the column pass reads
+// aligned columns); an item reads 24 window values from a 16-aligned start.
+// Both pitches are odd multiples of 4 floats, so 8 lanes on 8 consecutive
+// rows hit 8 distinct 16-byte bank groups with 128-bit accesses.
+constexpr int kFacItem = 16;
+__host__ __device__ constexpr int fac_hcols(int tw) { return tw; }
 __host__ __device__ constexpr int fac_odd4(int n) { return (n / 4) % 2 ? n : n + 4; }
 __host__ __device__ constexpr int fac_hpitch(int tw) { return fac_odd4(fac_hcols(tw)); }
-__host__ __device__ constexpr int fac_rpitch(int tw) { return fac_odd4(fac_hcols(tw) + 4); }
+__host__ __device__ constexpr int fac_rpitch(int tw) { return fac_odd4(fac_hcols(tw) + 8); }
 constexpr int kFacMaxStages = 6;
 // Frame records arrive in chunks of kFacRecordChunk frames (one bulk copy per
 // chunk, two chunk buffers); a chunk buffer is refilled while frame t + stages
