@@ -16,7 +16,9 @@
 // applied as the item reads the window, so the row-pass buffer holds exactly
 // the tile's columns), one CTA barrier, thread 0 refills the window's stage
 // with frame t + stages, and each warp runs the column pass of its
-// (trajectory slot, 32 x 32 sub-tile).  The row-pass buffer is double-buffered, so one barrier
+// (trajectory slot, 32 x 32 sub-tile): a lane owns 2 adjacent columns x 16
+// rows, reading 20 row-pass pairs with 64-bit loads (a half-warp reads one
+// row's 32 columns, conflict-free).  The row-pass buffer is double-buffered, so one barrier
 // per frame orders both its writes and its reuse.  FP32 throughout, with the
 // blocked accumulation of the general kernel (partials over 16 frames).
 #include <cuda.h>
@@ -126,7 +128,9 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
 
     const int kk = warp < p.warps ? p.members[(size_t)g * KT + slot] : -1;
     const bool active = kk >= 0 && tile_y0 + 32 * sub_y < p.H && tile_x0 + 32 * sub_x < p.W;
-    float acc[32], blk[32];
+    // lane: column pair cp (2 adjacent columns), row half rh (16 rows)
+    const int cp = lane & 15, rh = lane >> 4;
+    float acc[32], blk[32];  // [r * 2 + j]: row 16 rh + r, column 2 cp + j
 #pragma unroll
     for (int r = 0; r < 32; r++) {
         acc[r] = 0.f;
@@ -141,13 +145,15 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
         if (ready) {
             // row pass: item (row, m) -> 16 outputs H(row, 16m .. 16m + 15);
-            // consecutive threads take consecutive rows
+            // consecutive threads take consecutive rows, from the last thread
+            // down: the last warps are the row-pass-only warps and the slots
+            // a short group leaves empty, so they take the items first
             const int nrows = fh->nrows, cofs = fh->cofs;
             const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
             const float *rs = rwin + (size_t)s * SF;
             float *hb = hbuf + (size_t)(t & 1) * BH * HP;
             const float rn = 1.0f / (float)nrows;  // m = floor((it + 1/2) / nrows): exact, it < 2^16
-            for (int it = threadIdx.x; it < nrows * NI; it += blockDim.x) {
+            for (int it = (int)blockDim.x - 1 - (int)threadIdx.x; it < nrows * NI; it += blockDim.x) {
                 const int m = (int)(((float)it + 0.5f) * rn), row = it - m * nrows;
                 const float *src = rs + row * RP + kFacItem * m;
                 float *dst = hb + row * HP + kFacItem * m;
@@ -171,15 +177,19 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         if (active) {
             const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
             const float uy0 = fs->uy[0], uy1 = fs->uy[1], uy2 = fs->uy[2], uy3 = fs->uy[3], uy4 = fs->uy[4];
-            const float *col = hbuf + (size_t)(t & 1) * BH * HP + (32 * sub_y + fs->oy) * HP + 32 * sub_x + lane;
+            const float *col = hbuf + (size_t)(t & 1) * BH * HP + (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x + 2 * cp;
+            const float u[5] = {uy0, uy1, uy2, uy3, uy4};
 #pragma unroll
-            for (int i = 0; i < 36; i++) {
-                const float h = col[i * HP];
-                if (i < 32) blk[i] = fmaf(uy0, h, blk[i]);
-                if (i >= 1 && i - 1 < 32) blk[i - 1] = fmaf(uy1, h, blk[i - 1]);
-                if (i >= 2 && i - 2 < 32) blk[i - 2] = fmaf(uy2, h, blk[i - 2]);
-                if (i >= 3 && i - 3 < 32) blk[i - 3] = fmaf(uy3, h, blk[i - 3]);
-                if (i >= 4) blk[i - 4] = fmaf(uy4, h, blk[i - 4]);
+            for (int i = 0; i < 20; i++) {
+                const float2 h = *reinterpret_cast<const float2 *>(col + i * HP);
+#pragma unroll
+                for (int b = 0; b < 5; b++) {
+                    const int r = i - b;
+                    if (r >= 0 && r < 16) {
+                        blk[2 * r] = fmaf(u[b], h.x, blk[2 * r]);
+                        blk[2 * r + 1] = fmaf(u[b], h.y, blk[2 * r + 1]);
+                    }
+                }
             }
         }
         if ((t + 1) % kFrameBlock == 0) {
@@ -211,17 +221,19 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) red[i] = 0ull;
     __syncthreads();
     const int64_t P = p.H * p.W;
-    const int64_t px = tile_x0 + 32 * sub_x + lane;
-    if (kk >= 0 && px < p.W) {
+    if (kk >= 0) {
 #pragma unroll
         for (int r = 0; r < 32; r++) {
-            const int64_t py = tile_y0 + 32 * sub_y + r;
-            if (py < p.H) {
+            const int rr = r >> 1, j = r & 1;
+            const int64_t px = tile_x0 + 32 * sub_x + 2 * cp + j;
+            const int64_t py = tile_y0 + 32 * sub_y + 16 * rh + rr;
+            if (py < p.H && px < p.W) {
                 const int64_t q = py * p.W + px;
                 const float isd = p.isd[(int64_t)kk * P + q];
                 const float snr = (acc[r] + blk[r]) * isd;
                 if (p.snr_all) p.snr_all[(int64_t)kk * P + q] = isd > 0.f ? snr : 0.f;
-                if (isd > 0.f) atomicMax(&red[(32 * sub_y + r) * TW + 32 * sub_x + lane], pack_key(snr, kk));
+                if (isd > 0.f)
+                    atomicMax(&red[(32 * sub_y + 16 * rh + rr) * TW + 32 * sub_x + 2 * cp + j], pack_key(snr, kk));
             }
         }
     }

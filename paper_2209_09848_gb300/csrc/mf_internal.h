@@ -138,6 +138,10 @@ struct Plan {
     int tile_h() const { return kernel == 2 ? f_th : kTile * kShapes[shape].tys; }
     int tile_w() const { return kernel == 2 ? f_tw : kTile * kShapes[shape].txs; }
     int warps() const { return kernel == 2 ? f_kt * (f_th / 32) * (f_tw / 32) : kWarps; }
+    // warps launched: the factored kernel rounds up to a multiple of 4 so
+    // that each SM scheduler has as many warps; the extra warps make row-pass
+    // items only
+    int launch_warps() const { return kernel == 2 ? (warps() + 3) / 4 * 4 : kWarps; }
     size_t smem() const;
 };
 

@@ -858,7 +858,7 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
         rc = fac_params(a, &map, &fp, &nblocks, err, errlen);
         if (rc) return rc;
         LaunchScope ls(kKNumerator, stream);
-        rc = fac_enqueue(&map, fp, pl.f_tw, pl.warps(), pl.smem(), nblocks, stream, err, errlen);
+        rc = fac_enqueue(&map, fp, pl.f_tw, pl.launch_warps(), pl.smem(), nblocks, stream, err, errlen);
         if (rc) return rc;
         return enqueue_finalize(a, stream, err, errlen);
     }
@@ -988,7 +988,7 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
             fi.cta_begin = grp.total;
             grp.total += nblocks;
             grp.smem = std::max(grp.smem, pl.smem());
-            grp.warps = std::max(grp.warps, pl.warps());
+            grp.warps = std::max(grp.warps, pl.launch_warps());
             fmaps.push_back(m);
             fitems.push_back(fi);
         }
