@@ -532,7 +532,7 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
     // lambda(p + u) with the collapsed kernel G_k(u) = sum over (t, a, b)
     // with s_{k,t} + (a, b) = u of W_{k,t}(a, b)^2, summed here in FP64.
     // Each row of G_k's support becomes one run of weights starting at a
-    // column that is a multiple of 4 and padded to whole chunks of 8.
+    // column that is a multiple of 4 and padded to whole chunks of 4.
     std::vector<mf::RunRec> runs;
     std::vector<int32_t> run_off(K + 1, 0);
     std::vector<float> wts;
@@ -597,7 +597,7 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
                 ++jt;
             }
             const int32_t x0 = (int32_t)(4 * floor_div(it->first.second, 4));
-            const int32_t nch = (int32_t)((xmax - x0 + 1 + 7) / 8);
+            const int32_t nch = (int32_t)((xmax - x0 + 1 + 3) / 4);
             while (wts.size() % 4) wts.push_back(0.f);
             mf::RunRec r;
             r.dy = row;
@@ -605,7 +605,7 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
             r.nch = nch;
             r.woff = (int32_t)wts.size();
             const size_t base = wts.size();
-            wts.resize(base + (size_t)nch * 8, 0.f);
+            wts.resize(base + (size_t)nch * 4, 0.f);
             for (auto q = it; q != jt; ++q) wts[base + (q->first.second - x0)] = (float)q->second;
             runs.push_back(r);
             it = jt;

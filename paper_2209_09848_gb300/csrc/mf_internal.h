@@ -65,7 +65,7 @@ inline size_t frame_block_bytes(int kt) { return sizeof(FrameHdr) + (size_t)kt *
 constexpr int kRecordChunk = 4;
 
 // One row of the collapsed denominator kernel G_k: weights for columns
-// x0 .. x0 + 8 * nch - 1 (x0 a multiple of 4) of row offset dy.
+// x0 .. x0 + 4 * nch - 1 (x0 a multiple of 4) of row offset dy.
 struct alignas(16) RunRec {
     int32_t dy, x0, nch, woff;  // woff: index of the first weight (multiple of 4)
 };

@@ -105,7 +105,7 @@ __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rst
 // kernel G_k.  A thread owns 8 consecutive start pixels of one row, a warp 256
 // of them, a CTA 8 rows; blockIdx.y walks the trajectories.  For each run the
 // thread slides an 8-wide register window along the lambda row (one aligned
-// float4 pair per 8 taps), so every loaded value feeds 8 FMAs.  Products and
+// float4 per 4 taps), so every loaded value feeds 8 FMAs.  Products and
 // partial sums are FP32 over at most kDenTaps taps; the partials are added in
 // FP64.  The result is stored as 1 / sqrt(D) (0 where D = 0).
 __global__ void __launch_bounds__(256) k_denominator(const float *__restrict__ lam, int64_t lw, int64_t pad,
@@ -131,39 +131,33 @@ __global__ void __launch_bounds__(256) k_denominator(const float *__restrict__ l
             const RunRec rr = runs[r];
             const float4 *row = reinterpret_cast<const float4 *>(lam + (py + rr.dy + pad) * lw + px0 + rr.x0 + pad);
             const float4 *wp = reinterpret_cast<const float4 *>(wts + rr.woff);
-            float v[16];
+            // 12-value window of lambda in three float4 slots that rotate:
+            // chunk ch (4 taps) uses slot ch mod 3 onwards and, before its
+            // FMAs, loads the slot two ahead; unrolled by 3 so that every
+            // register index is static
+            float v[12];
             {
                 const float4 p0 = __ldg(row), p1 = __ldg(row + 1);
                 v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
                 v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
             }
-            // two chunks per step with the halves of v swapping roles, so the
-            // sliding window needs no register moves
-            for (int ch = 0; ch < rr.nch; ch += 2) {
-                {
-                    const float4 p2 = __ldg(row + 2 * ch + 2), p3 = __ldg(row + 2 * ch + 3);
-                    v[8] = p2.x; v[9] = p2.y; v[10] = p2.z; v[11] = p2.w;
-                    v[12] = p3.x; v[13] = p3.y; v[14] = p3.z; v[15] = p3.w;
-                    const float4 w0 = __ldg(wp + 2 * ch), w1 = __ldg(wp + 2 * ch + 1);
-                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            for (int ch = 0; ch < rr.nch; ch += 3) {
 #pragma unroll
-                    for (int i = 0; i < 8; i++)
+                for (int u = 0; u < 3; u++) {
+                    if (ch + u < rr.nch) {
+                        const float4 pn = __ldg(row + ch + u + 2);
+                        const int ns = ((u + 2) % 3) * 4;  // slot receiving columns 4 (ch + u + 2) ..
+                        v[ns] = pn.x; v[ns + 1] = pn.y; v[ns + 2] = pn.z; v[ns + 3] = pn.w;
+                        const float4 w4 = __ldg(wp + ch + u);
+                        const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                        for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[i + c], a[c]);
-                }
-                if (ch + 1 < rr.nch) {
-                    const float4 p2 = __ldg(row + 2 * ch + 4), p3 = __ldg(row + 2 * ch + 5);
-                    v[0] = p2.x; v[1] = p2.y; v[2] = p2.z; v[3] = p2.w;
-                    v[4] = p3.x; v[5] = p3.y; v[6] = p3.z; v[7] = p3.w;
-                    const float4 w0 = __ldg(wp + 2 * ch + 2), w1 = __ldg(wp + 2 * ch + 3);
-                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                        for (int i = 0; i < 4; i++)
 #pragma unroll
-                    for (int i = 0; i < 8; i++)
-#pragma unroll
-                        for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[(8 + i + c) & 15], a[c]);
+                            for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[(4 * u + i + c) % 12], a[c]);
+                    }
                 }
             }
-            taps += rr.nch * 8;
+            taps += rr.nch * 4;
             if (taps >= kDenTaps) {
 #pragma unroll
                 for (int c = 0; c < 8; c++) {
