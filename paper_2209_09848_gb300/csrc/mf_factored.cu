@@ -10,17 +10,19 @@
 // frame) this costs 5 FMAs plus the row pass's share, against 25 FMAs for the
 // general 5 x 5 stencil; the arithmetic is the same sum regrouped.
 //
-// Per frame: every thread waits for the frame's window (TMA box, mbarrier
-// with a bounded wait), the CTA's threads split the row pass into items of 16
-// outputs (at most one per thread for the usual layouts; the column phase is
-// applied as the item reads the window, so the row-pass buffer holds exactly
-// the tile's columns), one CTA barrier, thread 0 refills the window's stage
-// with frame t + stages, and each warp runs the column pass of its
-// (trajectory slot, 32 x 32 sub-tile): a lane owns 2 adjacent columns x 16
-// rows, reading 20 row-pass pairs with 64-bit loads (a half-warp reads one
-// row's 32 columns, conflict-free).  The row-pass buffer is double-buffered, so one barrier
-// per frame orders both its writes and its reuse.  FP32 throughout, with the
-// blocked accumulation of the general kernel (partials over 16 frames).
+// Per pair of frames (t, t + 1): every thread waits for both windows (TMA
+// boxes, mbarriers with bounded waits); the CTA's threads split both row
+// passes into items of 16 outputs (the column phase is applied as an item
+// reads the window, so the row-pass buffer holds exactly the tile's columns;
+// items go to the last warps first, so a row-pass-only 16th warp and the
+// warps of empty slots take them); one CTA barrier; thread 0 refills both
+// stages with frames t + stages and t + 1 + stages; each warp runs the
+// column passes of its (trajectory slot, 32 x 32 sub-tile) for both frames:
+// a lane owns 2 adjacent columns x 16 rows, reading 20 row-pass pairs with
+// 64-bit loads (a half-warp reads one row's 32 columns, conflict-free).  Four
+// row-pass buffers rotate, so one barrier per two frames orders both their
+// writes and their reuse.  FP32 throughout, with the blocked accumulation of
+// the general kernel (partials over 16 frames).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -89,8 +91,8 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
 
     const int SF = fac_stage_floats(TW, BH);                              // stage stride, 128-byte multiple
     float *rwin = reinterpret_cast<float *>(smem);                       // [NS][SF] windows of BH x RP
-    float *hbuf = rwin + (size_t)NS * SF;                                 // [2][BH][HP]
-    unsigned char *fb = reinterpret_cast<unsigned char *>(hbuf + (size_t)2 * BH * HP);  // [2][R] blocks
+    float *hbuf = rwin + (size_t)NS * SF;                                 // [kFacHBufs][BH][HP]
+    unsigned char *fb = reinterpret_cast<unsigned char *>(hbuf + (size_t)kFacHBufs * BH * HP);  // [2][R] blocks
     uint64_t *bars = reinterpret_cast<uint64_t *>(fb + 2 * R * kBB);
     int *last_issued = reinterpret_cast<int *>(bars + NS);
     int *bad_flag = last_issued + NS;
@@ -136,73 +138,89 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         acc[r] = 0.f;
         blk[r] = 0.f;
     }
-    bool bad = false;
-    int s = 0;
-    uint32_t par = 0;
-    for (int t = 0; t < p.T; t++) {
-        const bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
-        const unsigned char *fblk = fb + (((t / R) & 1) * R + t % R) * kBB;
-        const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
-        if (ready) {
-            // row pass: item (row, m) -> 16 outputs H(row, 16m .. 16m + 15);
-            // consecutive threads take consecutive rows, from the last thread
-            // down: the last warps are the row-pass-only warps and the slots
-            // a short group leaves empty, so they take the items first
-            const int nrows = fh->nrows, cofs = fh->cofs;
-            const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
-            const float *rs = rwin + (size_t)s * SF;
-            float *hb = hbuf + (size_t)(t & 1) * BH * HP;
-            const float rn = 1.0f / (float)nrows;  // m = floor((it + 1/2) / nrows): exact, it < 2^16
-            for (int it = (int)blockDim.x - 1 - (int)threadIdx.x; it < nrows * NI; it += blockDim.x) {
-                const int m = (int)(((float)it + 0.5f) * rn), row = it - m * nrows;
-                const float *src = rs + row * RP + kFacItem * m;
-                float *dst = hb + row * HP + kFacItem * m;
-                switch (cofs) {
-                    case 0: row_item<0>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                    case 1: row_item<1>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                    case 2: row_item<2>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                    default: row_item<3>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+    auto record = [&](int f) { return fb + (((f / R) & 1) * R + f % R) * kBB; };
+    auto column = [&](int f) {
+        if (!active) return;
+        const unsigned char *fblk = record(f);
+        const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
+        const float u[5] = {fs->uy[0], fs->uy[1], fs->uy[2], fs->uy[3], fs->uy[4]};
+        const float *col = hbuf + (size_t)(f % kFacHBufs) * BH * HP + (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x + 2 * cp;
+#pragma unroll
+        for (int i = 0; i < 20; i++) {
+            const float2 h = *reinterpret_cast<const float2 *>(col + i * HP);
+#pragma unroll
+            for (int b = 0; b < 5; b++) {
+                const int r = i - b;
+                if (r >= 0 && r < 16) {
+                    blk[2 * r] = fmaf(u[b], h.x, blk[2 * r]);
+                    blk[2 * r + 1] = fmaf(u[b], h.y, blk[2 * r + 1]);
                 }
             }
         }
+    };
+    // the row passes of frames f0 (stage s0) and f0 + 1 (stage s1, if it
+    // exists) as one list of items: item it < n0 is (row, m) of frame f0
+    auto row_pair = [&](int f0, int s0, int s1, bool two) {
+        const FacHdr *h0 = reinterpret_cast<const FacHdr *>(record(f0));
+        const FacHdr *h1 = reinterpret_cast<const FacHdr *>(record(two ? f0 + 1 : f0));
+        const int n0 = h0->nrows * NI, n1 = two ? h1->nrows * NI : 0;
+        for (int it = (int)blockDim.x - 1 - (int)threadIdx.x; it < n0 + n1; it += blockDim.x) {
+            const bool second = it >= n0;
+            const FacHdr *fh = second ? h1 : h0;
+            const int f = second ? f0 + 1 : f0, st = second ? s1 : s0, j = second ? it - n0 : it;
+            const int nrows = fh->nrows, cofs = fh->cofs;
+            const float rn = 1.0f / (float)nrows;
+            const int m = (int)(((float)j + 0.5f) * rn), row = j - m * nrows;
+            const float *src = rwin + (size_t)st * SF + row * RP + kFacItem * m;
+            float *dst = hbuf + (size_t)(f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
+            const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
+            switch (cofs) {
+                case 0: row_item<0>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                case 1: row_item<1>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                case 2: row_item<2>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                default: row_item<3>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+            }
+        }
+    };
+
+    bool bad = false;
+    int s = 0;  // stage of frame t and its phase
+    uint32_t par = 0;
+    for (int t = 0; t < p.T; t += 2) {
+        const bool two = t + 1 < p.T;
+        const int s1 = (s + 1 == NS) ? 0 : s + 1;
+        const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
+        bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
+        if (ready && two) ready = mbar_wait(smem_u32(&bars[s1]), par1, 1, p.status);
+        if (ready) row_pair(t, s, s1, two);
         if (__syncthreads_or(!ready)) {
             bad = true;
             break;
         }
-        // every thread is done with stage s: refill it with frame t + NS
-        if (threadIdx.x == 0 && t + NS < p.T) {
+        // every thread is done with stages s (and s1): refill them with frames t + NS (and t + 1 + NS)
+        if (threadIdx.x == 0) {
             fence_proxy_async();
-            issue(t + NS, s, fh->next_roy, fh->next_rox);
-        }
-        if (active) {
-            const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
-            const float uy0 = fs->uy[0], uy1 = fs->uy[1], uy2 = fs->uy[2], uy3 = fs->uy[3], uy4 = fs->uy[4];
-            const float *col = hbuf + (size_t)(t & 1) * BH * HP + (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x + 2 * cp;
-            const float u[5] = {uy0, uy1, uy2, uy3, uy4};
-#pragma unroll
-            for (int i = 0; i < 20; i++) {
-                const float2 h = *reinterpret_cast<const float2 *>(col + i * HP);
-#pragma unroll
-                for (int b = 0; b < 5; b++) {
-                    const int r = i - b;
-                    if (r >= 0 && r < 16) {
-                        blk[2 * r] = fmaf(u[b], h.x, blk[2 * r]);
-                        blk[2 * r + 1] = fmaf(u[b], h.y, blk[2 * r + 1]);
-                    }
-                }
+            if (t + NS < p.T) {
+                const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t));
+                issue(t + NS, s, fh->next_roy, fh->next_rox);
+            }
+            if (two && t + 1 + NS < p.T) {
+                const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t + 1));
+                issue(t + 1 + NS, s1, fh->next_roy, fh->next_rox);
             }
         }
-        if ((t + 1) % kFrameBlock == 0) {
+        column(t);
+        if (two) column(t + 1);
+        if ((t + 2) % kFrameBlock == 0) {
 #pragma unroll
             for (int r = 0; r < 32; r++) {
                 acc[r] += blk[r];
                 blk[r] = 0.f;
             }
         }
-        if (++s == NS) {
-            s = 0;
-            par ^= 1u;
-        }
+        // advance two stages
+        s = (s1 + 1 == NS) ? 0 : s1 + 1;
+        par = (s1 + 1 == NS) ? (par1 ^ 1u) : par1;
     }
     if (bad) {
         // let any copy still in flight land before the CTA's shared memory goes away

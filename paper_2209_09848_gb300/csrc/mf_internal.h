@@ -116,9 +116,14 @@ constexpr int kFacRecordChunk = 8;
 static_assert(kFacRecordChunk >= kFacMaxStages, "record chunks must outlive the frames in flight");
 // Floats of one window stage, rounded to 128 bytes (TMA destination alignment).
 __host__ __device__ constexpr int fac_stage_floats(int tw, int bh) { return (bh * fac_rpitch(tw) + 31) / 32 * 32; }
+// Row-pass buffers: the CTA makes the row passes of two frames, meets at one
+// barrier, then runs both column passes; the next pair writes the other two
+// buffers, so one barrier per two frames orders writes and reuse.
+constexpr int kFacHBufs = 4;
 inline size_t fac_smem_bytes(int tw, int bh, int ns, int kt) {
     return 1024 + (size_t)ns * fac_stage_floats(tw, bh) * sizeof(float) +
-           2 * (size_t)bh * fac_hpitch(tw) * sizeof(float) + 2 * (size_t)kFacRecordChunk * fac_block_bytes(kt) +
+           (size_t)kFacHBufs * bh * fac_hpitch(tw) * sizeof(float) +
+           2 * (size_t)kFacRecordChunk * fac_block_bytes(kt) +
            (size_t)ns * (sizeof(uint64_t) + sizeof(int)) + sizeof(int) + 64;
 }
 
