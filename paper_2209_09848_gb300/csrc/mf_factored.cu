@@ -143,8 +143,10 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         if (!active) return;
         const unsigned char *fblk = record(f);
         const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
-        const float u[5] = {fs->uy[0], fs->uy[1], fs->uy[2], fs->uy[3], fs->uy[4]};
-        const float *col = hbuf + (size_t)(f % kFacHBufs) * BH * HP + (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x + 2 * cp;
+        const float4 u4 = *reinterpret_cast<const float4 *>(fs->uy);
+        const float2 u5 = *reinterpret_cast<const float2 *>(fs->uy + 4);  // u_y(2) and the row offset
+        const float u[5] = {u4.x, u4.y, u4.z, u4.w, u5.x};
+        const float *col = hbuf + (size_t)(f % kFacHBufs) * BH * HP + (32 * sub_y + 16 * rh + __float_as_int(u5.y)) * HP + 32 * sub_x + 2 * cp;
 #pragma unroll
         for (int i = 0; i < 20; i++) {
             const float2 h = *reinterpret_cast<const float2 *>(col + i * HP);
@@ -169,8 +171,7 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
             const FacHdr *fh = second ? h1 : h0;
             const int f = second ? f0 + 1 : f0, st = second ? s1 : s0, j = second ? it - n0 : it;
             const int nrows = fh->nrows, cofs = fh->cofs;
-            const float rn = 1.0f / (float)nrows;
-            const int m = (int)(((float)j + 0.5f) * rn), row = j - m * nrows;
+            const int m = (int)(((float)j + 0.5f) * fh->inv_nrows), row = j - m * nrows;
             const float *src = rwin + (size_t)st * SF + row * RP + kFacItem * m;
             float *dst = hbuf + (size_t)(f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
             const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];

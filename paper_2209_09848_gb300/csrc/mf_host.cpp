@@ -506,6 +506,7 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
             }
             fh.cofs = h.pad;
             fh.nrows = h.nrows;
+            fh.inv_nrows = 1.0f / (float)h.nrows;
             for (int a = 0; a < 5; a++) fh.ux[a] = (float)t->fx[((size_t)k0 * T + f) * 5 + a];
             std::memcpy(b, &fh, sizeof fh);
             for (int w = 0; w < kt; w++) {

@@ -88,7 +88,8 @@ struct alignas(16) FacHdr {
     int32_t cofs;                // row-pass column of output column 0 (0..3)
     int32_t nrows;               // row-pass rows this frame needs
     float ux[5];                 // u_x(a), a = -2..2
-    int32_t pad[3];
+    float inv_nrows;             // 1 / nrows, rounded to FP32 (splits row-pass items)
+    int32_t pad[2];
 };
 static_assert(sizeof(FacHdr) == 48, "FacHdr is 48 bytes");
 struct alignas(16) FacSlot {
