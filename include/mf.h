@@ -276,7 +276,35 @@ mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint
                           int32_t *n_out, void *workspace, size_t workspace_bytes,
                           mf_stream stream);
 
-/* Per-kernel accounting of the library's own launches (for benchmarks and
+/* The search with the residual stack in HOST memory (not in the paper):
+ * the whole path a user with frames on the host runs, enqueued on `stream`
+ * in order -- upload of the stack into the workspace (one 2-D copy when the
+ * rows are contiguous, one per frame otherwise), mf_search, optionally
+ * mf_rescore_topk (k_top > 0) from the uploaded stack, and download of the
+ * results into host memory.
+ *   host_stack  residuals as in mf_search, but `data` is HOST memory (pinned
+ *               for asynchronous copies; pageable memory works but the copy
+ *               then synchronises); frame_scale, if given, is DEVICE memory;
+ *   sigma, mask DEVICE memory as in mf_search (static per field);
+ *   snr_max_host float[H*W], argmax_host int32[H*W]: HOST memory;
+ *   k_top       0 for no candidates, else 1..16384: cand_host
+ *               mf_candidate[k_top] and n_cand_host int32, HOST memory;
+ *   workspace   DEVICE memory of mf_search_host_workspace_size bytes,
+ *               256-byte aligned (holds the stack copy, the maps and the
+ *               search / rescore workspaces).
+ * Results are valid once the stream has reached them (synchronise it).
+ * Calls on different streams with different workspaces overlap: one call's
+ * upload runs on the copy engine while another's kernels run.
+ * Errors: those of mf_search and mf_rescore_topk, plus MF_EINVAL for a
+ * missing output or a small workspace; nothing is enqueued on MF_EINVAL. */
+mf_status mf_search_host_workspace_size(const mf_stack *stack, const mf_prf_table *table,
+                                        int32_t k_top, size_t *bytes);
+mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const uint8_t *mask,
+                         const mf_prf_table *table, float *snr_max_host, int32_t *argmax_host,
+                         int32_t k_top, mf_candidate *cand_host, int32_t *n_cand_host,
+                         void *workspace, size_t workspace_bytes, mf_stream stream);
+
+/* Per-kernel accounting of the library's own launches/* Per-kernel accounting of the library's own launches (for benchmarks and
  * roofline reports; not in the paper).  Launch counts are always kept; device
  * times are recorded with CUDA events on the launching stream only while
  * profiling is enabled. */

@@ -121,6 +121,8 @@ def load():
             "mf_search_noalloc": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P], ctypes.c_int),
             "mf_rescore_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
+            "mf_search_host_workspace_size": ([ctypes.POINTER(Stack), P, I32, ctypes.POINTER(SZ)], ctypes.c_int),
+            "mf_search_host": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
             "mf_profile_enable": ([I32], ctypes.c_int),
             "mf_profile_read": ([ctypes.POINTER(Profile), I32], ctypes.c_int),
             "mf_batch_create": ([pp], ctypes.c_int),
@@ -332,6 +334,41 @@ def search_noalloc(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, ma
     _check(load().mf_search_noalloc(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
                                     _ptr(argmax), _ptr(snr_all), _stream_ptr(stream)))
     return snr_max, argmax, snr_all
+
+
+def search_host_workspace_size(stack: torch.Tensor, table: PrfTable, k_top: int = 0) -> int:
+    """mf_search_host_workspace_size for a host stack tensor."""
+    st = make_stack(stack, None)
+    n = ctypes.c_size_t()
+    _check(load().mf_search_host_workspace_size(ctypes.byref(st), table.handle, int(k_top), ctypes.byref(n)))
+    return n.value
+
+
+def search_host(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torch.Tensor | None = None,
+                frame_scale: torch.Tensor | None = None, k_top: int = 0, workspace=None, out=None, stream=None):
+    """mf_search_host: the stack is a CPU tensor (pinned for asynchronous
+    upload), sigma / mask / frame_scale live on the GPU; returns CPU tensors
+    (snr_max [H, W], argmax [H, W], candidate records [k_top] uint8 or None,
+    n_candidates [1] int32 or None), valid after the stream is synchronised.
+    `out` may pass those four tensors (pinned) to reuse them."""
+    if stack.device.type != "cpu":
+        raise ValueError("search_host takes a CPU stack; use search for device stacks")
+    st = make_stack(stack, frame_scale)
+    T, H, W = stack.shape
+    dev = sigma.device
+    if out is None:
+        pin = stack.is_pinned()
+        smax = torch.empty((H, W), dtype=torch.float32, pin_memory=pin)
+        amax = torch.empty((H, W), dtype=torch.int32, pin_memory=pin)
+        cand = torch.zeros((k_top, CANDIDATE_BYTES), dtype=torch.uint8, pin_memory=pin) if k_top else None
+        ncand = torch.zeros(1, dtype=torch.int32, pin_memory=pin) if k_top else None
+    else:
+        smax, amax, cand, ncand = out
+    ws = _workspace(search_host_workspace_size(stack, table, k_top), dev, workspace)
+    _check(load().mf_search_host(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(smax), _ptr(amax),
+                                 int(k_top), _ptr(cand), _ptr(ncand), _ptr(ws), ws.numel() * ws.element_size(),
+                                 _stream_ptr(stream)))
+    return smax, amax, cand, ncand
 
 
 def rescore_workspace_size(H, W, k_top) -> int:

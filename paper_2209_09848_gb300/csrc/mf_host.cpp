@@ -1142,6 +1142,123 @@ mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint
     return ok();
 }
 
+// ------------------------------------------------- host-buffer search ---
+
+namespace {
+
+struct HostSearchLayout {
+    size_t stack_off, smax_off, amax_off, cand_off, n_off, search_off, rescore_off, total;
+    size_t search_bytes, rescore_bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+HostSearchLayout host_search_layout(const mf_stack *st, const mf_prf_table *table, int32_t k_top) {
+    HostSearchLayout L{};
+    const int64_t T = st->T, H = st->H, W = st->W;
+    size_t off = 0;
+    L.stack_off = off;
+    off = align256(off + (size_t)T * H * W * elem_size(st->dtype));
+    L.smax_off = off;
+    off = align256(off + (size_t)H * W * sizeof(float));
+    L.amax_off = off;
+    off = align256(off + (size_t)H * W * sizeof(int32_t));
+    L.cand_off = off;
+    off = align256(off + (size_t)(k_top > 0 ? k_top : 0) * sizeof(mf_candidate));
+    L.n_off = off;
+    off = align256(off + sizeof(int32_t));
+    L.search_bytes = mf::search_layout(T, H, W, table).total;
+    L.search_off = off;
+    off = align256(off + L.search_bytes);
+    L.rescore_bytes = k_top > 0 ? mf::rescore_workspace(H, W, k_top) : 0;
+    L.rescore_off = off;
+    off = align256(off + L.rescore_bytes);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+mf_status mf_search_host_workspace_size(const mf_stack *stack, const mf_prf_table *table, int32_t k_top,
+                                        size_t *bytes) {
+    if (!bytes || !table || !stack) return fail(MF_EINVAL, "NULL argument");
+    if (stack->T < 1 || stack->H < 0 || stack->W < 0) return fail(MF_EINVAL, "bad stack shape");
+    if (stack->dtype != MF_F32 && stack->dtype != MF_BF16 && stack->dtype != MF_F16)
+        return fail(MF_EINVAL, "unknown dtype %d", stack->dtype);
+    if (k_top < 0) return fail(MF_EINVAL, "k_top=%d is negative", k_top);
+    *bytes = host_search_layout(stack, table, k_top).total;
+    return ok();
+}
+
+mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const uint8_t *mask,
+                         const mf_prf_table *table, float *snr_max_host, int32_t *argmax_host, int32_t k_top,
+                         mf_candidate *cand_host, int32_t *n_cand_host, void *workspace, size_t workspace_bytes,
+                         mf_stream stream) {
+    mf_status s = check_stack(host_stack);
+    if (s != MF_OK) return s;
+    if (!table) return fail(MF_EINVAL, "table is NULL");
+    if (host_stack->T != table->T)
+        return fail(MF_EINVAL, "stack has T=%lld, table has T=%d", (long long)host_stack->T, table->T);
+    const int64_t T = host_stack->T, H = host_stack->H, W = host_stack->W;
+    if (H * W == 0) return ok();
+    if (!sigma || !snr_max_host || !argmax_host) return fail(MF_EINVAL, "sigma, snr_max and argmax are required");
+    if (k_top < 0 || (int64_t)k_top > H * W) return fail(MF_EINVAL, "k_top=%d out of range", k_top);
+    if (k_top > 16384) return fail(MF_EUNSUPPORTED, "k_top above 16384");
+    if (k_top > 0 && (!cand_host || !n_cand_host)) return fail(MF_EINVAL, "k_top > 0 needs cand and n_cand");
+    const HostSearchLayout L = host_search_layout(host_stack, table, k_top);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", L.total, workspace_bytes);
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != table->device)
+        return fail(MF_EINVAL, "table lives on device %d, current device is %d", table->device, dev);
+    char *ws = (char *)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = elem_size(host_stack->dtype);
+    // upload: one 2-D copy when rows are contiguous, else one per frame
+    cudaError_t e;
+    if (host_stack->row_stride == W) {
+        e = cudaMemcpy2DAsync(ws + L.stack_off, (size_t)H * W * es, host_stack->data,
+                              (size_t)(T > 1 ? host_stack->frame_stride : H * W) * es, (size_t)H * W * es, (size_t)T,
+                              cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaSuccess;
+        for (int64_t t = 0; t < T && e == cudaSuccess; t++)
+            e = cudaMemcpy2DAsync(ws + L.stack_off + (size_t)t * H * W * es, (size_t)W * es,
+                                  (const char *)host_stack->data + (size_t)t * host_stack->frame_stride * es,
+                                  (size_t)host_stack->row_stride * es, (size_t)W * es, (size_t)H,
+                                  cudaMemcpyHostToDevice, st);
+    }
+    if (e != cudaSuccess) return fail(MF_ECUDA, "stack upload: %s", cudaGetErrorString(e));
+    mf_stack dstack = *host_stack;
+    dstack.data = ws + L.stack_off;
+    dstack.row_stride = W;
+    dstack.frame_stride = H * W;
+    float *smax = (float *)(ws + L.smax_off);
+    int32_t *amax = (int32_t *)(ws + L.amax_off);
+    s = mf_search(&dstack, sigma, mask, table, smax, amax, nullptr, ws + L.search_off, L.search_bytes, stream);
+    if (s != MF_OK) return s;
+    if (k_top > 0) {
+        s = mf_rescore_topk(&dstack, sigma, mask, table, smax, amax, k_top, (mf_candidate *)(ws + L.cand_off),
+                            (int32_t *)(ws + L.n_off), ws + L.rescore_off, L.rescore_bytes, stream);
+        if (s != MF_OK) return s;
+    }
+    e = cudaMemcpyAsync(snr_max_host, smax, (size_t)H * W * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(argmax_host, amax, (size_t)H * W * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && k_top > 0)
+        e = cudaMemcpyAsync(cand_host, ws + L.cand_off, (size_t)k_top * sizeof(mf_candidate), cudaMemcpyDeviceToHost,
+                            st);
+    if (e == cudaSuccess && k_top > 0)
+        e = cudaMemcpyAsync(n_cand_host, ws + L.n_off, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "result download: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+}  // extern "C"
+
 mf_status mf_profile_enable(int32_t on) {
     mf::profile_enable(on);
     return ok();

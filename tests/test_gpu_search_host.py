@@ -1,0 +1,72 @@
+"""mf_search_host (stack in host memory): the same maps and candidates as
+the device-stack calls, for contiguous and strided pinned stacks and for
+pageable memory; the FP64 oracle on one case."""
+import numpy as np
+import pytest
+
+from _util import check_search
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2209_09848_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    m.load()
+    return m
+
+
+def _case(T=21, H=90, W=77, seed=5):
+    from paper_2209_09848_gb300 import synth
+    c = synth.small_case(T, H, W, seed, mask_frac=0.02, movers=3)
+    vx, vy = synth.velocity_grid(4, 3, -0.4, 0.4)
+    return c, vx, vy
+
+
+@pytest.mark.parametrize("layout", ["pinned", "strided", "pageable"])
+def test_host_stack_matches_device_stack(mf, layout):
+    c, vx, vy = _case()
+    T, H, W = c["res"].shape
+    table = mf.prf_table_create(vx, vy, T)
+    sigma = torch.from_numpy(c["sigma"]).cuda()
+    mask = torch.from_numpy(c["mask"]).cuda()
+    res = torch.from_numpy(c["res"])
+    if layout == "strided":
+        big = torch.zeros((T, H + 3, W + 5), dtype=torch.float32).pin_memory()
+        big[:, 1:H + 1, 2:W + 2] = res
+        host = big[:, 1:H + 1, 2:W + 2]
+    elif layout == "pinned":
+        host = res.clone().pin_memory()
+    else:
+        host = res.clone()
+    k_top = 50
+    smax, amax, cand, n = mf.search_host(host, sigma, table, mask=mask, k_top=k_top)
+    torch.cuda.synchronize()
+    assert mf.device_status() == 0
+    dm, da, _ = mf.search(res.cuda(), sigma, table, mask=mask)
+    raw, dn = mf.rescore_topk(res.cuda(), sigma, table, dm, da, k_top, mask=mask)
+    torch.cuda.synchronize()
+    assert torch.equal(smax, dm.cpu()) and torch.equal(amax, da.cpu())
+    assert int(n.item()) == int(dn.item())
+    assert torch.equal(cand, raw.cpu())
+
+
+def test_host_stack_against_oracle_and_errors(mf, oracle):
+    c, vx, vy = _case(T=12, H=64, W=70, seed=9)
+    T, H, W = c["res"].shape
+    table = mf.prf_table_create(vx, vy, T)
+    sigma = torch.from_numpy(c["sigma"]).cuda()
+    mask = torch.from_numpy(c["mask"]).cuda()
+    host = torch.from_numpy(c["res"]).pin_memory()
+    smax, amax, _, _ = mf.search_host(host, sigma, table, mask=mask)
+    torch.cuda.synchronize()
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    check_search(smax.numpy(), amax.numpy(), None, N, D, oracle, label="search_host")
+    with pytest.raises(mf.MFError):  # workspace too small
+        mf.search_host(host, sigma, table, mask=mask, workspace=torch.empty(256, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(mf.MFError):  # k_top beyond the pixels
+        mf.search_host(host, sigma, table, mask=mask, k_top=H * W + 1)
