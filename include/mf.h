@@ -136,7 +136,12 @@ mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const 
  *
  * Factored kernel: group = trajectories per CTA (all with one v_x), tile_h a
  * multiple of 32, tile_w 32 or 64, with group * tile_h / 32 * tile_w / 32 <= 16
- * warps; stages = frame windows in flight (2..6); 0 = planner's choice.
+ * warps; stages = frame windows in flight (2..6); segments = number of
+ * consecutive frame ranges the frames are split into (1..16): within a
+ * segment a CTA follows each trajectory from where it stands at the
+ * segment's first frame, so the rows a group's window spans grow with the
+ * segment's length instead of the stack's; each segment's numerators go to
+ * their own plane and are summed per pixel at the end; 0 = planner's choice.
  * An autotuner times several layouts and keeps the fastest. */
 typedef struct {
     int32_t shape;
@@ -149,6 +154,7 @@ typedef struct {
     int32_t tile_h;      /* factored: output rows per CTA, 0 = automatic */
     int32_t tile_w;      /* factored: output columns per CTA, 0 = automatic */
     int32_t stages;      /* factored: frame windows in flight, 0 = automatic */
+    int32_t segments;    /* factored: time segments, 0 = automatic (see below) */
 } mf_plan_opts;
 
 /* mf_prf_table_create with layout options (opts NULL = automatic).
@@ -199,6 +205,8 @@ typedef struct {
     int32_t lockstep;         /* numerator frame hand-off (see mf_plan_opts) */
     int32_t kernel;           /* numerator: 1 general, 2 factored (see mf_plan_opts) */
     int32_t stages;           /* frame windows in flight per CTA */
+    int32_t time_segments;    /* time segments of the factored numerator (1 otherwise) */
+    int32_t reserved;
 } mf_table_info;
 
 /* Layout of an existing table. */
@@ -304,7 +312,7 @@ mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const u
                          int32_t k_top, mf_candidate *cand_host, int32_t *n_cand_host,
                          void *workspace, size_t workspace_bytes, mf_stream stream);
 
-/* Per-kernel accounting of the library's own launches/* Per-kernel accounting of the library's own launches (for benchmarks and
+/* Per-kernel accounting of the library's own launches (for benchmarks and
  * roofline reports; not in the paper).  Launch counts are always kept; device
  * times are recorded with CUDA events on the launching stream only while
  * profiling is enabled. */

@@ -49,10 +49,10 @@ CANDIDATE_BYTES = ctypes.sizeof(Candidate)
 class PlanOpts(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("vec", ctypes.c_int32), ("lockstep", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("group", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("tile_w", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("stages", ctypes.c_int32), ("segments", ctypes.c_int32)]
 
 
-_LAYOUT_KEYS = ("shape", "vec", "lockstep", "kernel", "group", "tile_h", "tile_w", "stages")
+_LAYOUT_KEYS = ("shape", "vec", "lockstep", "kernel", "group", "tile_h", "tile_w", "stages", "segments")
 
 
 def _opts(**kw):
@@ -63,7 +63,7 @@ def _opts(**kw):
     o.shape = -1 if kw.get("shape") is None else int(kw["shape"])
     o.vec = 0 if kw.get("vec") is None else int(kw["vec"])
     o.lockstep = -1 if kw.get("lockstep") is None else int(kw["lockstep"])
-    for k in ("kernel", "group", "tile_h", "tile_w", "stages"):
+    for k in ("kernel", "group", "tile_h", "tile_w", "stages", "segments"):
         setattr(o, k, 0 if kw.get(k) is None else int(kw[k]))
     return ctypes.byref(o)
 
@@ -75,7 +75,8 @@ class TableInfo(ctypes.Structure):
                 ("window_rows", ctypes.c_int32), ("segments", ctypes.c_int32),
                 ("max_abs_shift", ctypes.c_int32), ("g_nnz", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("cost", ctypes.c_double), ("vec", ctypes.c_int32),
-                ("lockstep", ctypes.c_int32), ("kernel", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("lockstep", ctypes.c_int32), ("kernel", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("time_segments", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -208,8 +209,8 @@ class PrfTable:
 def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> PrfTable:
     """mf_prf_table_create, or mf_prf_table_create_ex when layout options are
     given: shape, vec, lockstep (general numerator), kernel (1 general,
-    2 factored), group, tile_h, tile_w, stages (factored numerator); None or
-    absent = automatic."""
+    2 factored), group, tile_h, tile_w, stages, segments (factored
+    numerator); None or absent = automatic."""
     import numpy as np
     bad = set(layout) - set(_LAYOUT_KEYS)
     if bad:

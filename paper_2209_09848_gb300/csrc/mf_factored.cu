@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <type_traits>
 
 #include "mf_device.cuh"
 #include "mf_internal.h"
@@ -71,16 +72,58 @@ __device__ __forceinline__ void row_item(const float *__restrict__ src, float *_
         reinterpret_cast<float4 *>(dst)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
+// The (group, segment, tile) of CTA `cta` of a search, in the order
+// segment, tile row, tile column, group: the CTAs running at the same time
+// then read the same frames of neighbouring tiles for every group, which
+// keeps those frames in L2.  Tile rows are in reference coordinates (a
+// trajectory's start pixel is the tile pixel minus its s_y at the segment's
+// first frame) and start at the group's smallest such s_y; every group of a
+// segment gets as many tile rows as the group with the widest spread needs,
+// ceil((H + spread) / tile_h).  False if cta is past the last tile.
+__device__ __forceinline__ bool fac_locate(const FacParams &p, int tw, long long cta, int &g, int &j, int &y0,
+                                           int &x0, int &t0, int &t1) {
+    const int4 *segs = reinterpret_cast<const int4 *>(p.segs);
+    for (j = 0; j < p.S; j++) {
+        int spread = 0;
+        for (int e = 0; e < p.G; e++) spread = max(spread, segs[(size_t)e * p.S + j].w);
+        const long long rows = (p.H + spread + p.th - 1) / p.th;
+        const long long n = rows * p.tiles_x * p.G;
+        if (cta < n) {
+            g = (int)(cta % p.G);
+            const long long rest = cta / p.G;
+            const int4 sg = segs[(size_t)g * p.S + j];
+            y0 = sg.z + (int)(rest / p.tiles_x) * p.th;
+            x0 = (int)(rest % p.tiles_x) * tw;
+            t0 = sg.x;
+            t1 = sg.y;
+            return true;
+        }
+        cta -= n;
+    }
+    return false;
+}
+
 template <int TW>
-__device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParams &p, int g, int tile,
+__device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParams &p, long long cta,
                                          unsigned char *smem) {
     constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / kFacItem;
     constexpr int R = kFacRecordChunk;
     constexpr int NSUBX = TW / 32;
 
     const int NS = p.ns, BH = p.bh, KT = p.kt;
-    const int tile_y0 = (tile / p.tiles_x) * p.th;
-    const int tile_x0 = (tile % p.tiles_x) * TW;
+    int g = 0, seg = 0, tile_y0 = 0, tile_x0 = 0, t0 = 0, t1 = 0;
+    if (!fac_locate(p, TW, cta, g, seg, tile_y0, tile_x0, t0, t1)) return true;  // uniform: nothing to do
+    {
+        // a tile row past every member's start pixels (groups with a smaller
+        // spread than the segment's widest) has nothing to compute
+        bool any = false;
+        for (int w = 0; w < KT; w++) {
+            if (p.members[(size_t)g * KT + w] < 0) continue;
+            const int r = tile_y0 - p.refs[((size_t)g * p.S + seg) * KT + w];
+            any |= r + p.th > 0 && r < p.H;
+        }
+        if (!any) return true;  // same for every thread of the CTA
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nsub = (p.th / 32) * NSUBX;
     // a slot's warps are consecutive, so they spread over the SM's four
@@ -96,7 +139,6 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     uint64_t *bars = reinterpret_cast<uint64_t *>(fb + 2 * R * kBB);
     int *last_issued = reinterpret_cast<int *>(bars + NS);
     int *bad_flag = last_issued + NS;
-    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem);  // epilogue reuses the windows
 
     const unsigned char *gblocks = p.blocks + (size_t)g * p.T * kBB;
     if (threadIdx.x == 0) {
@@ -122,14 +164,18 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     };
     if (threadIdx.x == 0) {
         fence_proxy_async();
-        for (int s = 0; s < NS && s < p.T; s++) {
-            const FrameHdr h = p.hdr[(size_t)g * p.T + s];
-            issue(s, s, h.roy, h.rox);
+        for (int s = 0; s < NS && t0 + s < t1; s++) {
+            const FrameHdr h = p.hdr[(size_t)g * p.T + t0 + s];
+            issue(t0 + s, s, h.roy, h.rox);
         }
     }
 
     const int kk = warp < p.warps ? p.members[(size_t)g * KT + slot] : -1;
-    const bool active = kk >= 0 && tile_y0 + 32 * sub_y < p.H && tile_x0 + 32 * sub_x < p.W;
+    // the slot's s_y at the segment's first frame; its start pixels are the
+    // tile pixels minus that: a warp whose rows hold none is idle
+    const int ref = kk >= 0 ? p.refs[((size_t)g * p.S + seg) * KT + slot] : 0;
+    const int qrow = tile_y0 + 32 * sub_y - ref;
+    const bool active = kk >= 0 && qrow + 32 > 0 && qrow < p.H && tile_x0 + 32 * sub_x < p.W;
     // lane: column pair cp (2 adjacent columns), row half rh (16 rows)
     const int cp = lane & 15, rh = lane >> 4;
     float acc[32], blk[32];  // [r * 2 + j]: row 16 rh + r, column 2 cp + j
@@ -187,8 +233,8 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     bool bad = false;
     int s = 0;  // stage of frame t and its phase
     uint32_t par = 0;
-    for (int t = 0; t < p.T; t += 2) {
-        const bool two = t + 1 < p.T;
+    for (int t = t0; t < t1; t += 2) {
+        const bool two = t + 1 < t1;
         const int s1 = (s + 1 == NS) ? 0 : s + 1;
         const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
         bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
@@ -201,18 +247,18 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         // every thread is done with stages s (and s1): refill them with frames t + NS (and t + 1 + NS)
         if (threadIdx.x == 0) {
             fence_proxy_async();
-            if (t + NS < p.T) {
+            if (t + NS < t1) {
                 const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t));
                 issue(t + NS, s, fh->next_roy, fh->next_rox);
             }
-            if (two && t + 1 + NS < p.T) {
+            if (two && t + 1 + NS < t1) {
                 const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t + 1));
                 issue(t + 1 + NS, s1, fh->next_roy, fh->next_rox);
             }
         }
         column(t);
         if (two) column(t + 1);
-        if ((t + 2) % kFrameBlock == 0) {
+        if ((t - t0 + 2) % kFrameBlock == 0) {
 #pragma unroll
             for (int r = 0; r < 32; r++) {
                 acc[r] += blk[r];
@@ -228,40 +274,25 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         if (threadIdx.x == 0) {
             for (int q = 0; q < NS; q++) {
                 const int f = last_issued[q];
-                if (f >= 0) mbar_wait(smem_u32(&bars[q]), (uint32_t)((f / NS) & 1), 2, p.status);
+                if (f >= 0) mbar_wait(smem_u32(&bars[q]), (uint32_t)(((f - t0) / NS) & 1), 2, p.status);
             }
         }
         return false;
     }
 
-    // Epilogue: SNR = N / sqrt(D); max over the CTA's trajectories in a tile
-    // of packed (SNR, k) keys, then one atomicMax per pixel.
-    const int TH = p.th;
-    for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) red[i] = 0ull;
-    __syncthreads();
+    // Epilogue: this segment's numerator of each (trajectory, start pixel) into
+    // the segment's plane; the start pixel is the tile pixel minus the
+    // trajectory's s_y at the segment's first frame (each is written once)
     const int64_t P = p.H * p.W;
     if (kk >= 0) {
+        float *plane = p.planes + ((size_t)seg * p.K + kk) * P;
 #pragma unroll
         for (int r = 0; r < 32; r++) {
-            const int rr = r >> 1, j = r & 1;
-            const int64_t px = tile_x0 + 32 * sub_x + 2 * cp + j;
-            const int64_t py = tile_y0 + 32 * sub_y + 16 * rh + rr;
-            if (py < p.H && px < p.W) {
-                const int64_t q = py * p.W + px;
-                const float isd = p.isd[(int64_t)kk * P + q];
-                const float snr = (acc[r] + blk[r]) * isd;
-                if (p.snr_all) p.snr_all[(int64_t)kk * P + q] = isd > 0.f ? snr : 0.f;
-                if (isd > 0.f)
-                    atomicMax(&red[(32 * sub_y + 16 * rh + rr) * TW + 32 * sub_x + 2 * cp + j], pack_key(snr, kk));
-            }
+            const int rr = r >> 1, jj = r & 1;
+            const int64_t px = tile_x0 + 32 * sub_x + 2 * cp + jj;
+            const int64_t py = (int64_t)tile_y0 + 32 * sub_y + 16 * rh + rr - ref;
+            if (py >= 0 && py < p.H && px < p.W) plane[py * p.W + px] = acc[r] + blk[r];
         }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
-        const unsigned long long key = red[i];
-        if (key == 0ull) continue;
-        const int64_t py = tile_y0 + i / TW, qx = tile_x0 + i % TW;
-        atomicMax(&p.keys[py * p.W + qx], key);
     }
     // the barriers may be initialised again for this CTA's next tile
     if (threadIdx.x == 0)
@@ -274,7 +305,7 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
                                                           const FacParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    fac_tile<TW>(ymap, p, (int)(blockIdx.x % (unsigned)p.G), (int)(blockIdx.x / (unsigned)p.G), smem);
+    fac_tile<TW>(ymap, p, (long long)blockIdx.x, smem);
 }
 
 // Persistent factored numerator over a batch of searches: one CTA per SM
@@ -307,13 +338,84 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMa
         __syncthreads();
         if (w >= total) break;
         const FacParams &p = items[i].p;
-        const long long local = w - items[i].cta_begin;
-        if (!fac_tile<TW>(maps[i], p, (int)(local % p.G), (int)(local / p.G), smem)) break;
+        if (!fac_tile<TW>(maps[i], p, w - items[i].cta_begin, smem)) break;
         __syncthreads();
     }
 }
 
+// Per pixel: N_k = sum of the segment planes (segment order), SNR = N_k /
+// sqrt(D_k) over the filters with D_k > 0, the maximum and the smallest k
+// attaining it (-1 and 0 where no filter has D > 0), and optionally the SNR
+// cube (0 where D = 0).  V consecutive pixels per thread (V = 4 when P is a
+// multiple of 4: 128-bit loads).
+template <int V>
+__global__ void k_finalize_planes(const float *__restrict__ planes, const float *__restrict__ isd, int S, int K,
+                                  int64_t P, float *__restrict__ snr_max, int32_t *__restrict__ argmax,
+                                  float *__restrict__ snr_all) {
+    using VecT = typename std::conditional<V == 4, float4, float>::type;
+    const int64_t n = P / V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float best[V];
+        int arg[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            best[v] = 0.f;
+            arg[v] = -1;
+        }
+        for (int k = 0; k < K; k++) {
+            float nk[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) nk[v] = 0.f;
+            for (int j = 0; j < S; j++) {
+                const VecT x = reinterpret_cast<const VecT *>(planes + ((int64_t)j * K + k) * P)[i];
+                const float *xf = reinterpret_cast<const float *>(&x);
+#pragma unroll
+                for (int v = 0; v < V; v++) nk[v] += xf[v];
+            }
+            const VecT dv = reinterpret_cast<const VecT *>(isd + (int64_t)k * P)[i];
+            const float *d = reinterpret_cast<const float *>(&dv);
+            float snr[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                snr[v] = nk[v] * d[v];
+                if (d[v] > 0.f && (arg[v] < 0 || snr[v] > best[v])) {
+                    best[v] = snr[v];
+                    arg[v] = k;
+                }
+                if (d[v] <= 0.f) snr[v] = 0.f;
+            }
+            if (snr_all) reinterpret_cast<VecT *>(snr_all + (int64_t)k * P)[i] = *reinterpret_cast<const VecT *>(snr);
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            snr_max[i * V + v] = arg[v] < 0 ? 0.f : best[v];
+            argmax[i * V + v] = arg[v];
+        }
+    }
+}
+
 }  // namespace
+
+int fac_finalize_enqueue(const float *planes, const float *isd, int S, int K, int64_t P, float *snr_max,
+                         int32_t *argmax, float *snr_all, void *stream, char *err, size_t errlen) {
+    if (P <= 0) return 0;
+    const bool vec = P % 4 == 0 && (uintptr_t)snr_all % 16 == 0;
+    const int64_t items = vec ? P / 4 : P;
+    int64_t blocks = (items + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (vec)
+        k_finalize_planes<4><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(planes, isd, S, K, P, snr_max, argmax,
+                                                                                 snr_all);
+    else
+        k_finalize_planes<1><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(planes, isd, S, K, P, snr_max, argmax,
+                                                                                 snr_all);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "k_finalize_planes: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    return 0;
+}
 
 int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen) {
     cudaError_t e = cudaFuncSetAttribute(tw == 64 ? k_numerator_fac_batch<64> : k_numerator_fac_batch<32>,

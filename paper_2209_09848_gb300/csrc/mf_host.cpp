@@ -247,13 +247,18 @@ mf_status plan_groups(mf_prf_table &t) {
 
 // Factored numerator: trajectories with the same v_x form a class (they
 // share s_x and u_x at every frame); each class, sorted by v_y, is split into
-// groups of consecutive members, one group per CTA.  For each candidate CTA
-// geometry (trajectories per CTA, tile) the window rows BH follow from the
-// largest s_y spread of a group, the stages from the shared-memory budget,
+// groups of consecutive members, one group per CTA.  The frames are split
+// into segments; within a segment a CTA follows each member from its s_y at
+// the segment's first frame, so the rows a group's window spans at frame t
+// grow with t - (segment start) only.  For each candidate CTA geometry
+// (trajectories per CTA, tile) and segment count, the window rows BH follow
+// from the largest such spread, the stages from the shared-memory budget,
 // and the cost from a per-frame model of one CTA in SM cycles: FP32 FMAs of
 // both passes at 128 per cycle, or the shared-memory bytes they move at 128
-// per cycle, whichever is larger, plus a fixed cost for the frame barrier.
-// Returns false if the table is not separable or no geometry fits.
+// per cycle, whichever is larger, a fixed cost for the frame barrier, and a
+// penalty when a pair of frames has more row-pass items than the CTA has
+// threads; plus, per segment, writing and reading a K x P plane.  Returns
+// false if the table is not separable or no geometry fits.
 bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
     if (t.fx.empty() || t.vx.size() != (size_t)t.K) return false;
     const int K = t.K, T = t.T;
@@ -282,13 +287,25 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
             }
         }
     }
+    // segment counts: starts at multiples of the record chunk, at least one
+    // chunk per segment
+    std::vector<int> seg_counts;
+    if (t.forced_segments) {
+        seg_counts.push_back(t.forced_segments);
+    } else {
+        for (int S : {1, 2, 3, 4, 6, 8}) seg_counts.push_back(S);
+    }
+    auto seg_starts = [&](int S, std::vector<int32_t> &t0) {
+        t0.clear();
+        for (int j = 0; j < S; j++) {
+            const int f = (int)((int64_t)j * T / S) / mf::kFacRecordChunk * mf::kFacRecordChunk;
+            if (t0.empty() || f > t0.back()) t0.push_back(f);
+        }
+        t0.push_back(T);
+        return (int)t0.size() - 1;
+    };
     bool have = false;
     for (const Geo &geo : geos) {
-        mf::Plan p;
-        p.kernel = 2;
-        p.f_kt = geo.kt;
-        p.f_th = geo.th;
-        p.f_tw = geo.tw;
         std::vector<std::vector<int>> groups;
         for (const auto &c : classes) {
             const int n = (int)c.size();
@@ -299,53 +316,97 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
                 i += sz;
             }
         }
-        // rows of each (group, frame) and the window height
-        std::vector<int> nrows(groups.size() * (size_t)T);
-        int bh = 0;
-        for (size_t g = 0; g < groups.size(); g++)
-            for (int f = 0; f < T; f++) {
-                int mn = INT32_MAX, mx = INT32_MIN;
-                for (int k : groups[g]) {
-                    const int sy = t.shifts[((size_t)k * T + f) * 2 + 1];
-                    mn = std::min(mn, sy);
-                    mx = std::max(mx, sy);
+        const int G = (int)groups.size();
+        const int warps = geo.kt * (geo.th / 32) * (geo.tw / 32);
+        const int threads = 32 * ((warps + 3) / 4 * 4);
+        for (int S_req : seg_counts) {
+            std::vector<int32_t> t0;
+            const int S = seg_starts(S_req, t0);
+            if (t.forced_segments && S != S_req) continue;  // fewer frames than the segments asked for
+            mf::Plan p;
+            p.kernel = 2;
+            p.f_kt = geo.kt;
+            p.f_th = geo.th;
+            p.f_tw = geo.tw;
+            p.f_seg = S;
+            p.seg_t0 = t0;
+            p.seg_qy.assign((size_t)G * S * 2, 0);
+            p.seg_ref.assign((size_t)G * S * geo.kt, INT32_MIN);
+            // rows of each (group, frame) and the window height
+            std::vector<int> nrows((size_t)G * T);
+            int bh = 0;
+            for (int g = 0; g < G; g++)
+                for (int j = 0; j < S; j++) {
+                    int rmn = INT32_MAX, rmx = INT32_MIN;
+                    for (size_t i = 0; i < groups[g].size(); i++) {
+                        const int k = groups[g][i];
+                        const int sy0 = t.shifts[((size_t)k * T + t0[j]) * 2 + 1];
+                        p.seg_ref[((size_t)g * S + j) * geo.kt + i] = sy0;
+                        rmn = std::min(rmn, sy0);
+                        rmx = std::max(rmx, sy0);
+                    }
+                    p.seg_qy[((size_t)g * S + j) * 2 + 0] = rmn;
+                    p.seg_qy[((size_t)g * S + j) * 2 + 1] = rmx - rmn;
+                    for (int f = t0[j]; f < t0[j + 1]; f++) {
+                        int mn = INT32_MAX, mx = INT32_MIN;
+                        for (size_t i = 0; i < groups[g].size(); i++) {
+                            const int k = groups[g][i];
+                            const int rel = t.shifts[((size_t)k * T + f) * 2 + 1] -
+                                            p.seg_ref[((size_t)g * S + j) * geo.kt + i];
+                            mn = std::min(mn, rel);
+                            mx = std::max(mx, rel);
+                        }
+                        nrows[(size_t)g * T + f] = geo.th + 4 + (mx - mn);
+                        bh = std::max(bh, nrows[(size_t)g * T + f]);
+                    }
                 }
-                nrows[g * T + f] = geo.th + 4 + (mx - mn);
-                bh = std::max(bh, nrows[g * T + f]);
+            if (bh > 256) continue;
+            int ns = 0;
+            for (int c = t.forced_stages ? t.forced_stages : mf::kFacMaxStages; c >= 2; c--) {
+                if (mf::fac_smem_bytes(geo.tw, bh, c, geo.kt) <= (size_t)mf::kSmemBudget &&
+                    (size_t)c * mf::fac_stage_floats(geo.tw, bh) * 4 >= (size_t)geo.th * geo.tw * 8) {
+                    ns = c;
+                    break;
+                }
+                if (t.forced_stages) break;
             }
-        if (bh > 256) continue;
-        int ns = 0;
-        for (int c = t.forced_stages ? t.forced_stages : mf::kFacMaxStages; c >= 2; c--) {
-            if (mf::fac_smem_bytes(geo.tw, bh, c, geo.kt) <= (size_t)mf::kSmemBudget &&
-                (size_t)c * mf::fac_stage_floats(geo.tw, bh) * 4 >= (size_t)geo.th * geo.tw * 8) {
-                ns = c;
-                break;
+            if (ns == 0) continue;
+            p.f_ns = ns;
+            p.f_bh = bh;
+            const double hc = mf::fac_hcols(geo.tw), rp = mf::fac_rpitch(geo.tw);
+            const double ni = hc / mf::kFacItem;
+            const double sub = (geo.th / 32) * (geo.tw / 32);
+            double cyc = 0.0;
+            for (int g = 0; g < G; g++) {
+                const double n = (double)groups[g].size();
+                for (int j = 0; j < S; j++) {
+                    // tile rows cover the members' spread at the segment start
+                    // too (nominal 1024-row image)
+                    const double extra = 1.0 + p.seg_qy[((size_t)g * S + j) * 2 + 1] / 1024.0;
+                    double seg = 0.0;
+                    for (int f = t0[j]; f < t0[j + 1]; f++) {
+                        const double nr = nrows[(size_t)g * T + f];
+                        const double fma = (n * geo.th * geo.tw * 5.0 + nr * hc * 5.0) / 128.0;
+                        const double sm = (n * sub * 40.0 * 128.0 + nr * ni * 160.0 + bh * rp * 4.0) / 128.0;
+                        const double rounds = std::ceil(2.0 * nr * ni / threads);
+                        seg += std::max(fma, sm) / 0.8 + 200.0 + 300.0 * (rounds - 1.0);
+                    }
+                    cyc += seg * extra;
+                }
             }
-            if (t.forced_stages) break;
-        }
-        if (ns == 0) continue;
-        p.f_ns = ns;
-        p.f_bh = bh;
-        const double hc = mf::fac_hcols(geo.tw), rp = mf::fac_rpitch(geo.tw);
-        const double sub = (geo.th / 32) * (geo.tw / 32);
-        double cyc = 0.0;
-        for (size_t g = 0; g < groups.size(); g++) {
-            const double n = (double)groups[g].size();
-            for (int f = 0; f < T; f++) {
-                const double nr = nrows[g * T + f];
-                const double fma = (n * geo.th * geo.tw * 5.0 + nr * hc * 5.0) / 128.0;
-                const double sm = (n * sub * 36.0 * 128.0 + nr * (hc / 16.0) * 160.0 + bh * rp * 4.0) / 128.0;
-                cyc += std::max(fma, sm) / 0.8 + 200.0;
+            // planes: S x K x 4 bytes written and read per pixel (at ~6.7 TB/s,
+            // 152 SMs at 2.07 GHz: 0.38 S K cycles per pixel), and the extra
+            // CTA prologues and epilogues per segment (measured: about three
+            // times the traffic term)
+            p.cost = cyc / ((double)geo.th * geo.tw) + 1.2 * S * K;
+            p.G = G;
+            p.members.assign((size_t)G * geo.kt, -1);
+            for (int g = 0; g < G; g++)
+                for (size_t i = 0; i < groups[g].size(); i++) p.members[(size_t)g * geo.kt + i] = groups[g][i];
+            if (!have || p.cost < out.cost) {
+                out = std::move(p);
+                have = true;
             }
-        }
-        p.cost = cyc / ((double)geo.th * geo.tw);
-        p.G = (int)groups.size();
-        p.members.assign((size_t)p.G * geo.kt, -1);
-        for (size_t g = 0; g < groups.size(); g++)
-            for (size_t i = 0; i < groups[g].size(); i++) p.members[g * geo.kt + i] = groups[g][i];
-        if (!have || p.cost < out.cost) {
-            out = std::move(p);
-            have = true;
         }
     }
     if (!have) return false;
@@ -371,6 +432,7 @@ mf_status upload(T **dst, const T *src, size_t n) {
 struct HostLayouts {
     std::vector<mf::FrameHdr> hdr;
     std::vector<unsigned char> blocks;
+    std::vector<int32_t> segs;  // factored: [G][S][4]
     std::vector<mf::RunRec> runs;
     std::vector<int32_t> run_off;
     std::vector<float> wts;
@@ -378,6 +440,7 @@ struct HostLayouts {
 
 size_t layout_bytes(const mf_prf_table *t, const HostLayouts &h) {
     return h.blocks.size() + h.hdr.size() * sizeof(mf::FrameHdr) + t->plan.members.size() * sizeof(int32_t) +
+           h.segs.size() * sizeof(int32_t) + t->plan.seg_ref.size() * sizeof(int32_t) +
            h.runs.size() * sizeof(mf::RunRec) +
            h.run_off.size() * sizeof(int32_t) + h.wts.size() * sizeof(float) + t->taps.size() * sizeof(double) +
            t->shifts.size() * sizeof(int32_t);
@@ -471,17 +534,24 @@ void general_layouts(mf_prf_table *t, HostLayouts &out) {
 void fac_layouts(mf_prf_table *t, HostLayouts &out) {
     const int T = t->T;
     const mf::Plan &p = t->plan;
-    const int kt = p.f_kt;
+    const int kt = p.f_kt, S = p.f_seg;
+    std::vector<int> seg_of(T);
+    for (int j = 0; j < S; j++)
+        for (int f = p.seg_t0[j]; f < p.seg_t0[j + 1]; f++) seg_of[f] = j;
+    // s_y of slot w at frame f relative to its s_y at the segment's first frame
+    auto rel = [&](int g, int w, int f) {
+        const int k = p.members[(size_t)g * kt + w];
+        return t->shifts[((size_t)k * T + f) * 2 + 1] - p.seg_ref[((size_t)g * S + seg_of[f]) * kt + w];
+    };
     std::vector<mf::FrameHdr> hdr((size_t)p.G * T);
     for (int g = 0; g < p.G; g++) {
         const int k0 = p.members[(size_t)g * kt];
         for (int f = 0; f < T; f++) {
             int mny = INT32_MAX, mxy = INT32_MIN;
             for (int w = 0; w < kt; w++) {
-                const int k = p.members[(size_t)g * kt + w];
-                if (k < 0) continue;
-                mny = std::min(mny, t->shifts[((size_t)k * T + f) * 2 + 1]);
-                mxy = std::max(mxy, t->shifts[((size_t)k * T + f) * 2 + 1]);
+                if (p.members[(size_t)g * kt + w] < 0) continue;
+                mny = std::min(mny, rel(g, w, f));
+                mxy = std::max(mxy, rel(g, w, f));
             }
             const int64_t sx = t->shifts[((size_t)k0 * T + f) * 2 + 0];
             mf::FrameHdr &h = hdr[(size_t)g * T + f];
@@ -500,9 +570,10 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
             const mf::FrameHdr &h = hdr[(size_t)g * T + f];
             mf::FacHdr fh;
             std::memset(&fh, 0, sizeof fh);
-            if (f + p.f_ns < T) {
-                fh.next_roy = hdr[(size_t)g * T + f + p.f_ns].roy;
-                fh.next_rox = hdr[(size_t)g * T + f + p.f_ns].rox;
+            const int fn = f + p.f_ns;  // frame loaded next into this stage, if in the same segment
+            if (fn < p.seg_t0[seg_of[f] + 1]) {
+                fh.next_roy = hdr[(size_t)g * T + fn].roy;
+                fh.next_rox = hdr[(size_t)g * T + fn].rox;
             }
             fh.cofs = h.pad;
             fh.nrows = h.nrows;
@@ -516,14 +587,25 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
                 if (k >= 0) {
                     const size_t ktf = (size_t)k * T + f;
                     for (int c = 0; c < 5; c++) fs.uy[c] = (float)t->fy[ktf * 5 + c];
-                    fs.oy = t->shifts[ktf * 2 + 1] - 2 - h.roy;
+                    fs.oy = rel(g, w, f) - 2 - h.roy;
                 }
                 std::memcpy(b + sizeof fh + (size_t)w * sizeof fs, &fs, sizeof fs);
             }
         }
     }
+    // per (group, segment): first frame, end frame, min s_y, spread
+    std::vector<int32_t> segs((size_t)p.G * S * 4);
+    for (int g = 0; g < p.G; g++)
+        for (int j = 0; j < S; j++) {
+            int32_t *q = &segs[((size_t)g * S + j) * 4];
+            q[0] = p.seg_t0[j];
+            q[1] = p.seg_t0[j + 1];
+            q[2] = p.seg_qy[((size_t)g * S + j) * 2 + 0];
+            q[3] = p.seg_qy[((size_t)g * S + j) * 2 + 1];
+        }
     out.hdr = std::move(hdr);
     out.blocks = std::move(blocks);
+    out.segs = std::move(segs);
 }
 
 // Denominator layout: constant-shift runs of the collapsed kernels.
@@ -627,6 +709,10 @@ mf_status finish_table(mf_prf_table *t) {
     if ((s = upload(&t->d_blocks, h.blocks.data(), h.blocks.size())) != MF_OK) return s;
     if ((s = upload(&t->d_hdr, h.hdr.data(), h.hdr.size())) != MF_OK) return s;
     if ((s = upload(&t->d_members, t->plan.members.data(), t->plan.members.size())) != MF_OK) return s;
+    if (t->plan.kernel == 2) {
+        if ((s = upload(&t->d_segs, h.segs.data(), h.segs.size())) != MF_OK) return s;
+        if ((s = upload(&t->d_refs, t->plan.seg_ref.data(), t->plan.seg_ref.size())) != MF_OK) return s;
+    }
     if ((s = upload(&t->d_runs, h.runs.data(), h.runs.size())) != MF_OK) return s;
     if ((s = upload(&t->d_run_off, h.run_off.data(), h.run_off.size())) != MF_OK) return s;
     if ((s = upload(&t->d_wts, h.wts.data(), h.wts.size())) != MF_OK) return s;
@@ -656,6 +742,7 @@ void fill_info(const mf_prf_table *t, mf_table_info *info) {
     info->lockstep = fac ? 1 : t->plan.lockstep;
     info->kernel = t->plan.kernel;
     info->stages = fac ? t->plan.f_ns : mf::kStages;
+    info->time_segments = fac ? t->plan.f_seg : 1;
     info->device_bytes = (int64_t)t->device_bytes;
 }
 
@@ -663,6 +750,8 @@ void free_device(mf_prf_table *t) {
     cudaFree(t->d_blocks);
     cudaFree(t->d_hdr);
     cudaFree(t->d_members);
+    cudaFree(t->d_segs);
+    cudaFree(t->d_refs);
     cudaFree(t->d_runs);
     cudaFree(t->d_run_off);
     cudaFree(t->d_wts);
@@ -671,6 +760,8 @@ void free_device(mf_prf_table *t) {
     t->d_blocks = nullptr;
     t->d_hdr = nullptr;
     t->d_members = nullptr;
+    t->d_segs = nullptr;
+    t->d_refs = nullptr;
     t->d_runs = nullptr;
     t->d_run_off = nullptr;
     t->d_wts = nullptr;
@@ -721,6 +812,18 @@ namespace mf {
 
 mf_status set_error(mf_status s, const char *msg) { return fail(s, "%s", msg); }
 
+long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W) {
+    const Plan &p = tab.plan;
+    const long long tiles_x = (W + p.f_tw - 1) / p.f_tw;
+    long long n = 0;
+    for (int j = 0; j < p.f_seg; j++) {
+        int spread = 0;
+        for (int g = 0; g < p.G; g++) spread = std::max(spread, p.seg_qy[((size_t)g * p.f_seg + j) * 2 + 1]);
+        n += (H + spread + p.f_th - 1) / p.f_th * tiles_x * p.G;
+    }
+    return n;
+}
+
 WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab) {
     WorkspaceLayout L;
     // zero border wide enough for every denominator read: shifts up to
@@ -739,6 +842,7 @@ WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_tabl
     L.y_off = take((size_t)T * H * L.y_pitch * sizeof(float));
     L.isd_off = take((size_t)tab->K * H * W * sizeof(float));
     L.keys_off = take((size_t)H * W * sizeof(unsigned long long));
+    L.planes_off = take(tab->plan.kernel == 2 ? (size_t)tab->plan.f_seg * tab->K * H * W * sizeof(float) : 0);
     L.total = off;
     return L;
 }
@@ -817,6 +921,11 @@ static mf_status apply_opts(mf_prf_table *t, const mf_plan_opts *opts) {
     t->forced_th = opts->tile_h;
     t->forced_tw = opts->tile_w;
     t->forced_stages = opts->stages;
+    if (opts->segments < 0 || opts->segments > mf::kFacMaxSegments) {
+        delete t;
+        return fail(MF_EINVAL, "segments=%d out of range 0..%d", opts->segments, mf::kFacMaxSegments);
+    }
+    t->forced_segments = opts->segments;
     return MF_OK;
 }
 

@@ -128,9 +128,19 @@ inline size_t fac_smem_bytes(int tw, int bh, int ns, int kt) {
            (size_t)ns * (sizeof(uint64_t) + sizeof(int)) + sizeof(int) + 64;
 }
 
+constexpr int kFacMaxSegments = 16;
+
 struct Plan {
     int kernel = 1;       // 1: general 5 x 5 numerator, 2: factored numerator
     int f_kt = 0, f_th = 0, f_tw = 0, f_ns = 0, f_bh = 0;  // factored numerator geometry
+    // factored numerator time segments: frames seg_t0[j] .. seg_t0[j + 1] - 1
+    // (starts are multiples of kFacRecordChunk); per (group, segment) the
+    // smallest s_y of the members at the segment's first frame and the
+    // members' spread there; per (group, segment, slot) that member's s_y
+    int f_seg = 1;
+    std::vector<int32_t> seg_t0;      // f_seg + 1
+    std::vector<int32_t> seg_qy;      // G * f_seg * 2: (min s_y, spread)
+    std::vector<int32_t> seg_ref;     // G * f_seg * kt, INT32_MIN for an empty slot
     int shape = 0;        // index into kShapes
     int vec = 2;          // width of the numerator's shared-memory loads (1, 2 or 4 floats)
     int lockstep = 0;     // numerator frame hand-off: 1 = CTA barrier per frame
@@ -175,6 +185,7 @@ struct mf_prf_table {
     std::vector<double> fx, fy;   // K*T*5
     std::vector<double> vx, vy;   // K
     mf::Plan plan;
+    int forced_segments = 0;  // factored time segments, 0: automatic
     int forced_kernel = 0;  // 0: automatic, 1: general, 2: factored
     int forced_group = 0, forced_th = 0, forced_tw = 0, forced_stages = 0;  // factored geometry, 0: automatic
     int forced_shape = -1;  // -1: cost model
@@ -186,6 +197,8 @@ struct mf_prf_table {
     // device copies
     unsigned char *d_blocks = nullptr;   // [G][T] frame blocks (frame_block_bytes or fac_block_bytes)
     int32_t *d_members = nullptr;        // [G][kt] trajectory of each slot, -1 for none
+    int32_t *d_segs = nullptr;           // factored: [G][S] (first frame, last frame + 1, min s_y, spread)
+    int32_t *d_refs = nullptr;           // factored: [G][S][kt] s_y of each slot at the segment's first frame
     mf::FrameHdr *d_hdr = nullptr;       // [G][T]
     mf::RunRec *d_runs = nullptr;        // [n_seg]
     int32_t *d_run_off = nullptr;        // [K + 1]
@@ -197,7 +210,7 @@ struct mf_prf_table {
 namespace mf {
 
 struct WorkspaceLayout {
-    size_t lam_off, y_off, isd_off, keys_off, total;
+    size_t lam_off, y_off, isd_off, keys_off, planes_off, total;
     int64_t pad;       // zero border of the padded lambda image
     int64_t lam_w;     // padded lambda row pitch
     int64_t lam_h;
@@ -259,15 +272,22 @@ struct FacParams {
     const unsigned char *blocks;  // [G][T] blocks of fac_block_bytes(kt)
     const FrameHdr *hdr;          // [G][T] window origins (pad = column phase)
     const int32_t *members;       // [G][kt] trajectory of each slot, -1 for none
-    const float *isd;             // [K][H][W] 1 / sqrt(D)
-    unsigned long long *keys;     // [H][W] packed (SNR, k)
-    float *snr_all;               // [K][H][W] or null
+    const int32_t *segs;          // [G][S][4] first frame, end frame, min s_y, spread
+    const int32_t *refs;          // [G][S][kt] s_y of each slot at the segment's first frame
+    float *planes;                // [S][K][H][W] numerator of each segment
     int *status;                  // device status word
-    int T, G, kt, th, bh, ns;
+    int T, G, kt, th, bh, ns, S, K;
     int warps;                    // warps of the layout (a batched launch may have more)
     int64_t H, W;
     int tiles_x;
 };
+// Sum of the segment planes, SNR with 1 / sqrt(D), per-pixel max over k
+// (smallest k on ties) and the optional SNR cube.
+int fac_finalize_enqueue(const float *planes, const float *isd, int S, int K, int64_t P, float *snr_max,
+                         int32_t *argmax, float *snr_all, void *stream, char *err, size_t errlen);
+// CTAs of a factored search: sum over (group, segment) of the tile rows
+// ceil((H + spread) / tile_h) times the tile columns.
+long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W);
 struct FacBatchItem {
     FacParams p;
     long long cta_begin;  // first entry of this search in the batch's work list

@@ -779,9 +779,9 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     fp->blocks = tab.d_blocks;
     fp->hdr = tab.d_hdr;
     fp->members = tab.d_members;
-    fp->isd = reinterpret_cast<float *>(a.ws + L.isd_off);
-    fp->keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
-    fp->snr_all = a.snr_all;
+    fp->segs = tab.d_segs;
+    fp->refs = tab.d_refs;
+    fp->planes = reinterpret_cast<float *>(a.ws + L.planes_off);
     fp->status = status;
     fp->T = (int)T;
     fp->G = pl.G;
@@ -789,11 +789,13 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     fp->th = pl.f_th;
     fp->bh = pl.f_bh;
     fp->ns = pl.f_ns;
+    fp->S = pl.f_seg;
+    fp->K = tab.K;
     fp->warps = pl.warps();
     fp->H = H;
     fp->W = W;
     fp->tiles_x = (int)((W + pl.f_tw - 1) / pl.f_tw);
-    *nblocks = (long long)pl.G * fp->tiles_x * ((H + pl.f_th - 1) / pl.f_th);
+    *nblocks = fac_ctas(tab, H, W);
     return 0;
 }
 
@@ -829,6 +831,12 @@ NumBatchKernel pick_numerator_batch(int shape) {
 
 int enqueue_finalize(const SearchArgs &a, cudaStream_t stream, char *err, size_t errlen) {
     const int64_t P = a.stack->H * a.stack->W;
+    if (a.tab->plan.kernel == 2) {
+        LaunchScope ls(kKFinalize, stream);
+        return fac_finalize_enqueue(reinterpret_cast<const float *>(a.ws + a.L.planes_off),
+                                    reinterpret_cast<const float *>(a.ws + a.L.isd_off), a.tab->plan.f_seg, a.tab->K,
+                                    P, a.snr_max, a.argmax, a.snr_all, stream, err, errlen);
+    }
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + a.L.keys_off);
     {
         LaunchScope ls(kKFinalize, stream);

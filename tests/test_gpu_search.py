@@ -184,27 +184,29 @@ def test_every_cta_shape(mf, oracle, shape, vec, lockstep):
 
 
 FACTORED = [
-    # group, tile_h, tile_w, stages (0 = planner's choice)
-    (1, 0, 32, 0),
-    (1, 0, 64, 0),
-    (2, 0, 64, 2),
-    (3, 0, 32, 0),
-    (4, 128, 32, 4),
-    (5, 96, 32, 6),
-    (6, 64, 32, 5),
-    (8, 64, 32, 3),
-    (16, 32, 32, 2),
-    (2, 32, 64, 0),
+    # group, tile_h, tile_w, stages, segments (0 = planner's choice)
+    (1, 0, 32, 0, 1),
+    (1, 0, 64, 0, 2),
+    (2, 0, 64, 2, 0),
+    (3, 0, 32, 0, 3),
+    (4, 128, 32, 4, 1),
+    (5, 96, 32, 6, 5),
+    (6, 64, 32, 5, 2),
+    (8, 64, 32, 3, 4),
+    (16, 32, 32, 2, 1),
+    (2, 32, 64, 0, 3),
+    (4, 64, 32, 3, 5),
 ]
 
 
-@pytest.mark.parametrize("group,tile_h,tile_w,stages", FACTORED)
-def test_factored_layouts(mf, oracle, group, tile_h, tile_w, stages):
+@pytest.mark.parametrize("group,tile_h,tile_w,stages,segments", FACTORED)
+def test_factored_layouts(mf, oracle, group, tile_h, tile_w, stages, segments):
     """The factored numerator (row pass shared by the trajectories of one v_x,
     column pass per trajectory) gives the oracle's answer for every CTA
-    geometry and stage count, on a ragged frame spanning several tiles, with
-    more frames than a record chunk and a frame block, and a grid whose v_y
-    spread makes the window rows differ from frame to frame."""
+    geometry, stage count and number of time segments (segments of 8 to 40
+    frames), on a ragged frame spanning several tiles, with more frames than a
+    record chunk and a frame block, and a grid whose v_y spread makes the
+    window rows differ from frame to frame."""
     from paper_2209_09848_gb300 import synth
     T, H, W = 40, 203, 157
     c = synth.small_case(T, H, W, 60 + group, mask_frac=0.02, movers=3)
@@ -213,8 +215,10 @@ def test_factored_layouts(mf, oracle, group, tile_h, tile_w, stages):
     vx = np.repeat(gx, gy.size)
     vy = np.tile(gy, gx.size)
     table = mf.prf_table_create(vx, vy, T, kernel=2, group=group, tile_h=tile_h or None, tile_w=tile_w,
-                                stages=stages or None)
+                                stages=stages or None, segments=segments or None)
     info = table.info()
+    if segments:
+        assert info["time_segments"] == segments
     assert info["kernel"] == 2 and info["warps_per_group"] == group and info["tile_w"] == tile_w
     if tile_h:
         assert info["tile_h"] == tile_h

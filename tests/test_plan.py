@@ -48,8 +48,9 @@ def test_distinct_vx_gives_single_trajectory_groups(mf):
 
 def test_forced_geometry_is_reported(mf):
     vx, vy = _grid(10, 10)
-    info = mf.prf_plan(vx, vy, 1000, kernel=2, group=4, tile_h=128, tile_w=32, stages=3)
+    info = mf.prf_plan(vx, vy, 1000, kernel=2, group=4, tile_h=128, tile_w=32, stages=3, segments=1)
     assert (info["warps_per_group"], info["tile_h"], info["tile_w"], info["stages"]) == (4, 128, 32, 3)
+    assert info["time_segments"] == 1
     assert info["groups"] == 30
     # rows: tile + footprint + the largest s_y spread of a group; the 10 v_y
     # of a column split into groups of 4, 3 and 3 consecutive values
@@ -60,7 +61,8 @@ def test_forced_geometry_is_reported(mf):
 
 
 @pytest.mark.parametrize("opts", [dict(kernel=3), dict(kernel=2, group=17), dict(kernel=2, tile_h=48),
-                                  dict(kernel=2, tile_w=96), dict(kernel=2, stages=1), dict(kernel=2, stages=7)])
+                                  dict(kernel=2, tile_w=96), dict(kernel=2, stages=1), dict(kernel=2, stages=7),
+                                  dict(kernel=2, segments=17), dict(kernel=2, segments=-1)])
 def test_invalid_layout_options(mf, opts):
     vx, vy = _grid(3, 3)
     with pytest.raises(mf.MFError) as e:
@@ -72,7 +74,25 @@ def test_window_too_tall_is_unsupported(mf):
     # 10 v_y spanning 2 px/frame over 140 frames: no group of 10 fits 256 rows
     vx, vy = _grid(2, 10, -1.0, 1.0)
     with pytest.raises(mf.MFError) as e:
-        mf.prf_plan(vx, vy, 140, kernel=2, group=10)
+        mf.prf_plan(vx, vy, 140, kernel=2, group=10, segments=1)
     assert e.value.status == 5
+    # shorter time segments bring the spread under the limit
+    assert mf.prf_plan(vx, vy, 140, kernel=2, group=10)["window_rows"] <= 256
     info = mf.prf_plan(vx, vy, 140)  # the planner splits the columns instead
     assert info["kernel"] == 2 and info["window_rows"] <= 256
+
+
+def test_segments_shrink_the_window(mf):
+    """Within a time segment a CTA follows each trajectory from its position
+    at the segment's first frame, so the window rows shrink roughly as the
+    segment length; the planner splits the paper grid's frames."""
+    vx, vy = _grid(10, 10)
+    rows = {S: mf.prf_plan(vx, vy, 1000, kernel=2, group=5, tile_h=96, tile_w=32, segments=S)["window_rows"]
+            for S in (1, 2, 4, 8)}
+    assert rows[1] > rows[2] > rows[4] > rows[8] >= 96 + 4
+    assert rows[1] - 100 > 3 * (rows[4] - 100)
+    assert mf.prf_plan(vx, vy, 1000)["time_segments"] > 1
+    # segments start on whole record chunks of 8 frames: 24 frames hold 3
+    assert mf.prf_plan(vx, vy, 24, kernel=2, segments=3)["time_segments"] == 3
+    with pytest.raises(mf.MFError):
+        mf.prf_plan(vx, vy, 24, kernel=2, segments=4)
