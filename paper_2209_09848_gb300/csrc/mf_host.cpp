@@ -376,6 +376,9 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
             const double hc = mf::fac_hcols(geo.tw), rp = mf::fac_rpitch(geo.tw);
             const double ni = hc / mf::kFacItem;
             const double sub = (geo.th / 32) * (geo.tw / 32);
+            // the column-pass warps are dealt to the SM's four schedulers; the
+            // busiest sets the pace
+            const double skew = (double)((warps + 3) / 4 * 4) / warps;
             double cyc = 0.0;
             for (int g = 0; g < G; g++) {
                 const double n = (double)groups[g].size();
@@ -386,12 +389,15 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
                     double seg = 0.0;
                     for (int f = t0[j]; f < t0[j + 1]; f++) {
                         const double nr = nrows[(size_t)g * T + f];
-                        const double fma = (n * geo.th * geo.tw * 5.0 + nr * hc * 5.0) / 128.0;
-                        const double sm = (n * sub * 40.0 * 128.0 + nr * ni * 160.0 + bh * rp * 4.0) / 128.0;
+                        // the row pass overlaps the column passes of other warps:
+                        // weighted by what measurements of the two fitted
+                        const double fma = (n * geo.th * geo.tw * 5.0 * skew + 0.5 * nr * hc * 5.0) / 128.0;
+                        const double sm = (n * sub * 40.0 * 128.0 + 0.5 * nr * ni * 160.0 + bh * rp * 4.0) / 128.0;
                         const double rounds = std::ceil(2.0 * nr * ni / threads);
                         seg += std::max(fma, sm) / 0.8 + 200.0 + 300.0 * (rounds - 1.0);
                     }
-                    cyc += seg * extra;
+                    // prologue (first windows in flight) and epilogue of each CTA
+                    cyc += (seg + 20000.0) * extra;
                 }
             }
             // planes: S x K x 4 bytes written and read per pixel (at ~6.7 TB/s,
