@@ -338,26 +338,28 @@ def run_ours(args):
 
     # end to end through the host-buffer entry point (mf_search_host): every
     # step uploads its stack from pinned host memory, searches, re-scores and
-    # downloads the maps and candidates; steps alternate between two streams
-    # and two workspaces, so one step's upload overlaps the previous step's
-    # kernels (each step's copies stay inside the timed region)
+    # downloads the maps and candidates; uploads go on a copy stream and steps
+    # alternate two workspaces (ordered by one event each), so one step's
+    # upload overlaps the previous step's kernels on the compute stream (each
+    # step's copies stay inside the timed region)
     e2e = None
     if not args.no_e2e:
         host = torch.empty((T, H, W), dtype=torch.float32, pin_memory=True)
         host.copy_(res)
         k_top = 0 if args.no_rescore else K_TOP
-        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        comp, copy = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        frees = [torch.cuda.Event(), torch.cuda.Event()]
         wss = [torch.empty(mf.search_host_workspace_size(host, table, k_top), dtype=torch.uint8, device=dev)
-               for _ in streams]
+               for _ in frees]
         outs = [(torch.empty((H, W), dtype=torch.float32, pin_memory=True),
                  torch.empty((H, W), dtype=torch.int32, pin_memory=True),
                  torch.zeros((k_top, mf.CANDIDATE_BYTES), dtype=torch.uint8, pin_memory=True) if k_top else None,
-                 torch.zeros(1, dtype=torch.int32, pin_memory=True) if k_top else None) for _ in streams]
+                 torch.zeros(1, dtype=torch.int32, pin_memory=True) if k_top else None) for _ in frees]
         e2e_steps = max(2, args.steps)
         # one untimed pass through each stream and workspace
         for i in range(2):
             mf.search_host(host, sigma, table, mask=mask, k_top=k_top, workspace=wss[i], out=outs[i],
-                           stream=streams[i])
+                           stream=comp, copy_stream=copy, ws_free=frees[i])
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
@@ -365,14 +367,15 @@ def run_ours(args):
         for i in range(e2e_steps):
             j = i % 2
             mf.search_host(host, sigma, table, mask=mask, k_top=k_top, workspace=wss[j], out=outs[j],
-                           stream=streams[j])
+                           stream=comp, copy_stream=copy, ws_free=frees[j])
         torch.cuda.synchronize(dev)
         e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dist, dev)
         same = bool(torch.equal(outs[(e2e_steps - 1) % 2][0], snr_max.cpu()))
         e2e = {"value": job_throughput(units_rank, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
                "d2h_bytes_per_step": H * W * 8 + (k_top * mf.CANDIDATE_BYTES + 4 if k_top else 0),
                "steps": e2e_steps, "call": "mf_search_host (pinned host stack in, host maps and candidates out)",
-               "pipelined": "2 streams x 2 workspaces: a step's upload overlaps the previous step's kernels",
+               "pipelined": "copy stream + compute stream, 2 workspaces: a step's upload overlaps the previous "
+                            "step's kernels",
                "maps_equal_device_timed_run": same}
         del host, wss
 

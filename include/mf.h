@@ -300,9 +300,16 @@ mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint
  *   workspace   DEVICE memory of mf_search_host_workspace_size bytes,
  *               256-byte aligned (holds the stack copy, the maps and the
  *               search / rescore workspaces).
- * Results are valid once the stream has reached them (synchronise it).
- * Calls on different streams with different workspaces overlap: one call's
- * upload runs on the copy engine while another's kernels run.
+ *   copy_stream NULL: everything runs on `stream`.  Otherwise the upload
+ *               runs on copy_stream and `stream` waits for it before the
+ *               kernels, so a caller that alternates two workspaces keeps
+ *               uploading the next stack while the kernels of the previous
+ *               one run on `stream`;
+ *   ws_free     NULL, or a CUDA event (cudaEvent_t) tied to this workspace:
+ *               the upload waits for it and the call records it on `stream`
+ *               once it no longer needs the workspace (after the download);
+ *               pass the same event with the same workspace every time.
+ * Results are valid once `stream` has reached them (synchronise it).
  * Errors: those of mf_search and mf_rescore_topk, plus MF_EINVAL for a
  * missing output or a small workspace; nothing is enqueued on MF_EINVAL. */
 mf_status mf_search_host_workspace_size(const mf_stack *stack, const mf_prf_table *table,
@@ -310,7 +317,8 @@ mf_status mf_search_host_workspace_size(const mf_stack *stack, const mf_prf_tabl
 mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const uint8_t *mask,
                          const mf_prf_table *table, float *snr_max_host, int32_t *argmax_host,
                          int32_t k_top, mf_candidate *cand_host, int32_t *n_cand_host,
-                         void *workspace, size_t workspace_bytes, mf_stream stream);
+                         void *workspace, size_t workspace_bytes, mf_stream stream,
+                         mf_stream copy_stream, void *ws_free);
 
 /* Per-kernel accounting of the library's own launches (for benchmarks and
  * roofline reports; not in the paper).  Launch counts are always kept; device

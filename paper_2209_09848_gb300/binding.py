@@ -123,7 +123,7 @@ def load():
             "mf_rescore_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
             "mf_search_host_workspace_size": ([ctypes.POINTER(Stack), P, I32, ctypes.POINTER(SZ)], ctypes.c_int),
-            "mf_search_host": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
+            "mf_search_host": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P, P, P], ctypes.c_int),
             "mf_profile_enable": ([I32], ctypes.c_int),
             "mf_profile_read": ([ctypes.POINTER(Profile), I32], ctypes.c_int),
             "mf_batch_create": ([pp], ctypes.c_int),
@@ -346,12 +346,15 @@ def search_host_workspace_size(stack: torch.Tensor, table: PrfTable, k_top: int 
 
 
 def search_host(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torch.Tensor | None = None,
-                frame_scale: torch.Tensor | None = None, k_top: int = 0, workspace=None, out=None, stream=None):
+                frame_scale: torch.Tensor | None = None, k_top: int = 0, workspace=None, out=None, stream=None,
+                copy_stream=None, ws_free=None):
     """mf_search_host: the stack is a CPU tensor (pinned for asynchronous
     upload), sigma / mask / frame_scale live on the GPU; returns CPU tensors
     (snr_max [H, W], argmax [H, W], candidate records [k_top] uint8 or None,
     n_candidates [1] int32 or None), valid after the stream is synchronised.
-    `out` may pass those four tensors (pinned) to reuse them."""
+    `out` may pass those four tensors (pinned) to reuse them.  copy_stream
+    (torch.cuda.Stream) runs the upload apart from the kernels; ws_free
+    (torch.cuda.Event) orders calls that reuse one workspace."""
     if stack.device.type != "cpu":
         raise ValueError("search_host takes a CPU stack; use search for device stacks")
     st = make_stack(stack, frame_scale)
@@ -366,9 +369,14 @@ def search_host(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask:
     else:
         smax, amax, cand, ncand = out
     ws = _workspace(search_host_workspace_size(stack, table, k_top), dev, workspace)
+    if ws_free is not None and not ws_free.cuda_event:
+        # torch creates the CUDA event on its first record: make it exist
+        ws_free.record(stream if stream is not None else torch.cuda.current_stream())
     _check(load().mf_search_host(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(smax), _ptr(amax),
                                  int(k_top), _ptr(cand), _ptr(ncand), _ptr(ws), ws.numel() * ws.element_size(),
-                                 _stream_ptr(stream)))
+                                 _stream_ptr(stream),
+                                 None if copy_stream is None else ctypes.c_void_p(copy_stream.cuda_stream),
+                                 None if ws_free is None else ctypes.c_void_p(ws_free.cuda_event)))
     return smax, amax, cand, ncand
 
 

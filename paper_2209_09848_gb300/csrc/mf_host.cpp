@@ -1310,7 +1310,7 @@ mf_status mf_search_host_workspace_size(const mf_stack *stack, const mf_prf_tabl
 mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const uint8_t *mask,
                          const mf_prf_table *table, float *snr_max_host, int32_t *argmax_host, int32_t k_top,
                          mf_candidate *cand_host, int32_t *n_cand_host, void *workspace, size_t workspace_bytes,
-                         mf_stream stream) {
+                         mf_stream stream, mf_stream copy_stream, void *ws_free) {
     mf_status s = check_stack(host_stack);
     if (s != MF_OK) return s;
     if (!table) return fail(MF_EINVAL, "table is NULL");
@@ -1331,20 +1331,30 @@ mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const u
         return fail(MF_EINVAL, "table lives on device %d, current device is %d", table->device, dev);
     char *ws = (char *)workspace;
     cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t up = copy_stream ? (cudaStream_t)copy_stream : st;
+    cudaEvent_t freed = (cudaEvent_t)ws_free;
     const size_t es = elem_size(host_stack->dtype);
+    cudaError_t e = cudaSuccess;
+    if (freed) e = cudaStreamWaitEvent(up, freed, 0);  // the previous call on this workspace is done with it
     // upload: one 2-D copy when rows are contiguous, else one per frame
-    cudaError_t e;
-    if (host_stack->row_stride == W) {
+    if (e == cudaSuccess && host_stack->row_stride == W) {
         e = cudaMemcpy2DAsync(ws + L.stack_off, (size_t)H * W * es, host_stack->data,
                               (size_t)(T > 1 ? host_stack->frame_stride : H * W) * es, (size_t)H * W * es, (size_t)T,
-                              cudaMemcpyHostToDevice, st);
+                              cudaMemcpyHostToDevice, up);
     } else {
-        e = cudaSuccess;
         for (int64_t t = 0; t < T && e == cudaSuccess; t++)
             e = cudaMemcpy2DAsync(ws + L.stack_off + (size_t)t * H * W * es, (size_t)W * es,
                                   (const char *)host_stack->data + (size_t)t * host_stack->frame_stride * es,
                                   (size_t)host_stack->row_stride * es, (size_t)W * es, (size_t)H,
-                                  cudaMemcpyHostToDevice, st);
+                                  cudaMemcpyHostToDevice, up);
+    }
+    if (e == cudaSuccess && up != st) {
+        // the kernels wait for the upload (the event object may go once the wait is enqueued)
+        cudaEvent_t landed = nullptr;
+        e = cudaEventCreateWithFlags(&landed, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(landed, up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, landed, 0);
+        if (landed) cudaEventDestroy(landed);
     }
     if (e != cudaSuccess) return fail(MF_ECUDA, "stack upload: %s", cudaGetErrorString(e));
     mf_stack dstack = *host_stack;
@@ -1368,6 +1378,7 @@ mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const u
                             st);
     if (e == cudaSuccess && k_top > 0)
         e = cudaMemcpyAsync(n_cand_host, ws + L.n_off, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && freed) e = cudaEventRecord(freed, st);
     if (e != cudaSuccess) return fail(MF_ECUDA, "result download: %s", cudaGetErrorString(e));
     return ok();
 }

@@ -70,3 +70,32 @@ def test_host_stack_against_oracle_and_errors(mf, oracle):
         mf.search_host(host, sigma, table, mask=mask, workspace=torch.empty(256, dtype=torch.uint8, device="cuda"))
     with pytest.raises(mf.MFError):  # k_top beyond the pixels
         mf.search_host(host, sigma, table, mask=mask, k_top=H * W + 1)
+
+
+def test_pipelined_calls_keep_their_own_results(mf):
+    """Uploads on a copy stream, kernels on one compute stream, two
+    workspaces alternating with one event each: four different stacks in
+    flight give exactly their own device-stack results."""
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 18, 70, 66
+    vx, vy = synth.velocity_grid(3, 3, -0.3, 0.3)
+    table = mf.prf_table_create(vx, vy, T)
+    cases = [synth.small_case(T, H, W, 40 + i, mask_frac=0.01, movers=2) for i in range(4)]
+    sigma = torch.from_numpy(cases[0]["sigma"]).cuda()
+    hosts = [torch.from_numpy(c["res"]).pin_memory() for c in cases]
+    comp, copy = torch.cuda.Stream(), torch.cuda.Stream()
+    frees = [torch.cuda.Event(), torch.cuda.Event()]
+    wss = [torch.empty(mf.search_host_workspace_size(hosts[0], table, 20), dtype=torch.uint8, device="cuda")
+           for _ in frees]
+    outs = []
+    for i, h in enumerate(hosts):
+        outs.append(mf.search_host(h, sigma, table, k_top=20, workspace=wss[i % 2], stream=comp,
+                                   copy_stream=copy, ws_free=frees[i % 2]))
+    torch.cuda.synchronize()
+    assert mf.device_status() == 0
+    for h, (smax, amax, cand, n) in zip(hosts, outs):
+        dm, da, _ = mf.search(h.cuda(), sigma, table)
+        raw, dn = mf.rescore_topk(h.cuda(), sigma, table, dm, da, 20)
+        torch.cuda.synchronize()
+        assert torch.equal(smax, dm.cpu()) and torch.equal(amax, da.cpu())
+        assert torch.equal(cand, raw.cpu()) and int(n.item()) == int(dn.item())
