@@ -150,14 +150,14 @@ def flop_per_unit(kernel: int, vx) -> float:
 
 
 def _traffic_from_profiles(kernel: int = 2):
-    """DRAM bytes per numerator launch from the committed ncu summary of the
-    kernel the plan uses, if any."""
+    """DRAM bytes of the numerator per step (all its launches) from the
+    committed ncu summary of the kernel the plan uses, if any."""
     name = "k_numerator_fac_paper_shaped.md" if kernel == 2 else "k_numerator_paper_shaped.md"
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             for line in f:
-                if line.startswith("traffic_bytes_per_full_launch:"):
+                if line.startswith("traffic_bytes_per_step:"):
                     v = line.split(":", 1)[1].strip()
                     return None if v in ("", "null") else float(v)
     except OSError:
@@ -327,13 +327,15 @@ def run_ours(args):
     value = job_throughput(units_rank, ws, ms * 1e-3)
 
     peaks, peak_src = _peaks()
+    # numerator time per step (a factored plan with time segments makes one
+    # launch per segment)
     num_launches, num_ms_total = prof["k_numerator"]
-    num_ms = num_ms_total / max(1, num_launches)
+    num_ms = num_ms_total / args.steps
     peak_tf = _fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
     fpu = flop_per_unit(info["kernel"], vx)
     achieved_tf = units_rank * fpu / (num_ms * 1e-3) / 1e12
     traffic = _traffic_from_profiles(info["kernel"])
-    kernel_ms = {k: round(v[1] / max(1, v[0]), 3) for k, v in prof.items() if k != "_launches" and v[0]}
+    kernel_ms = {k: round(v[1] / args.steps, 3) for k, v in prof.items() if k != "_launches" and v[0]}
     launches = int(prof["_launches"])
 
     # end to end through the host-buffer entry point (mf_search_host): every
@@ -415,8 +417,9 @@ def run_ours(args):
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s)" % (
                              float(peaks.get("sm_max_mhz", 2070.0)), peak_src),
-                         "flop_per_unit": fpu, "avg_launch_ms": num_ms},
-            "kernel_ms": kernel_ms,
+                         "flop_per_unit": fpu, "numerator_ms_per_step": num_ms,
+                         "numerator_launches_per_step": num_launches // args.steps},
+            "kernel_ms_per_step": kernel_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -636,7 +639,7 @@ def run_precision(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         prof = mf.profile_read(reset=True)
-        num_ms = prof["k_numerator"][1] / max(1, prof["k_numerator"][0])
+        num_ms = prof["k_numerator"][1] / args.steps  # per step: one launch per time segment
         g_max = smax.cpu().numpy()[ys, xs].astype(np.float64)
         err = np.abs(g_max - o_max) / np.maximum(1.0, np.abs(o_max))
         cands = mf.decode_candidates(raw, int(n.item()))

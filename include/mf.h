@@ -140,8 +140,9 @@ mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const 
  * consecutive frame ranges the frames are split into (1..16): within a
  * segment a CTA follows each trajectory from where it stands at the
  * segment's first frame, so the rows a group's window spans grow with the
- * segment's length instead of the stack's; each segment's numerators go to
- * their own plane and are summed per pixel at the end; 0 = planner's choice.
+ * segment's length instead of the stack's; segments run as consecutive
+ * launches, the first storing the numerators and the others adding to them
+ * (a fixed summation order); 0 = planner's choice.
  * An autotuner times several layouts and keeps the fastest. */
 typedef struct {
     int32_t shape;

@@ -72,35 +72,29 @@ __device__ __forceinline__ void row_item(const float *__restrict__ src, float *_
         reinterpret_cast<float4 *>(dst)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
-// The (group, segment, tile) of CTA `cta` of a search, in the order
-// segment, tile row, tile column, group: the CTAs running at the same time
-// then read the same frames of neighbouring tiles for every group, which
-// keeps those frames in L2.  Tile rows are in reference coordinates (a
+// The (group, tile) of CTA `cta` of the launch that computes segment p.seg,
+// in the order tile row, tile column, group: the CTAs running at the same
+// time then read the same frames of neighbouring tiles for every group,
+// which keeps those frames in L2.  Tile rows are in reference coordinates (a
 // trajectory's start pixel is the tile pixel minus its s_y at the segment's
-// first frame) and start at the group's smallest such s_y; every group of a
-// segment gets as many tile rows as the group with the widest spread needs,
+// first frame) and start at the group's smallest such s_y; every group gets
+// as many tile rows as the segment's widest spread needs,
 // ceil((H + spread) / tile_h).  False if cta is past the last tile.
-__device__ __forceinline__ bool fac_locate(const FacParams &p, int tw, long long cta, int &g, int &j, int &y0,
-                                           int &x0, int &t0, int &t1) {
+__device__ __forceinline__ bool fac_locate(const FacParams &p, int tw, long long cta, int &g, int &y0, int &x0,
+                                           int &t0, int &t1) {
     const int4 *segs = reinterpret_cast<const int4 *>(p.segs);
-    for (j = 0; j < p.S; j++) {
-        int spread = 0;
-        for (int e = 0; e < p.G; e++) spread = max(spread, segs[(size_t)e * p.S + j].w);
-        const long long rows = (p.H + spread + p.th - 1) / p.th;
-        const long long n = rows * p.tiles_x * p.G;
-        if (cta < n) {
-            g = (int)(cta % p.G);
-            const long long rest = cta / p.G;
-            const int4 sg = segs[(size_t)g * p.S + j];
-            y0 = sg.z + (int)(rest / p.tiles_x) * p.th;
-            x0 = (int)(rest % p.tiles_x) * tw;
-            t0 = sg.x;
-            t1 = sg.y;
-            return true;
-        }
-        cta -= n;
-    }
-    return false;
+    int spread = 0;
+    for (int e = 0; e < p.G; e++) spread = max(spread, segs[(size_t)e * p.S + p.seg].w);
+    const long long rows = (p.H + spread + p.th - 1) / p.th;
+    if (cta >= rows * p.tiles_x * p.G) return false;
+    g = (int)(cta % p.G);
+    const long long rest = cta / p.G;
+    const int4 sg = segs[(size_t)g * p.S + p.seg];
+    y0 = sg.z + (int)(rest / p.tiles_x) * p.th;
+    x0 = (int)(rest % p.tiles_x) * tw;
+    t0 = sg.x;
+    t1 = sg.y;
+    return true;
 }
 
 template <int TW>
@@ -111,8 +105,9 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     constexpr int NSUBX = TW / 32;
 
     const int NS = p.ns, BH = p.bh, KT = p.kt;
-    int g = 0, seg = 0, tile_y0 = 0, tile_x0 = 0, t0 = 0, t1 = 0;
-    if (!fac_locate(p, TW, cta, g, seg, tile_y0, tile_x0, t0, t1)) return true;  // uniform: nothing to do
+    const int seg = p.seg;
+    int g = 0, tile_y0 = 0, tile_x0 = 0, t0 = 0, t1 = 0;
+    if (!fac_locate(p, TW, cta, g, tile_y0, tile_x0, t0, t1)) return true;  // uniform: nothing to do
     {
         // a tile row past every member's start pixels (groups with a smaller
         // spread than the segment's widest) has nothing to compute
@@ -280,18 +275,23 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         return false;
     }
 
-    // Epilogue: this segment's numerator of each (trajectory, start pixel) into
-    // the segment's plane; the start pixel is the tile pixel minus the
-    // trajectory's s_y at the segment's first frame (each is written once)
+    // Epilogue: this segment's numerator of each (trajectory, start pixel)
+    // into the plane, stored by segment 0 and added by the later segments
+    // (launched in order, so the sum follows the segment order); the start
+    // pixel is the tile pixel minus the trajectory's s_y at the segment's
+    // first frame, and each is reached by one CTA of the launch
     const int64_t P = p.H * p.W;
     if (kk >= 0) {
-        float *plane = p.planes + ((size_t)seg * p.K + kk) * P;
+        float *plane = p.plane + (size_t)kk * P;
 #pragma unroll
         for (int r = 0; r < 32; r++) {
             const int rr = r >> 1, jj = r & 1;
             const int64_t px = tile_x0 + 32 * sub_x + 2 * cp + jj;
             const int64_t py = (int64_t)tile_y0 + 32 * sub_y + 16 * rh + rr - ref;
-            if (py >= 0 && py < p.H && px < p.W) plane[py * p.W + px] = acc[r] + blk[r];
+            if (py >= 0 && py < p.H && px < p.W) {
+                const int64_t q = py * p.W + px;
+                plane[q] = seg == 0 ? acc[r] + blk[r] : plane[q] + (acc[r] + blk[r]);
+            }
         }
     }
     // the barriers may be initialised again for this CTA's next tile
@@ -343,14 +343,13 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMa
     }
 }
 
-// Per pixel: N_k = sum of the segment planes (segment order), SNR = N_k /
-// sqrt(D_k) over the filters with D_k > 0, the maximum and the smallest k
-// attaining it (-1 and 0 where no filter has D > 0), and optionally the SNR
-// cube (0 where D = 0).  V consecutive pixels per thread (V = 4 when P is a
-// multiple of 4: 128-bit loads).
+// Per pixel: SNR_k = N_k / sqrt(D_k) over the filters with D_k > 0, the
+// maximum and the smallest k attaining it (-1 and 0 where no filter has
+// D > 0), and optionally the SNR cube (0 where D = 0).  V consecutive pixels
+// per thread (V = 4 when P is a multiple of 4: 128-bit loads).
 template <int V>
-__global__ void k_finalize_planes(const float *__restrict__ planes, const float *__restrict__ isd, int S, int K,
-                                  int64_t P, float *__restrict__ snr_max, int32_t *__restrict__ argmax,
+__global__ void k_finalize_planes(const float *__restrict__ plane, const float *__restrict__ isd, int K, int64_t P,
+                                  float *__restrict__ snr_max, int32_t *__restrict__ argmax,
                                   float *__restrict__ snr_all) {
     using VecT = typename std::conditional<V == 4, float4, float>::type;
     const int64_t n = P / V;
@@ -363,21 +362,14 @@ __global__ void k_finalize_planes(const float *__restrict__ planes, const float 
             arg[v] = -1;
         }
         for (int k = 0; k < K; k++) {
-            float nk[V];
-#pragma unroll
-            for (int v = 0; v < V; v++) nk[v] = 0.f;
-            for (int j = 0; j < S; j++) {
-                const VecT x = reinterpret_cast<const VecT *>(planes + ((int64_t)j * K + k) * P)[i];
-                const float *xf = reinterpret_cast<const float *>(&x);
-#pragma unroll
-                for (int v = 0; v < V; v++) nk[v] += xf[v];
-            }
+            const VecT xv = reinterpret_cast<const VecT *>(plane + (int64_t)k * P)[i];
             const VecT dv = reinterpret_cast<const VecT *>(isd + (int64_t)k * P)[i];
+            const float *x = reinterpret_cast<const float *>(&xv);
             const float *d = reinterpret_cast<const float *>(&dv);
             float snr[V];
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                snr[v] = nk[v] * d[v];
+                snr[v] = x[v] * d[v];
                 if (d[v] > 0.f && (arg[v] < 0 || snr[v] > best[v])) {
                     best[v] = snr[v];
                     arg[v] = k;
@@ -396,18 +388,18 @@ __global__ void k_finalize_planes(const float *__restrict__ planes, const float 
 
 }  // namespace
 
-int fac_finalize_enqueue(const float *planes, const float *isd, int S, int K, int64_t P, float *snr_max,
-                         int32_t *argmax, float *snr_all, void *stream, char *err, size_t errlen) {
+int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P, float *snr_max, int32_t *argmax,
+                         float *snr_all, void *stream, char *err, size_t errlen) {
     if (P <= 0) return 0;
     const bool vec = P % 4 == 0 && (uintptr_t)snr_all % 16 == 0;
     const int64_t items = vec ? P / 4 : P;
     int64_t blocks = (items + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (vec)
-        k_finalize_planes<4><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(planes, isd, S, K, P, snr_max, argmax,
+        k_finalize_planes<4><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(plane, isd, K, P, snr_max, argmax,
                                                                                  snr_all);
     else
-        k_finalize_planes<1><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(planes, isd, S, K, P, snr_max, argmax,
+        k_finalize_planes<1><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(plane, isd, K, P, snr_max, argmax,
                                                                                  snr_all);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -400,10 +400,10 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
                     cyc += (seg + 20000.0) * extra;
                 }
             }
-            // planes: S x K x 4 bytes written and read per pixel (at ~6.7 TB/s,
-            // 152 SMs at 2.07 GHz: 0.38 S K cycles per pixel), and the extra
-            // CTA prologues and epilogues per segment (measured: about three
-            // times the traffic term)
+            // plane: K x 4 bytes written per segment and read by the next (at
+            // ~6.7 TB/s, 152 SMs at 2.07 GHz: 0.38 K cycles per pixel each),
+            // the extra CTA prologues and epilogues and the launch tail per
+            // segment (measured: about three times the traffic term)
             p.cost = cyc / ((double)geo.th * geo.tw) + 1.2 * S * K;
             p.G = G;
             p.members.assign((size_t)G * geo.kt, -1);
@@ -818,16 +818,13 @@ namespace mf {
 
 mf_status set_error(mf_status s, const char *msg) { return fail(s, "%s", msg); }
 
-long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W) {
+long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W, int seg) {
     const Plan &p = tab.plan;
+    if (seg < 0 || seg >= p.f_seg) return 0;
     const long long tiles_x = (W + p.f_tw - 1) / p.f_tw;
-    long long n = 0;
-    for (int j = 0; j < p.f_seg; j++) {
-        int spread = 0;
-        for (int g = 0; g < p.G; g++) spread = std::max(spread, p.seg_qy[((size_t)g * p.f_seg + j) * 2 + 1]);
-        n += (H + spread + p.f_th - 1) / p.f_th * tiles_x * p.G;
-    }
-    return n;
+    int spread = 0;
+    for (int g = 0; g < p.G; g++) spread = std::max(spread, p.seg_qy[((size_t)g * p.f_seg + seg) * 2 + 1]);
+    return (H + spread + p.f_th - 1) / p.f_th * tiles_x * p.G;
 }
 
 WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab) {
@@ -848,7 +845,7 @@ WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_tabl
     L.y_off = take((size_t)T * H * L.y_pitch * sizeof(float));
     L.isd_off = take((size_t)tab->K * H * W * sizeof(float));
     L.keys_off = take((size_t)H * W * sizeof(unsigned long long));
-    L.planes_off = take(tab->plan.kernel == 2 ? (size_t)tab->plan.f_seg * tab->K * H * W * sizeof(float) : 0);
+    L.planes_off = take(tab->plan.kernel == 2 ? (size_t)tab->K * H * W * sizeof(float) : 0);
     L.total = off;
     return L;
 }

@@ -274,20 +274,21 @@ struct FacParams {
     const int32_t *members;       // [G][kt] trajectory of each slot, -1 for none
     const int32_t *segs;          // [G][S][4] first frame, end frame, min s_y, spread
     const int32_t *refs;          // [G][S][kt] s_y of each slot at the segment's first frame
-    float *planes;                // [S][K][H][W] numerator of each segment
+    float *plane;                 // [K][H][W] numerator: segment 0 stores, later segments add
     int *status;                  // device status word
     int T, G, kt, th, bh, ns, S, K;
+    int seg;                      // the segment this launch computes
     int warps;                    // warps of the layout (a batched launch may have more)
     int64_t H, W;
     int tiles_x;
 };
-// Sum of the segment planes, SNR with 1 / sqrt(D), per-pixel max over k
+// SNR with 1 / sqrt(D) from the numerator plane, per-pixel max over k
 // (smallest k on ties) and the optional SNR cube.
-int fac_finalize_enqueue(const float *planes, const float *isd, int S, int K, int64_t P, float *snr_max,
-                         int32_t *argmax, float *snr_all, void *stream, char *err, size_t errlen);
-// CTAs of a factored search: sum over (group, segment) of the tile rows
-// ceil((H + spread) / tile_h) times the tile columns.
-long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W);
+int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P, float *snr_max, int32_t *argmax,
+                         float *snr_all, void *stream, char *err, size_t errlen);
+// CTAs of segment `seg` of a factored search: groups x tile columns x tile
+// rows ceil((H + spread) / tile_h), spread the widest of the segment's groups.
+long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W, int seg);
 struct FacBatchItem {
     FacParams p;
     long long cta_begin;  // first entry of this search in the batch's work list

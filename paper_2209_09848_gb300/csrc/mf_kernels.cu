@@ -781,7 +781,7 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     fp->members = tab.d_members;
     fp->segs = tab.d_segs;
     fp->refs = tab.d_refs;
-    fp->planes = reinterpret_cast<float *>(a.ws + L.planes_off);
+    fp->plane = reinterpret_cast<float *>(a.ws + L.planes_off);
     fp->status = status;
     fp->T = (int)T;
     fp->G = pl.G;
@@ -790,12 +790,13 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     fp->bh = pl.f_bh;
     fp->ns = pl.f_ns;
     fp->S = pl.f_seg;
+    fp->seg = 0;
     fp->K = tab.K;
     fp->warps = pl.warps();
     fp->H = H;
     fp->W = W;
     fp->tiles_x = (int)((W + pl.f_tw - 1) / pl.f_tw);
-    *nblocks = fac_ctas(tab, H, W);
+    *nblocks = fac_ctas(tab, H, W, 0);
     return 0;
 }
 
@@ -834,8 +835,8 @@ int enqueue_finalize(const SearchArgs &a, cudaStream_t stream, char *err, size_t
     if (a.tab->plan.kernel == 2) {
         LaunchScope ls(kKFinalize, stream);
         return fac_finalize_enqueue(reinterpret_cast<const float *>(a.ws + a.L.planes_off),
-                                    reinterpret_cast<const float *>(a.ws + a.L.isd_off), a.tab->plan.f_seg, a.tab->K,
-                                    P, a.snr_max, a.argmax, a.snr_all, stream, err, errlen);
+                                    reinterpret_cast<const float *>(a.ws + a.L.isd_off), a.tab->K, P, a.snr_max,
+                                    a.argmax, a.snr_all, stream, err, errlen);
     }
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + a.L.keys_off);
     {
@@ -859,9 +860,16 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
         long long nblocks = 0;
         rc = fac_params(a, &map, &fp, &nblocks, err, errlen);
         if (rc) return rc;
-        LaunchScope ls(kKNumerator, stream);
-        rc = fac_enqueue(&map, fp, pl.f_tw, pl.launch_warps(), pl.smem(), nblocks, stream, err, errlen);
-        if (rc) return rc;
+        // one launch per time segment, in order: segment 0 stores the
+        // numerator plane, the later ones add to it
+        for (int j = 0; j < pl.f_seg; j++) {
+            fp.seg = j;
+            LaunchScope ls(kKNumerator, stream);
+            rc = fac_enqueue(&map, fp, pl.f_tw, pl.launch_warps(), pl.smem(), fac_ctas(*a.tab, a.stack->H,
+                                                                                       a.stack->W, j),
+                             stream, err, errlen);
+            if (rc) return rc;
+        }
         return enqueue_finalize(a, stream, err, errlen);
     }
     NumParams np;
@@ -906,6 +914,7 @@ struct BatchDevice {
     // layout needs
     struct FacGroup {
         int tw = 32;
+        int seg = 0;               // time segment (groups run in segment order)
         int first = 0, count = 0;  // range in d_fmaps / d_fitems
         long long total = 0;       // CTA work entries
         size_t smem = 0;
@@ -971,31 +980,38 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
     }
     std::vector<CUtensorMap> fmaps;
     std::vector<FacBatchItem> fitems;
-    for (int tw : {32, 64}) {
-        BatchDevice::FacGroup grp;
-        grp.tw = tw;
-        grp.first = (int)fitems.size();
-        for (int i = 0; i < n; i++) {
-            const Plan &pl = items[i].tab->plan;
-            if (pl.kernel != 2 || pl.f_tw != tw) continue;
-            CUtensorMap m;
-            FacBatchItem fi;
-            std::memset(&fi, 0, sizeof fi);
-            long long nblocks = 0;
-            int rc = fac_params(items[i], &m, &fi.p, &nblocks, err, errlen);
-            if (rc) {
-                batch_free(b);
-                return rc;
+    int max_seg = 0;
+    for (int i = 0; i < n; i++)
+        if (items[i].tab->plan.kernel == 2) max_seg = std::max(max_seg, items[i].tab->plan.f_seg);
+    for (int j = 0; j < max_seg; j++) {
+        for (int tw : {32, 64}) {
+            BatchDevice::FacGroup grp;
+            grp.tw = tw;
+            grp.seg = j;
+            grp.first = (int)fitems.size();
+            for (int i = 0; i < n; i++) {
+                const Plan &pl = items[i].tab->plan;
+                if (pl.kernel != 2 || pl.f_tw != tw || j >= pl.f_seg) continue;
+                CUtensorMap m;
+                FacBatchItem fi;
+                std::memset(&fi, 0, sizeof fi);
+                long long nblocks = 0;
+                int rc = fac_params(items[i], &m, &fi.p, &nblocks, err, errlen);
+                if (rc) {
+                    batch_free(b);
+                    return rc;
+                }
+                fi.p.seg = j;
+                fi.cta_begin = grp.total;
+                grp.total += fac_ctas(*items[i].tab, items[i].stack->H, items[i].stack->W, j);
+                grp.smem = std::max(grp.smem, pl.smem());
+                grp.warps = std::max(grp.warps, pl.launch_warps());
+                fmaps.push_back(m);
+                fitems.push_back(fi);
             }
-            fi.cta_begin = grp.total;
-            grp.total += nblocks;
-            grp.smem = std::max(grp.smem, pl.smem());
-            grp.warps = std::max(grp.warps, pl.launch_warps());
-            fmaps.push_back(m);
-            fitems.push_back(fi);
+            grp.count = (int)fitems.size() - grp.first;
+            if (grp.count > 0) b->fac.push_back(grp);
         }
-        grp.count = (int)fitems.size() - grp.first;
-        if (grp.count > 0) b->fac.push_back(grp);
     }
     cudaError_t e = cudaSuccess;
     if (!fitems.empty()) e = cudaMalloc((void **)&b->d_fmaps, fmaps.size() * sizeof(CUtensorMap));
@@ -1031,8 +1047,12 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         batch_free(b);
         return (int)e;
     }
-    for (const auto &grp : b->fac) {
-        const int rc = fac_batch_attr(grp.tw, grp.smem, err, errlen);
+    for (int tw : {32, 64}) {  // one attribute per kernel: the largest layout of that tile width
+        size_t smem = 0;
+        for (const auto &grp : b->fac)
+            if (grp.tw == tw) smem = std::max(smem, grp.smem);
+        if (smem == 0) continue;
+        const int rc = fac_batch_attr(tw, smem, err, errlen);
         if (rc) {
             batch_free(b);
             return rc;
