@@ -44,34 +44,29 @@ int64_t floor_div(int64_t a, int64_t b) {
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// 5x5 footprint of the PRF for a source at sub-pixel offset (phx, phy) from
-// the base pixel, renormalised to unit sum (Section 2: the PRF shares a point
-// source's flux between neighbouring pixels).
-// When fx / fy are given they receive the normalised 1-D factors: w[b * 5 +
-// a] = fy[b] * fx[a] up to rounding (the 5 x 5 sum is the product of the two
-// 1-D sums).
-void footprint(int kind, double sigma, double phx, double phy, double *w, double *fx = nullptr,
-               double *fy = nullptr) {
-    double gx[5], gy[5];
+// One axis of the PRF's 5 x 5 footprint for a source at sub-pixel offset ph
+// from the base pixel, before normalisation (Section 2: the PRF shares a
+// point source's flux between neighbouring pixels).  kind 0 integrates a
+// Gaussian over each pixel, kind 1 samples it at the pixel centre.
+void axis_profile(int kind, double sigma, double ph, double *g) {
     if (kind == 0) {
-        // pixel d spans [d - 1/2, d + 1/2]: six shared boundaries per axis
+        // pixel d spans [d - 1/2, d + 1/2]: six shared boundaries
         const double s = sigma * std::sqrt(2.0);
-        double ex[6], ey[6];
-        for (int i = 0; i < 6; i++) {
-            ex[i] = std::erf((i - 2.5 - phx) / s);
-            ey[i] = std::erf((i - 2.5 - phy) / s);
-        }
-        for (int i = 0; i < 5; i++) {
-            gx[i] = 0.5 * (ex[i + 1] - ex[i]);
-            gy[i] = 0.5 * (ey[i + 1] - ey[i]);
-        }
+        double e[6];
+        for (int i = 0; i < 6; i++) e[i] = std::erf((i - 2.5 - ph) / s);
+        for (int i = 0; i < 5; i++) g[i] = 0.5 * (e[i + 1] - e[i]);
     } else {
         for (int i = 0; i < 5; i++) {
             const int d = i - 2;
-            gx[i] = std::exp(-(d - phx) * (d - phx) / (2.0 * sigma * sigma));
-            gy[i] = std::exp(-(d - phy) * (d - phy) / (2.0 * sigma * sigma));
+            g[i] = std::exp(-(d - ph) * (d - ph) / (2.0 * sigma * sigma));
         }
     }
+}
+
+// The footprint from its two axis profiles, renormalised to unit sum, and
+// the normalised 1-D factors: w[b * 5 + a] = fy[b] * fx[a] up to rounding
+// (the 5 x 5 sum is the product of the two 1-D sums).
+void footprint_from_axes(const double *gx, const double *gy, double *w, double *fx, double *fy) {
     double total = 0.0;
     for (int b = 0; b < 5; b++)
         for (int a = 0; a < 5; a++) {
@@ -79,16 +74,14 @@ void footprint(int kind, double sigma, double phx, double phy, double *w, double
             total += w[b * 5 + a];
         }
     for (int i = 0; i < 25; i++) w[i] /= total;
-    if (fx && fy) {
-        double sx = 0.0, sy = 0.0;
-        for (int i = 0; i < 5; i++) {
-            sx += gx[i];
-            sy += gy[i];
-        }
-        for (int i = 0; i < 5; i++) {
-            fx[i] = gx[i] / sx;
-            fy[i] = gy[i] / sy;
-        }
+    double sx = 0.0, sy = 0.0;
+    for (int i = 0; i < 5; i++) {
+        sx += gx[i];
+        sy += gy[i];
+    }
+    for (int i = 0; i < 5; i++) {
+        fx[i] = gx[i] / sx;
+        fy[i] = gy[i] / sy;
     }
 }
 
@@ -271,22 +264,8 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
         classes.push_back(std::move(v));
     }
     struct Geo {
-        int kt, th, tw;
+        int th, tw;
     };
-    std::vector<Geo> geos;
-    for (int tw : {32, 64}) {
-        if (t.forced_tw && tw != t.forced_tw) continue;
-        for (int kt = 1; kt <= 16; kt++) {
-            if (t.forced_group && kt != t.forced_group) continue;
-            const int per = kt * (tw / 32);  // warps per 32 rows of tile
-            if (per > 16) continue;
-            if (t.forced_th) {
-                if (t.forced_th / 32 * per <= 16) geos.push_back({kt, t.forced_th, tw});
-            } else {
-                for (int th = std::min(224, 32 * (16 / per)); th >= 32; th -= 32) geos.push_back({kt, th, tw});
-            }
-        }
-    }
     // segment counts: starts at multiples of the record chunk, at least one
     // chunk per segment
     std::vector<int> seg_counts;
@@ -304,136 +283,235 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
         t0.push_back(T);
         return (int)t0.size() - 1;
     };
+    // rows past the tile a window can hold at all (256 rows, 32-row tile,
+    // 4 footprint rows)
+    constexpr int kMaxSpread = 256 - 32 - 4;
     bool have = false;
-    for (const Geo &geo : geos) {
+    std::vector<int32_t> t0;
+    std::vector<int32_t> rel((size_t)K * T);  // s_y at a frame minus s_y at its segment's first frame
+    std::vector<int32_t> mn(T), mx(T);
+    std::vector<int> count(kMaxSpread + 2);
+    for (int S_req : seg_counts) {
+        const int S = seg_starts(S_req, t0);
+        if (t.forced_segments && S != S_req) continue;  // fewer frames than the segments asked for
+        for (int k = 0; k < K; k++)
+            for (int j = 0; j < S; j++) {
+                const int32_t *sy = &t.shifts[(size_t)k * T * 2 + 1];
+                const int32_t ref = sy[(size_t)t0[j] * 2];
+                for (int f = t0[j]; f < t0[j + 1]; f++) rel[(size_t)k * T + f] = sy[(size_t)f * 2] - ref;
+            }
+        // the groups of each v_x class for the previous kt; several kt give
+        // the same split, and then the same spreads
+        std::vector<int> prev_split;
         std::vector<std::vector<int>> groups;
-        for (const auto &c : classes) {
-            const int n = (int)c.size();
-            const int ng = (n + geo.kt - 1) / geo.kt;
-            for (int g = 0, i = 0; g < ng; g++) {
-                const int sz = n / ng + (g < n % ng ? 1 : 0);
-                groups.emplace_back(c.begin() + i, c.begin() + i + sz);
-                i += sz;
+        std::vector<int32_t> seg_qy, seg_ref;
+        std::vector<std::vector<std::pair<int, int>>> hist;
+        int spread_max = 0, G = 0;
+        for (int kt = 1; kt <= 16; kt++) {
+            if (t.forced_group && kt != t.forced_group) continue;
+            std::vector<Geo> geos;
+            for (int tw : {32, 64}) {
+                if (t.forced_tw && tw != t.forced_tw) continue;
+                const int per = kt * (tw / 32);  // warps per 32 rows of tile
+                if (per > 16) continue;
+                if (t.forced_th) {
+                    if (t.forced_th / 32 * per <= 16) geos.push_back({t.forced_th, tw});
+                } else {
+                    for (int th = std::min(224, 32 * (16 / per)); th >= 32; th -= 32) geos.push_back({th, tw});
+                }
             }
-        }
-        const int G = (int)groups.size();
-        const int warps = geo.kt * (geo.th / 32) * (geo.tw / 32);
-        const int threads = 32 * ((warps + 3) / 4 * 4);
-        for (int S_req : seg_counts) {
-            std::vector<int32_t> t0;
-            const int S = seg_starts(S_req, t0);
-            if (t.forced_segments && S != S_req) continue;  // fewer frames than the segments asked for
-            mf::Plan p;
-            p.kernel = 2;
-            p.f_kt = geo.kt;
-            p.f_th = geo.th;
-            p.f_tw = geo.tw;
-            p.f_seg = S;
-            p.seg_t0 = t0;
-            p.seg_qy.assign((size_t)G * S * 2, 0);
-            p.seg_ref.assign((size_t)G * S * geo.kt, INT32_MIN);
-            // rows of each (group, frame) and the window height
-            std::vector<int> nrows((size_t)G * T);
-            int bh = 0;
-            for (int g = 0; g < G; g++)
-                for (int j = 0; j < S; j++) {
-                    int rmn = INT32_MAX, rmx = INT32_MIN;
-                    for (size_t i = 0; i < groups[g].size(); i++) {
-                        const int k = groups[g][i];
-                        const int sy0 = t.shifts[((size_t)k * T + t0[j]) * 2 + 1];
-                        p.seg_ref[((size_t)g * S + j) * geo.kt + i] = sy0;
-                        rmn = std::min(rmn, sy0);
-                        rmx = std::max(rmx, sy0);
+            if (geos.empty()) continue;
+            // each v_x class splits into groups of at most kt consecutive
+            // members, as even as possible
+            std::vector<int> split;
+            for (const auto &c : classes) split.push_back(((int)c.size() + kt - 1) / kt);
+            if (split != prev_split) {
+                prev_split = split;
+                groups.clear();
+                for (size_t ci = 0; ci < classes.size(); ci++) {
+                    const auto &c = classes[ci];
+                    const int n = (int)c.size(), ng = split[ci];
+                    for (int g = 0, i = 0; g < ng; g++) {
+                        const int sz = n / ng + (g < n % ng ? 1 : 0);
+                        groups.emplace_back(c.begin() + i, c.begin() + i + sz);
+                        i += sz;
                     }
-                    p.seg_qy[((size_t)g * S + j) * 2 + 0] = rmn;
-                    p.seg_qy[((size_t)g * S + j) * 2 + 1] = rmx - rmn;
-                    for (int f = t0[j]; f < t0[j + 1]; f++) {
-                        int mn = INT32_MAX, mx = INT32_MIN;
-                        for (size_t i = 0; i < groups[g].size(); i++) {
-                            const int k = groups[g][i];
-                            const int rel = t.shifts[((size_t)k * T + f) * 2 + 1] -
-                                            p.seg_ref[((size_t)g * S + j) * geo.kt + i];
-                            mn = std::min(mn, rel);
-                            mx = std::max(mx, rel);
+                }
+                G = (int)groups.size();
+                size_t gmax = 0;
+                for (const auto &m : groups) gmax = std::max(gmax, m.size());
+                // per (group, segment): the members' smallest s_y at the
+                // segment's first frame and their spread there, each member's
+                // s_y there, and how many frames have each row spread (largest
+                // minus smallest member shift relative to the segment start)
+                // as (spread, count) pairs
+                seg_qy.assign((size_t)G * S * 2, 0);
+                seg_ref.assign((size_t)G * S * gmax, INT32_MIN);
+                hist.assign((size_t)G * S, {});
+                spread_max = 0;
+                for (int g = 0; g < G && spread_max <= kMaxSpread; g++) {
+                    const auto &m = groups[g];
+                    for (int j = 0; j < S; j++) {
+                        int rmn = INT32_MAX, rmx = INT32_MIN;
+                        for (size_t i = 0; i < m.size(); i++) {
+                            const int sy0 = t.shifts[((size_t)m[i] * T + t0[j]) * 2 + 1];
+                            seg_ref[((size_t)g * S + j) * gmax + i] = sy0;
+                            rmn = std::min(rmn, sy0);
+                            rmx = std::max(rmx, sy0);
                         }
-                        nrows[(size_t)g * T + f] = geo.th + 4 + (mx - mn);
-                        bh = std::max(bh, nrows[(size_t)g * T + f]);
+                        seg_qy[((size_t)g * S + j) * 2 + 0] = rmn;
+                        seg_qy[((size_t)g * S + j) * 2 + 1] = rmx - rmn;
+                    }
+                    const int32_t *r0 = &rel[(size_t)m[0] * T];
+                    std::copy(r0, r0 + T, mn.begin());
+                    std::copy(r0, r0 + T, mx.begin());
+                    for (size_t i = 1; i < m.size(); i++) {
+                        const int32_t *r = &rel[(size_t)m[i] * T];
+                        for (int f = 0; f < T; f++) {
+                            mn[f] = std::min(mn[f], r[f]);
+                            mx[f] = std::max(mx[f], r[f]);
+                        }
+                    }
+                    for (int j = 0; j < S; j++) {
+                        std::fill(count.begin(), count.end(), 0);
+                        for (int f = t0[j]; f < t0[j + 1]; f++) count[std::min(mx[f] - mn[f], kMaxSpread + 1)]++;
+                        auto &h = hist[(size_t)g * S + j];
+                        for (int d = 0; d <= kMaxSpread + 1; d++)
+                            if (count[d]) {
+                                h.emplace_back(d, count[d]);
+                                spread_max = std::max(spread_max, d);
+                            }
                     }
                 }
-            if (bh > 256) continue;
-            int ns = 0;
-            for (int c = t.forced_stages ? t.forced_stages : mf::kFacMaxStages; c >= 2; c--) {
-                if (mf::fac_smem_bytes(geo.tw, bh, c, geo.kt) <= (size_t)mf::kSmemBudget &&
-                    (size_t)c * mf::fac_stage_floats(geo.tw, bh) * 4 >= (size_t)geo.th * geo.tw * 8) {
-                    ns = c;
-                    break;
-                }
-                if (t.forced_stages) break;
             }
-            if (ns == 0) continue;
-            p.f_ns = ns;
-            p.f_bh = bh;
-            const double hc = mf::fac_hcols(geo.tw), rp = mf::fac_rpitch(geo.tw);
-            const double ni = hc / mf::kFacItem;
-            const double sub = (geo.th / 32) * (geo.tw / 32);
-            // the column-pass warps are dealt to the SM's four schedulers; the
-            // busiest sets the pace
-            const double skew = (double)((warps + 3) / 4 * 4) / warps;
-            double cyc = 0.0;
-            for (int g = 0; g < G; g++) {
-                const double n = (double)groups[g].size();
-                for (int j = 0; j < S; j++) {
-                    // tile rows cover the members' spread at the segment start
-                    // too (nominal 1024-row image)
-                    const double extra = 1.0 + p.seg_qy[((size_t)g * S + j) * 2 + 1] / 1024.0;
-                    double seg = 0.0;
-                    for (int f = t0[j]; f < t0[j + 1]; f++) {
-                        const double nr = nrows[(size_t)g * T + f];
-                        // the row pass overlaps the column passes of other warps:
-                        // weighted by what measurements of the two fitted
-                        const double fma = (n * geo.th * geo.tw * 5.0 * skew + 0.5 * nr * hc * 5.0) / 128.0;
-                        const double sm = (n * sub * 40.0 * 128.0 + 0.5 * nr * ni * 160.0 + bh * rp * 4.0) / 128.0;
-                        const double rounds = std::ceil(2.0 * nr * ni / threads);
-                        seg += std::max(fma, sm) / 0.8 + 200.0 + 300.0 * (rounds - 1.0);
+            if (spread_max > kMaxSpread) continue;  // no tile height fits
+            for (const Geo &geo : geos) {
+                // window height: the tile, the footprint and the largest spread
+                const int bh = geo.th + 4 + spread_max;
+                if (bh > 256) continue;
+                int ns = 0;
+                for (int c = t.forced_stages ? t.forced_stages : mf::kFacMaxStages; c >= 2; c--) {
+                    if (mf::fac_smem_bytes(geo.tw, bh, c, kt) <= (size_t)mf::kSmemBudget &&
+                        (size_t)c * mf::fac_stage_floats(geo.tw, bh) * 4 >= (size_t)geo.th * geo.tw * 8) {
+                        ns = c;
+                        break;
                     }
-                    // prologue (first windows in flight) and epilogue of each CTA
-                    cyc += (seg + 20000.0) * extra;
+                    if (t.forced_stages) break;
                 }
-            }
-            // plane: K x 4 bytes written per segment and read by the next (at
-            // ~6.7 TB/s, 152 SMs at 2.07 GHz: 0.38 K cycles per pixel each),
-            // the extra CTA prologues and epilogues and the launch tail per
-            // segment (measured: about three times the traffic term)
-            p.cost = cyc / ((double)geo.th * geo.tw) + 1.2 * S * K;
-            p.G = G;
-            p.members.assign((size_t)G * geo.kt, -1);
-            for (int g = 0; g < G; g++)
-                for (size_t i = 0; i < groups[g].size(); i++) p.members[(size_t)g * geo.kt + i] = groups[g][i];
-            if (!have || p.cost < out.cost) {
+                if (ns == 0) continue;
+                const int warps = kt * (geo.th / 32) * (geo.tw / 32);
+                const int threads = 32 * ((warps + 3) / 4 * 4);
+                const double hc = mf::fac_hcols(geo.tw), rp = mf::fac_rpitch(geo.tw);
+                const double ni = hc / mf::kFacItem;
+                const double sub = (geo.th / 32) * (geo.tw / 32);
+                // the column-pass warps are dealt to the SM's four schedulers; the
+                // busiest sets the pace
+                const double skew = (double)((warps + 3) / 4 * 4) / warps;
+                double cyc = 0.0;
+                for (int g = 0; g < G; g++) {
+                    const double n = (double)groups[g].size();
+                    for (int j = 0; j < S; j++) {
+                        // tile rows cover the members' spread at the segment start
+                        // too (nominal 1024-row image)
+                        const double extra = 1.0 + seg_qy[((size_t)g * S + j) * 2 + 1] / 1024.0;
+                        double seg = 0.0;
+                        for (const auto &dc : hist[(size_t)g * S + j]) {
+                            const double nr = geo.th + 4 + dc.first;
+                            // the row pass overlaps the column passes of other warps:
+                            // weighted by what measurements of the two fitted
+                            const double fma = (n * geo.th * geo.tw * 5.0 * skew + 0.5 * nr * hc * 5.0) / 128.0;
+                            const double sm = (n * sub * 40.0 * 128.0 + 0.5 * nr * ni * 160.0 + bh * rp * 4.0) / 128.0;
+                            const double rounds = std::ceil(2.0 * nr * ni / threads);
+                            seg += dc.second * (std::max(fma, sm) / 0.8 + 200.0 + 300.0 * (rounds - 1.0));
+                        }
+                        // prologue (first windows in flight) and epilogue of each CTA
+                        cyc += (seg + 20000.0) * extra;
+                    }
+                }
+                // plane: K x 4 bytes written per segment and read by the next (at
+                // ~6.7 TB/s, 152 SMs at 2.07 GHz: 0.38 K cycles per pixel each),
+                // the extra CTA prologues and epilogues and the launch tail per
+                // segment (measured: about three times the traffic term)
+                const double cost = cyc / ((double)geo.th * geo.tw) + 1.2 * S * K;
+                if (have && cost >= out.cost) continue;
+                mf::Plan p;
+                p.kernel = 2;
+                p.f_kt = kt;
+                p.f_th = geo.th;
+                p.f_tw = geo.tw;
+                p.f_seg = S;
+                p.seg_t0 = t0;
+                p.seg_qy = seg_qy;
+                const size_t gmax = seg_ref.size() / ((size_t)G * S);
+                p.seg_ref.assign((size_t)G * S * kt, INT32_MIN);
+                for (size_t gj = 0; gj < (size_t)G * S; gj++)
+                    for (size_t i = 0; i < gmax; i++) p.seg_ref[gj * kt + i] = seg_ref[gj * gmax + i];
+                p.f_ns = ns;
+                p.f_bh = bh;
+                p.cost = cost;
+                p.G = G;
+                p.members.assign((size_t)G * kt, -1);
+                for (int g = 0; g < G; g++)
+                    for (size_t i = 0; i < groups[g].size(); i++) p.members[(size_t)g * kt + i] = groups[g][i];
                 out = std::move(p);
                 have = true;
             }
         }
     }
     if (!have) return false;
-    int mx = 0;
-    for (size_t i = 0; i < t.shifts.size(); i++) mx = std::max(mx, std::abs(t.shifts[i]));
-    out.max_abs_shift = mx;
+    int mxs = 0;
+    for (size_t i = 0; i < t.shifts.size(); i++) mxs = std::max(mxs, std::abs(t.shifts[i]));
+    out.max_abs_shift = mxs;
     return true;
 }
 
-template <class T>
-mf_status upload(T **dst, const T *src, size_t n) {
-    if (n == 0) {
+// A table's device arrays share one block, allocated and freed in stream
+// order (on a private non-blocking stream) where the device has memory
+// pools: unlike cudaFree, freeing it does not wait for the whole device, so
+// a finished search's table can be dropped while other streams still run.
+struct DeviceBlock {
+    struct Part {
+        void **dst;
+        const void *src;
+        size_t bytes, off;
+    };
+    std::vector<Part> parts;
+    size_t total = 0;
+    template <class T>
+    void add(T **dst, const T *src, size_t n) {
         *dst = nullptr;
+        if (n == 0) return;
+        total = (total + 255) / 256 * 256;
+        parts.push_back({(void **)dst, src, n * sizeof(T), total});
+        total += n * sizeof(T);
+    }
+    mf_status upload(void **block, bool *pooled) {
+        *block = nullptr;
+        *pooled = false;
+        if (total == 0) return MF_OK;
+        int dev = 0, pools = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, dev);
+        cudaStream_t st = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(MF_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
+        e = pools ? cudaMallocAsync(block, total, st) : cudaMalloc(block, total);
+        if (e != cudaSuccess) {
+            *block = nullptr;
+            cudaStreamDestroy(st);
+            return fail(MF_ENOMEM, "device allocation of %zu bytes: %s", total, cudaGetErrorString(e));
+        }
+        *pooled = pools != 0;
+        for (const Part &q : parts) {
+            *q.dst = (unsigned char *)*block + q.off;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(*q.dst, q.src, q.bytes, cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+        if (e != cudaSuccess) return fail(MF_ECUDA, "table upload: %s", cudaGetErrorString(e));
         return MF_OK;
     }
-    cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
-    if (e != cudaSuccess) return fail(MF_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
-    e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(MF_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
-    return MF_OK;
-}
+};
 
 struct HostLayouts {
     std::vector<mf::FrameHdr> hdr;
@@ -627,6 +705,7 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
     std::vector<float> wts;
     int64_t nnz_total = 0;
     std::vector<double> dense;
+    std::vector<char> hit;
     for (int k = 0; k < K; k++) {
         run_off[k] = (int32_t)runs.size();
         // bounding box of G_k's support
@@ -639,29 +718,36 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
             y_hi = std::max(y_hi, t->shifts[kt_ * 2 + 1] + 2);
         }
         const int64_t bw = (int64_t)x_hi - x_lo + 1, bh = (int64_t)y_hi - y_lo + 1;
-        std::map<std::pair<int32_t, int32_t>, double> sparse;  // (row, column) -> weight
-        const bool use_dense = bw * bh <= (int64_t)100 * T + 4096;
-        if (use_dense) dense.assign((size_t)(bw * bh), 0.0);
-        for (int f = 0; f < T; f++) {
-            const size_t kt_ = (size_t)k * T + f;
-            const int32_t sx = t->shifts[kt_ * 2 + 0], sy = t->shifts[kt_ * 2 + 1];
-            for (int b = 0; b < 5; b++)
-                for (int a = 0; a < 5; a++) {
-                    const double w = t->taps[kt_ * 25 + b * 5 + a];
-                    if (use_dense)
-                        dense[(size_t)((sy + b - 2 - y_lo) * bw + (sx + a - 2 - x_lo))] += w * w;
-                    else
-                        sparse[{sy + b - 2, sx + a - 2}] += w * w;
-                }
-        }
-        if (use_dense) {
-            // rows of the box: the support is where some frame's footprint landed
-            std::vector<char> hit((size_t)(bw * bh), 0);
+        // one run per row of the support: from the first column some frame's
+        // footprint reached to the last, starting at a multiple of 4
+        auto emit = [&](int32_t row, int32_t xfirst, int32_t xlast, const double *val, const int32_t *col,
+                        size_t n) {
+            const int32_t x0 = (int32_t)(4 * floor_div(xfirst, 4));
+            const int32_t nch = (int32_t)((xlast - x0 + 1 + 3) / 4);
+            while (wts.size() % 4) wts.push_back(0.f);
+            mf::RunRec r;
+            r.dy = row;
+            r.x0 = x0;
+            r.nch = nch;
+            r.woff = (int32_t)wts.size();
+            const size_t base = wts.size();
+            wts.resize(base + (size_t)nch * 4, 0.f);
+            for (size_t q = 0; q < n; q++) wts[base + (col ? col[q] : xfirst + (int32_t)q) - x0] = (float)val[q];
+            runs.push_back(r);
+        };
+        if (bw * bh <= (int64_t)100 * T + 4096) {
+            dense.assign((size_t)(bw * bh), 0.0);
+            hit.assign((size_t)(bw * bh), 0);
             for (int f = 0; f < T; f++) {
                 const size_t kt_ = (size_t)k * T + f;
                 const int32_t sx = t->shifts[kt_ * 2 + 0], sy = t->shifts[kt_ * 2 + 1];
                 for (int b = 0; b < 5; b++)
-                    for (int a = 0; a < 5; a++) hit[(size_t)((sy + b - 2 - y_lo) * bw + (sx + a - 2 - x_lo))] = 1;
+                    for (int a = 0; a < 5; a++) {
+                        const double w = t->taps[kt_ * 25 + b * 5 + a];
+                        const size_t i = (size_t)((sy + b - 2 - y_lo) * bw + (sx + a - 2 - x_lo));
+                        dense[i] += w * w;
+                        hit[i] = 1;
+                    }
             }
             for (int64_t r = 0; r < bh; r++) {
                 int64_t c0 = -1, c1 = -1;
@@ -671,33 +757,37 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
                         c1 = c;
                     }
                 if (c0 < 0) continue;
-                for (int64_t c = c0; c <= c1; c++) sparse[{(int32_t)(r + y_lo), (int32_t)(c + x_lo)}] +=
-                                                        dense[(size_t)(r * bw + c)];
+                nnz_total += c1 - c0 + 1;
+                emit((int32_t)(r + y_lo), (int32_t)(c0 + x_lo), (int32_t)(c1 + x_lo), &dense[(size_t)(r * bw + c0)],
+                     nullptr, (size_t)(c1 - c0 + 1));
             }
-        }
-        nnz_total += (int64_t)sparse.size();
-        auto it = sparse.begin();
-        while (it != sparse.end()) {
-            const int32_t row = it->first.first;
-            auto jt = it;
-            int32_t xmax = it->first.second;
-            while (jt != sparse.end() && jt->first.first == row) {
-                xmax = jt->first.second;
-                ++jt;
+        } else {
+            std::map<std::pair<int32_t, int32_t>, double> sparse;  // (row, column) -> weight
+            for (int f = 0; f < T; f++) {
+                const size_t kt_ = (size_t)k * T + f;
+                const int32_t sx = t->shifts[kt_ * 2 + 0], sy = t->shifts[kt_ * 2 + 1];
+                for (int b = 0; b < 5; b++)
+                    for (int a = 0; a < 5; a++) {
+                        const double w = t->taps[kt_ * 25 + b * 5 + a];
+                        sparse[{sy + b - 2, sx + a - 2}] += w * w;
+                    }
             }
-            const int32_t x0 = (int32_t)(4 * floor_div(it->first.second, 4));
-            const int32_t nch = (int32_t)((xmax - x0 + 1 + 3) / 4);
-            while (wts.size() % 4) wts.push_back(0.f);
-            mf::RunRec r;
-            r.dy = row;
-            r.x0 = x0;
-            r.nch = nch;
-            r.woff = (int32_t)wts.size();
-            const size_t base = wts.size();
-            wts.resize(base + (size_t)nch * 4, 0.f);
-            for (auto q = it; q != jt; ++q) wts[base + (q->first.second - x0)] = (float)q->second;
-            runs.push_back(r);
-            it = jt;
+            nnz_total += (int64_t)sparse.size();
+            std::vector<double> val;
+            std::vector<int32_t> col;
+            auto it = sparse.begin();
+            while (it != sparse.end()) {
+                const int32_t row = it->first.first;
+                val.clear();
+                col.clear();
+                auto jt = it;
+                for (; jt != sparse.end() && jt->first.first == row; ++jt) {
+                    val.push_back(jt->second);
+                    col.push_back(jt->first.second);
+                }
+                emit(row, col.front(), col.back(), val.data(), col.data(), val.size());
+                it = jt;
+            }
         }
     }
     run_off[K] = (int32_t)runs.size();
@@ -712,18 +802,20 @@ mf_status finish_table(mf_prf_table *t) {
     HostLayouts h;
     mf_status s = host_layouts(t, h);
     if (s != MF_OK) return s;
-    if ((s = upload(&t->d_blocks, h.blocks.data(), h.blocks.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_hdr, h.hdr.data(), h.hdr.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_members, t->plan.members.data(), t->plan.members.size())) != MF_OK) return s;
+    DeviceBlock blk;
+    blk.add(&t->d_blocks, h.blocks.data(), h.blocks.size());
+    blk.add(&t->d_hdr, h.hdr.data(), h.hdr.size());
+    blk.add(&t->d_members, t->plan.members.data(), t->plan.members.size());
     if (t->plan.kernel == 2) {
-        if ((s = upload(&t->d_segs, h.segs.data(), h.segs.size())) != MF_OK) return s;
-        if ((s = upload(&t->d_refs, t->plan.seg_ref.data(), t->plan.seg_ref.size())) != MF_OK) return s;
+        blk.add(&t->d_segs, h.segs.data(), h.segs.size());
+        blk.add(&t->d_refs, t->plan.seg_ref.data(), t->plan.seg_ref.size());
     }
-    if ((s = upload(&t->d_runs, h.runs.data(), h.runs.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_run_off, h.run_off.data(), h.run_off.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_wts, h.wts.data(), h.wts.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_taps64, t->taps.data(), t->taps.size())) != MF_OK) return s;
-    if ((s = upload(&t->d_shifts, t->shifts.data(), t->shifts.size())) != MF_OK) return s;
+    blk.add(&t->d_runs, h.runs.data(), h.runs.size());
+    blk.add(&t->d_run_off, h.run_off.data(), h.run_off.size());
+    blk.add(&t->d_wts, h.wts.data(), h.wts.size());
+    blk.add(&t->d_taps64, t->taps.data(), t->taps.size());
+    blk.add(&t->d_shifts, t->shifts.data(), t->shifts.size());
+    if ((s = blk.upload(&t->d_mem, &t->d_mem_pooled)) != MF_OK) return s;
     t->device_bytes = layout_bytes(t, h);
     return MF_OK;
 }
@@ -753,16 +845,16 @@ void fill_info(const mf_prf_table *t, mf_table_info *info) {
 }
 
 void free_device(mf_prf_table *t) {
-    cudaFree(t->d_blocks);
-    cudaFree(t->d_hdr);
-    cudaFree(t->d_members);
-    cudaFree(t->d_segs);
-    cudaFree(t->d_refs);
-    cudaFree(t->d_runs);
-    cudaFree(t->d_run_off);
-    cudaFree(t->d_wts);
-    cudaFree(t->d_taps64);
-    cudaFree(t->d_shifts);
+    if (t->d_mem) {
+        cudaStream_t st = nullptr;
+        if (t->d_mem_pooled && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
+            cudaFreeAsync(t->d_mem, st);
+            cudaStreamDestroy(st);
+        } else {
+            cudaFree(t->d_mem);
+        }
+    }
+    t->d_mem = nullptr;
     t->d_blocks = nullptr;
     t->d_hdr = nullptr;
     t->d_members = nullptr;
@@ -876,18 +968,33 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
     t->fy.resize((size_t)K * T * 5);
     t->vx.assign(vx, vx + K);
     t->vy.assign(vy, vy + K);
+    // the x profile depends on (v_x, frame) only and the y profile on (v_y,
+    // frame): evaluate each once per distinct velocity component
+    auto profiles = [&](const double *v, std::vector<int> &idx, std::vector<double> &prof) {
+        std::map<double, int> distinct;
+        idx.resize(K);
+        for (int k = 0; k < K; k++) idx[k] = distinct.emplace(v[k], (int)distinct.size()).first->second;
+        prof.resize(distinct.size() * (size_t)T * 5);
+        for (const auto &d : distinct)
+            for (int f = 0; f < T; f++) {
+                const double c = d.first * (double)f;
+                axis_profile(prf->kind, prf->sigma_px, c - std::floor(c + 0.5), &prof[((size_t)d.second * T + f) * 5]);
+            }
+    };
+    std::vector<int> ix, iy;
+    std::vector<double> px, py;
+    profiles(vx, ix, px);
+    profiles(vy, iy, py);
     for (int k = 0; k < K; k++) {
         for (int f = 0; f < T; f++) {
             // position after f frames, base pixel floor(c + 1/2), phase c - s
             const double cx = vx[k] * (double)f;
             const double cy = vy[k] * (double)f;
-            const double sx = std::floor(cx + 0.5);
-            const double sy = std::floor(cy + 0.5);
             const size_t kt = (size_t)k * T + f;
-            t->shifts[kt * 2 + 0] = (int32_t)sx;
-            t->shifts[kt * 2 + 1] = (int32_t)sy;
-            footprint(prf->kind, prf->sigma_px, cx - sx, cy - sy, &t->taps[kt * 25], &t->fx[kt * 5],
-                      &t->fy[kt * 5]);
+            t->shifts[kt * 2 + 0] = (int32_t)std::floor(cx + 0.5);
+            t->shifts[kt * 2 + 1] = (int32_t)std::floor(cy + 0.5);
+            footprint_from_axes(&px[((size_t)ix[k] * T + f) * 5], &py[((size_t)iy[k] * T + f) * 5], &t->taps[kt * 25],
+                                &t->fx[kt * 5], &t->fy[kt * 5]);
         }
     }
     *out_t = t;

@@ -195,6 +195,8 @@ struct mf_prf_table {
     int64_t g_nnz = 0;      // nonzero weights of the collapsed kernels
     size_t device_bytes = 0;
     // device copies
+    void *d_mem = nullptr;               // one device block holding every array below
+    bool d_mem_pooled = false;           // allocated with cudaMallocAsync
     unsigned char *d_blocks = nullptr;   // [G][T] frame blocks (frame_block_bytes or fac_block_bytes)
     int32_t *d_members = nullptr;        // [G][kt] trajectory of each slot, -1 for none
     int32_t *d_segs = nullptr;           // factored: [G][S] (first frame, last frame + 1, min s_y, spread)
