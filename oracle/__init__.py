@@ -2,6 +2,8 @@
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
-library.  See ``oracle/oracle.py`` for the functions and their citations.
+library.  See ``oracle/oracle.py`` (the search) and ``oracle/detect.py``
+(score normalisation and candidates) for the functions and their citations.
 """
 from .oracle import *  # noqa: F401,F403
+from .detect import *  # noqa: F401,F403

@@ -205,3 +205,37 @@ def add_movers_torch(res, movers, sigma_prf=0.7):
     flat = (tt[ok].long() * H + qy[ok].long()) * W + qx[ok].long()
     res.view(-1).index_add_(0, flat, val[ok])
     return res
+
+
+# ---------------------------------------------------------- score maps --
+
+def score_map(H, W, seed, K=100, mask_frac=0.01, n_sources=200, level=2.5, spread=0.45, peak=(2.0, 12.0),
+              gradient=0.5):
+    """A best-score map shaped like the search's output, for the detection
+    stage: snr_max [H, W] float32 and argmax [H, W] int32.  Noise pixels
+    scatter around `level` (the maximum over K trajectories of unit-normal
+    scores sits above 0) with a slow gradient across the image; sources add
+    compact bumps (3 x 3 to 5 x 5, heights in `peak`) at uniform random
+    centres (at most one per 400 pixels; nearby ones may touch); masked
+    pixels (clustered blobs) have argmax -1 and score 0."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:H, 0:W]
+    s = level + spread * rng.standard_normal((H, W)) + gradient * (yy / max(H, 1) - 0.5)
+    a = rng.integers(0, K, size=(H, W)).astype(np.int32)
+    n_src = min(n_sources, H * W // 400)
+    if n_src > 0:
+        ys = rng.integers(0, H, size=n_src)
+        xs = rng.integers(0, W, size=n_src)
+        for y, x in zip(ys, xs):
+            r = int(rng.integers(1, 3))
+            h = rng.uniform(*peak)
+            y0, y1, x0, x1 = max(0, y - r), min(H, y + r + 1), max(0, x - r), min(W, x + r + 1)
+            dy = (np.arange(y0, y1) - y)[:, None]
+            dx = (np.arange(x0, x1) - x)[None, :]
+            s[y0:y1, x0:x1] += h * np.exp(-(dy * dy + dx * dx) / 1.5)
+            a[y0:y1, x0:x1] = int(rng.integers(0, K))
+    if mask_frac > 0:
+        m = star_mask(H, W, rng, mask_frac).astype(bool)
+        s[m] = 0.0
+        a[m] = -1
+    return s.astype(np.float32), a
