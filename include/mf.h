@@ -321,6 +321,58 @@ mf_status mf_search_host(const mf_stack *host_stack, const float *sigma, const u
                          void *workspace, size_t workspace_bytes, mf_stream stream,
                          mf_stream copy_stream, void *ws_free);
 
+/* Score normalisation and candidate extraction (Section 3.3: each pixel's
+ * score is expressed in units of the standard deviation of the scores in the
+ * 255 x 255 square centred on it, and scores above 3 sigma are candidates).
+ *
+ * Per pixel p with a score (argmax[p] >= 0), over the window x window square
+ * centred on p, clipped to the image, counting only pixels with a score: n,
+ * mean and the population standard deviation sigma (FP64 sums of the scores
+ * and their squares; variance = mean square - mean^2).  The normalised score
+ * is z = (snr_max - mean) / sigma (subtract_mean = 1) or snr_max / sigma
+ * (subtract_mean = 0, the literal reading); it is 0 where p has no score,
+ * n < 2 or the window is constant (sigma^2 <= 1e-12 (mean^2 + sigma^2)).
+ * Candidates are pixels with z > threshold, decided in FP64; candidates that
+ * touch (8 neighbours) form one detection, reported at its largest z
+ * (smallest flat index y*W + x among equal z). */
+typedef struct {
+    int32_t window;        /* side of the square, odd, 1..2047 (255 in the paper) */
+    int32_t subtract_mean; /* 1: z = (s - mean) / sigma; 0: z = s / sigma */
+    double threshold;      /* candidates: z > threshold (3 in the paper) */
+} mf_detect_opts;
+
+/* One detection (mf_detect). */
+typedef struct {
+    int32_t y, x;     /* peak pixel */
+    int32_t k;        /* argmax trajectory at the peak */
+    int32_t npix;     /* candidate pixels in the detection */
+    double z;         /* normalised score at the peak (FP64) */
+    double mean;      /* local mean at the peak */
+    double sigma;     /* local standard deviation at the peak */
+    float snr;        /* snr_max at the peak */
+    int32_t reserved;
+} mf_detection;
+
+/* Bytes of workspace mf_detect needs (H * W < 2^31). */
+mf_status mf_detect_workspace_size(int64_t H, int64_t W, int32_t max_out, size_t *bytes);
+
+/* Normalise snr_max / argmax (device, H x W, as mf_search writes them) and
+ * extract the detections.
+ *   z_out    device float[H*W] for the normalised score, or NULL;
+ *   out      device mf_detection[max_out]: the max_out detections with the
+ *            largest z, ordered by z rounded to FP32 descending, then flat
+ *            index ascending (max_out 0..16384; 0 only counts);
+ *   n_out    device int32[2]: detections found, detections written.
+ * Asynchronous on `stream`; allocates nothing.  A union-find step that runs
+ * past its iteration budget records code 3 in the status word read by
+ * mf_device_status and leaves that pixel's detection incomplete.
+ * Errors: MF_EINVAL (NULL pointers, H or W < 1, H * W >= 2^31, window even or
+ * out of range, threshold not finite, small workspace), MF_EUNSUPPORTED
+ * (max_out above 16384); nothing is enqueued on an error. */
+mf_status mf_detect(const float *snr_max, const int32_t *argmax, int64_t H, int64_t W,
+                    const mf_detect_opts *opts, float *z_out, mf_detection *out, int32_t max_out,
+                    int32_t *n_out, void *workspace, size_t workspace_bytes, mf_stream stream);
+
 /* Per-kernel accounting of the library's own launches (for benchmarks and
  * roofline reports; not in the paper).  Launch counts are always kept; device
  * times are recorded with CUDA events on the launching stream only while

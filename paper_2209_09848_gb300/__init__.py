@@ -10,4 +10,5 @@ from .binding import (  # noqa: F401
     search_host, search_host_workspace_size, CANDIDATE_BYTES,
     rescore_topk, rescore_workspace_size, device_status, last_error, version, load, library_path,
     profile_enable, profile_read, decode_candidates, prf_plan, Batch,
+    detect, detect_workspace_size, decode_detections, DETECTION_BYTES,
 )

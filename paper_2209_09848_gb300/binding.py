@@ -46,6 +46,19 @@ class Candidate(ctypes.Structure):
 CANDIDATE_BYTES = ctypes.sizeof(Candidate)
 
 
+class DetectOpts(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("subtract_mean", ctypes.c_int32), ("threshold", ctypes.c_double)]
+
+
+class Detection(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_int32), ("x", ctypes.c_int32), ("k", ctypes.c_int32), ("npix", ctypes.c_int32),
+                ("z", ctypes.c_double), ("mean", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("snr", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+DETECTION_BYTES = ctypes.sizeof(Detection)
+
+
 class PlanOpts(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("vec", ctypes.c_int32), ("lockstep", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("group", ctypes.c_int32), ("tile_h", ctypes.c_int32),
@@ -124,6 +137,8 @@ def load():
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
             "mf_search_host_workspace_size": ([ctypes.POINTER(Stack), P, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_search_host": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P, P, P], ctypes.c_int),
+            "mf_detect_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
+            "mf_detect": ([P, P, I64, I64, ctypes.POINTER(DetectOpts), P, P, I32, P, P, SZ, P], ctypes.c_int),
             "mf_profile_enable": ([I32], ctypes.c_int),
             "mf_profile_read": ([ctypes.POINTER(Profile), I32], ctypes.c_int),
             "mf_batch_create": ([pp], ctypes.c_int),
@@ -409,6 +424,38 @@ def decode_candidates(raw: torch.Tensor, n: int):
     buf = raw[:n].cpu().numpy().tobytes()
     dt = np.dtype([("y", "<i4"), ("x", "<i4"), ("k", "<i4"), ("r", "<i4"), ("snr", "<f8"),
                    ("flux", "<f8"), ("snr_search", "<f4"), ("r2", "<f4")])
+    return np.frombuffer(buf, dtype=dt, count=n)
+
+
+def detect_workspace_size(H: int, W: int, max_out: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load().mf_detect_workspace_size(int(H), int(W), int(max_out), ctypes.byref(n)))
+    return n.value
+
+
+def detect(snr_max: torch.Tensor, argmax: torch.Tensor, window: int = 255, threshold: float = 3.0,
+           subtract_mean: bool = True, max_out: int = 4096, z_out: torch.Tensor | None = None, workspace=None,
+           stream=None):
+    """mf_detect: returns (detections as a uint8 tensor of max_out records,
+    n_out int32 [2] = (found, written)), both on the device."""
+    H, W = snr_max.shape
+    dev = snr_max.device
+    out = torch.zeros((max(max_out, 1), DETECTION_BYTES), dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(2, dtype=torch.int32, device=dev)
+    ws = _workspace(detect_workspace_size(H, W, max_out), dev, workspace)
+    opts = DetectOpts(int(window), 1 if subtract_mean else 0, float(threshold))
+    _check(load().mf_detect(_ptr(snr_max), _ptr(argmax), int(H), int(W), ctypes.byref(opts), _ptr(z_out),
+                            _ptr(out), int(max_out), _ptr(n_out), _ptr(ws), ws.numel() * ws.element_size(),
+                            _stream_ptr(stream)))
+    return out, n_out
+
+
+def decode_detections(raw: torch.Tensor, n: int):
+    """Detection records (uint8 tensor from detect) -> numpy structured array."""
+    import numpy as np
+    buf = raw[:n].cpu().numpy().tobytes()
+    dt = np.dtype([("y", "<i4"), ("x", "<i4"), ("k", "<i4"), ("npix", "<i4"), ("z", "<f8"), ("mean", "<f8"),
+                   ("sigma", "<f8"), ("snr", "<f4"), ("reserved", "<i4")])
     return np.frombuffer(buf, dtype=dt, count=n)
 
 

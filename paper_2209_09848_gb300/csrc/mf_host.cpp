@@ -1361,6 +1361,38 @@ mf_status mf_rescore_topk(const mf_stack *master, const float *sigma, const uint
     return ok();
 }
 
+mf_status mf_detect_workspace_size(int64_t H, int64_t W, int32_t max_out, size_t *bytes) {
+    if (!bytes) return fail(MF_EINVAL, "bytes is NULL");
+    if (H < 1 || W < 1 || H * W >= ((int64_t)1 << 31)) return fail(MF_EINVAL, "H=%lld W=%lld out of range",
+                                                                  (long long)H, (long long)W);
+    if (max_out < 0) return fail(MF_EINVAL, "max_out=%d < 0", max_out);
+    *bytes = mf::detect_workspace(H, W, max_out);
+    return ok();
+}
+
+mf_status mf_detect(const float *snr_max, const int32_t *argmax, int64_t H, int64_t W, const mf_detect_opts *opts,
+                    float *z_out, mf_detection *out, int32_t max_out, int32_t *n_out, void *workspace,
+                    size_t workspace_bytes, mf_stream stream) {
+    if (!snr_max || !argmax || !opts || !n_out || (max_out > 0 && !out)) return fail(MF_EINVAL, "NULL argument");
+    if (H < 1 || W < 1 || H * W >= ((int64_t)1 << 31))
+        return fail(MF_EINVAL, "H=%lld W=%lld out of range", (long long)H, (long long)W);
+    if (opts->window < 1 || opts->window > 2047 || opts->window % 2 == 0)
+        return fail(MF_EINVAL, "window=%d must be odd and in 1..2047", opts->window);
+    if (!std::isfinite(opts->threshold)) return fail(MF_EINVAL, "threshold not finite");
+    if (max_out < 0) return fail(MF_EINVAL, "max_out=%d < 0", max_out);
+    if (max_out > 16384) return fail(MF_EUNSUPPORTED, "max_out above 16384");
+    const size_t need = mf::detect_workspace(H, W, max_out);
+    if (!workspace || workspace_bytes < need)
+        return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", need, workspace_bytes);
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    mf::DetectArgs a{snr_max, argmax, H, W, opts->window, opts->subtract_mean ? 1 : 0, opts->threshold,
+                     z_out, out, max_out, n_out, (char *)workspace, workspace_bytes, stream};
+    char err[256] = {0};
+    const int rc = mf::launch_detect(a, err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
 // ------------------------------------------------- host-buffer search ---
 
 namespace {

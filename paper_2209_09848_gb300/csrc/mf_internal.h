@@ -261,7 +261,46 @@ struct RescoreArgs {
     void *stream;
 };
 size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top);
+
+// Top-k selection by a float score (mf_kernels.cu): among pixels with
+// valid[i] >= 0, the k_top largest keys (order-preserving score bits << 32 |
+// (0xFFFFFFFF - i)), i.e. score descending then index ascending, sorted
+// descending into the `top` slice of the workspace.  P < 2^32, k_top <=
+// kMaxTop.
+constexpr int kMaxTop = 16384;
+struct SelState {
+    unsigned long long prefix;  // selected high bits so far
+    unsigned long long thresh;  // final k_top-th largest key (0: take every valid key)
+    unsigned int need;          // keys still to take at and below the current prefix
+    unsigned int total;         // valid keys
+    unsigned int count;         // compacted keys
+    unsigned int pad;
+};
+struct SelectLayout {
+    size_t keys_off, hist_off, st_off, top_off, total;
+};
+SelectLayout select_layout(int64_t P, int32_t k_top);
+int launch_select(const float *score, const int32_t *valid, int64_t P, int32_t k_top, char *ws,
+                  const SelectLayout &L, void *stream, char *err, size_t errlen);
 int launch_rescore(const RescoreArgs &a, char *err, size_t errlen);
+
+// Score normalisation and candidate extraction (mf_detect.cu).
+struct DetectArgs {
+    const float *snr_max;
+    const int32_t *argmax;
+    int64_t H, W;
+    int32_t window, subtract_mean;
+    double threshold;
+    float *z_out;
+    mf_detection *out;
+    int32_t max_out;
+    int32_t *n_out;
+    char *ws;
+    size_t ws_bytes;
+    void *stream;
+};
+size_t detect_workspace(int64_t H, int64_t W, int32_t max_out);
+int launch_detect(const DetectArgs &a, char *err, size_t errlen);
 
 int read_device_status(int *status);
 
@@ -308,8 +347,15 @@ mf_status set_error(mf_status s, const char *msg);
 
 // Launch accounting (mf_profile_*).  Kernel ids index kKernelNames.
 enum KernelId { kKLambda = 0, kKWeight, kKDenominator, kKNumerator, kKFinalize, kKSelect, kKRescore,
-                kKCompact, kKSort, kKernelCount };
+                kKCompact, kKSort, kKDetStats, kKDetComponents, kKDetEmit, kKernelCount };
 int profile_enable(int on);
+// Bracket a launch made in another translation unit: prof_begin before it,
+// prof_end after it.
+struct ProfToken {
+    void *scope;
+};
+ProfToken prof_begin(int kid, void *stream);
+void prof_end(const ProfToken &t);
 int profile_read(mf_profile *out, int reset);
 
 }  // namespace mf

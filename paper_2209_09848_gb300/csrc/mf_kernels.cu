@@ -582,8 +582,9 @@ int grid_for(int64_t n, int threads) {
 
 // ---------------------------------------------------------- profiling ---
 
-const char *kKernelNames[kKernelCount] = {"k_lambda",  "k_weight", "k_denominator", "k_numerator", "k_finalize",
-                                          "k_select", "k_rescore", "k_compact",     "k_sort"};
+const char *kKernelNames[kKernelCount] = {"k_lambda",    "k_weight",      "k_denominator", "k_numerator",
+                                          "k_finalize",  "k_select",      "k_rescore",     "k_compact",
+                                          "k_sort",      "k_det_stats",   "k_det_cc",      "k_det_emit"};
 
 struct ProfPending {
     int kid;
@@ -620,6 +621,13 @@ struct LaunchScope {
 };
 
 }  // namespace
+
+ProfToken prof_begin(int kid, void *stream) {
+    LaunchScope *ls = new LaunchScope(kid, (cudaStream_t)stream);
+    return ProfToken{ls};
+}
+
+void prof_end(const ProfToken &t) { delete static_cast<LaunchScope *>(t.scope); }
 
 int profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -1124,15 +1132,6 @@ int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream_v
 
 namespace {
 
-struct SelState {
-    unsigned long long prefix;  // selected high bits so far
-    unsigned long long thresh;  // final k_top-th largest key (0: take every valid key)
-    unsigned int need;          // keys still to take at and below the current prefix
-    unsigned int total;         // valid keys
-    unsigned int count;         // compacted keys
-    unsigned int pad;
-};
-
 __global__ void k_sel_keys(const float *__restrict__ snr_max, const int32_t *__restrict__ argmax, int64_t P,
                            unsigned long long *__restrict__ keys, unsigned int *__restrict__ hist,
                            SelState *st) {
@@ -1225,7 +1224,6 @@ __global__ void k_sel_compact(const unsigned long long *__restrict__ keys, int64
 }
 
 // One CTA bitonic sort (descending) of up to kMaxTop keys in shared memory.
-constexpr int kMaxTop = 16384;
 __global__ void __launch_bounds__(1024) k_sel_sort(unsigned long long *__restrict__ keys, const SelState *st,
                                                    unsigned int cap) {
     extern __shared__ unsigned long long sk[];
@@ -1316,19 +1314,17 @@ __global__ void k_rescore(const TIn *__restrict__ r, int64_t fstride, int64_t rs
     }
 }
 
-struct RescoreLayout {
-    size_t keys_off, hist_off, st_off, top_off, total;
-};
+}  // namespace
 
-RescoreLayout rescore_layout(int64_t H, int64_t W, int32_t k_top) {
-    RescoreLayout L;
+SelectLayout select_layout(int64_t P, int32_t k_top) {
+    SelectLayout L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off = (off + bytes + 255) / 256 * 256;
         return o;
     };
-    L.keys_off = take((size_t)H * W * sizeof(unsigned long long));
+    L.keys_off = take((size_t)P * sizeof(unsigned long long));
     L.hist_off = take(65536 * sizeof(unsigned int));
     L.st_off = take(sizeof(SelState));
     L.top_off = take((size_t)k_top * sizeof(unsigned long long));
@@ -1336,32 +1332,25 @@ RescoreLayout rescore_layout(int64_t H, int64_t W, int32_t k_top) {
     return L;
 }
 
-}  // namespace
-
-size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top) { return rescore_layout(H, W, k_top).total; }
-
-int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
-    const mf_stack &st = *a.stack;
-    const mf_prf_table &tab = *a.tab;
-    cudaStream_t stream = (cudaStream_t)a.stream;
-    const int64_t H = st.H, W = st.W, P = H * W;
-    if (a.k_top > kMaxTop) {
+int launch_select(const float *score, const int32_t *valid, int64_t P, int32_t k_top, char *ws,
+                  const SelectLayout &L, void *stream_, char *err, size_t errlen) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (k_top > kMaxTop) {
         snprintf(err, errlen, "k_top above %d", kMaxTop);
         return (int)cudaErrorInvalidValue;
     }
-    const RescoreLayout L = rescore_layout(H, W, a.k_top);
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
-    unsigned int *hist = reinterpret_cast<unsigned int *>(a.ws + L.hist_off);
-    SelState *sst = reinterpret_cast<SelState *>(a.ws + L.st_off);
-    unsigned long long *top = reinterpret_cast<unsigned long long *>(a.ws + L.top_off);
-    cudaError_t e = cudaMemsetAsync(a.ws + L.hist_off, 0, L.top_off - L.hist_off, stream);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + L.keys_off);
+    unsigned int *hist = reinterpret_cast<unsigned int *>(ws + L.hist_off);
+    SelState *sst = reinterpret_cast<SelState *>(ws + L.st_off);
+    unsigned long long *top = reinterpret_cast<unsigned long long *>(ws + L.top_off);
+    cudaError_t e = cudaMemsetAsync(ws + L.hist_off, 0, L.top_off - L.hist_off, stream);
     if (e != cudaSuccess) {
         snprintf(err, errlen, "cudaMemsetAsync: %s", cudaGetErrorString(e));
         return (int)e;
     }
     {
         LaunchScope ls(kKSelect, stream);
-        k_sel_keys<<<grid_for(P, 256), 256, 0, stream>>>(a.snr_max, a.argmax, P, keys, hist, sst);
+        k_sel_keys<<<grid_for(P, 256), 256, 0, stream>>>(score, valid, P, keys, hist, sst);
     }
     MF_CHECK_LAUNCH("k_sel_keys");
     for (int pass = 0; pass < 4; pass++) {
@@ -1371,17 +1360,17 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
             MF_CHECK_LAUNCH("k_sel_hist");
         }
         LaunchScope ls(kKSelect, stream);
-        k_sel_pick<<<1, 1024, 0, stream>>>(hist, pass, sst, (unsigned)a.k_top);
+        k_sel_pick<<<1, 1024, 0, stream>>>(hist, pass, sst, (unsigned)k_top);
         MF_CHECK_LAUNCH("k_sel_pick");
     }
     {
         LaunchScope ls(kKCompact, stream);
-        k_sel_compact<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, top, sst, (unsigned)a.k_top);
+        k_sel_compact<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, top, sst, (unsigned)k_top);
     }
     MF_CHECK_LAUNCH("k_sel_compact");
     {
         unsigned int m = 1;
-        while (m < (unsigned)a.k_top) m <<= 1;
+        while (m < (unsigned)k_top) m <<= 1;
         const size_t smem = (size_t)m * sizeof(unsigned long long);
         e = cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
@@ -1389,9 +1378,24 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
             return (int)e;
         }
         LaunchScope ls(kKSort, stream);
-        k_sel_sort<<<1, 1024, smem, stream>>>(top, sst, (unsigned)a.k_top);
+        k_sel_sort<<<1, 1024, smem, stream>>>(top, sst, (unsigned)k_top);
     }
     MF_CHECK_LAUNCH("k_sel_sort");
+    return 0;
+}
+
+size_t rescore_workspace(int64_t H, int64_t W, int32_t k_top) { return select_layout(H * W, k_top).total; }
+
+int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
+    const mf_stack &st = *a.stack;
+    const mf_prf_table &tab = *a.tab;
+    cudaStream_t stream = (cudaStream_t)a.stream;
+    const int64_t H = st.H, W = st.W, P = H * W;
+    const SelectLayout L = select_layout(P, a.k_top);
+    SelState *sst = reinterpret_cast<SelState *>(a.ws + L.st_off);
+    unsigned long long *top = reinterpret_cast<unsigned long long *>(a.ws + L.top_off);
+    int rc = launch_select(a.snr_max, a.argmax, P, a.k_top, a.ws, L, stream, err, errlen);
+    if (rc) return rc;
     {
         const int threads = 256;
         const int blocks = (int)(((int64_t)a.k_top * 32 + threads - 1) / threads);
