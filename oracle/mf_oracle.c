@@ -92,6 +92,32 @@ void orc_trajectory_table(int K, int T, const double *vx, const double *vy,
     }
 }
 
+/* The same table with the frames' times and the pointing jitter (Section
+ * 2.1: the spacecraft's pointing jitters by a fraction of a pixel, and the
+ * filter follows the trajectory line including that jitter; Fig. 3: frames
+ * are missing while TESS downlinks, so time jumps).  Frame t is taken at
+ * time times[t] (in frame cadences; NULL: t) and every source appears
+ * displaced by (jx[t], jy[t]) pixels (NULL: 0), so the position is
+ * c = v * times[t] + j[t]. */
+void orc_trajectory_table_frames(int K, int T, const double *vx, const double *vy, const double *times,
+                                 const double *jx, const double *jy, double sigma, int kind,
+                                 int32_t *shifts, double *taps)
+{
+    for (int k = 0; k < K; k++) {
+        for (int t = 0; t < T; t++) {
+            double tau = times ? times[t] : (double)t;
+            double cx = vx[k] * tau + (jx ? jx[t] : 0.0);
+            double cy = vy[k] * tau + (jy ? jy[t] : 0.0);
+            double sx = floor(cx + 0.5);
+            double sy = floor(cy + 0.5);
+            shifts[((size_t)k * T + t) * 2 + 0] = (int32_t)sx;
+            shifts[((size_t)k * T + t) * 2 + 1] = (int32_t)sy;
+            orc_prf_taps(cx - sx, cy - sy, sigma, kind,
+                         taps + ((size_t)k * T + t) * 25);
+        }
+    }
+}
+
 /* Inverse variance per pixel (Section 3.2: Gaussian noise of known width;
  * bright pixels are clipped).  Masked pixels get weight 0. */
 void orc_inverse_variance(int H, int W, const float *sigma, const uint8_t *mask,

@@ -11,6 +11,9 @@ Functions and the passages they follow:
   source over neighbouring pixels; trajectories are straight lines in pixel
   space) and Section 3.2 (a filter is the trajectory line convolved with the
   PRF).  Gaussian PRF of width ``sigma_prf``, 5x5 footprint, renormalised.
+* ``trajectory_table_frames`` -- the same with each frame's time (Fig. 3:
+  the downlink gap makes time jump) and the pointing jitter (Section 2.1;
+  Section 3.2: the filter follows the trajectory including the jitter).
 * ``inverse_variance`` -- Section 3.2 (Gaussian noise of known width; bright
   pixels are clipped, read here as excluded: weight 0).
 * ``search_full`` / ``search_points`` -- Section 3.2, Eq. 5 (dot product of
@@ -44,7 +47,7 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = [
-    "build", "prf_taps", "trajectory_table", "inverse_variance", "search_full",
+    "build", "prf_taps", "trajectory_table", "trajectory_table_frames", "inverse_variance", "search_full",
     "search_points", "snr_and_best", "dense_template", "search_dense", "inject",
     "search_numpy", "topk_order", "threads",
 ]
@@ -72,6 +75,7 @@ def _load():
             lib.orc_pixel_integrated_gauss.argtypes = [i, d, d]
             lib.orc_pixel_integrated_gauss.restype = d
             lib.orc_trajectory_table.argtypes = [i, i, P, P, d, i, P, P]
+            lib.orc_trajectory_table_frames.argtypes = [i, i, P, P, P, P, P, d, i, P, P]
             lib.orc_inverse_variance.argtypes = [i, i, P, P, P]
             lib.orc_search_full.argtypes = [i, i, i, P, P, P, i, P, P, P, P]
             lib.orc_search_points.argtypes = [i, i, i, P, P, P, P, P, ctypes.c_long,
@@ -113,6 +117,26 @@ def trajectory_table(vx, vy, T: int, sigma: float = 0.7, kind: int = 0):
     taps = np.zeros((K, T, 5, 5), np.float64)
     _load().orc_trajectory_table(K, int(T), _ptr(vx), _ptr(vy), float(sigma), int(kind),
                                  _ptr(shifts), _ptr(taps))
+    return shifts, taps
+
+
+def trajectory_table_frames(vx, vy, T: int, times=None, jitter=None, sigma: float = 0.7, kind: int = 0):
+    """As ``trajectory_table`` with frame times and pointing jitter (Section
+    2.1 and Fig. 3): position c = v * times[t] + jitter[t].  ``times`` [T]
+    in frame cadences (None: 0..T-1); ``jitter`` [T, 2] as (x, y) pixels
+    (None: 0)."""
+    vx = np.ascontiguousarray(vx, np.float64)
+    vy = np.ascontiguousarray(vy, np.float64)
+    K = vx.shape[0]
+    tm = None if times is None else np.ascontiguousarray(times, np.float64)
+    jx = jy = None
+    if jitter is not None:
+        j = np.asarray(jitter, np.float64).reshape(T, 2)
+        jx, jy = np.ascontiguousarray(j[:, 0]), np.ascontiguousarray(j[:, 1])
+    shifts = np.zeros((K, T, 2), np.int32)
+    taps = np.zeros((K, T, 5, 5), np.float64)
+    _load().orc_trajectory_table_frames(K, int(T), _ptr(vx), _ptr(vy), _ptr(tm), _ptr(jx), _ptr(jy),
+                                        float(sigma), int(kind), _ptr(shifts), _ptr(taps))
     return shifts, taps
 
 

@@ -428,3 +428,80 @@ def test_topk_order_rule(oracle):
     amax = np.array([[0, 1, 2], [3, 0, -1]])
     assert list(oracle.topk_order(smax, amax, 4)) == [1, 3, 0, 2]
     assert list(oracle.topk_order(smax, amax, 10)) == [1, 3, 0, 2, 4]
+
+
+# ------------------------------------------- frame times and jitter (NEXT) --
+
+def _golden_frames():
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "trajectory_frames.txt")
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            v, tau, j, s, ph = (float(x) for x in line)
+            rows.append((v, tau, j, int(s), ph))
+    return rows
+
+
+def test_trajectory_frames_golden(oracle):
+    rows = _golden_frames()
+    assert len(rows) >= 10
+    for v, tau, j, s, ph in rows:
+        sx, tx = oracle.trajectory_table_frames([v], [0.0], 1, times=[tau], jitter=[[j, 0.0]])
+        assert (sx[0, 0, 0], sx[0, 0, 1]) == (s, 0), (v, tau, j)
+        np.testing.assert_allclose(tx[0, 0], oracle.prf_taps(ph, 0.0), atol=1e-14)
+        sy, ty = oracle.trajectory_table_frames([0.0], [v], 1, times=[tau], jitter=[[0.0, j]])
+        assert (sy[0, 0, 0], sy[0, 0, 1]) == (0, s), (v, tau, j)
+        np.testing.assert_allclose(ty[0, 0], oracle.prf_taps(0.0, ph), atol=1e-14)
+
+
+def test_frames_reduce_to_linear_and_select_rows(oracle):
+    # frames at 0..T-1 without jitter: the linear table; integer times with a
+    # gap: the rows of the linear table at those times (missing frames drop out)
+    vx, vy = [0.3, -0.17, 0.0], [0.11, 0.0, -0.42]
+    s0, t0 = oracle.trajectory_table(vx, vy, 40)
+    s1, t1 = oracle.trajectory_table_frames(vx, vy, 40)
+    assert np.array_equal(s0, s1) and np.array_equal(t0, t1)
+    tau = np.array([0, 1, 2, 3, 17, 18, 19, 39])
+    s2, t2 = oracle.trajectory_table_frames(vx, vy, len(tau), times=tau.astype(float))
+    assert np.array_equal(s2, s0[:, tau]) and np.array_equal(t2, t0[:, tau])
+
+
+def test_integer_jitter_moves_the_base_pixel_only(oracle):
+    g = _rng(8)
+    T = 12
+    j = g.integers(-3, 4, size=(T, 2)).astype(float)
+    vx, vy = g.uniform(-0.4, 0.4, 5), g.uniform(-0.4, 0.4, 5)
+    s0, t0 = oracle.trajectory_table(vx, vy, T)
+    s1, t1 = oracle.trajectory_table_frames(vx, vy, T, jitter=j)
+    assert np.array_equal(s1, s0 + j.astype(np.int32)[None])
+    np.testing.assert_allclose(t1, t0, atol=1e-15)
+
+
+def test_jittered_gapped_injection_closed_form(oracle):
+    """A source rendered by the scene model (independent PRF code in synth) at
+    p + v tau_t + j_t in each frame: the matched filter built with the same
+    times and jitter returns N/D = f and SNR = f sqrt(D) at p (Section 4.1
+    injection, Section 2.1 jitter, Fig. 3 time jump)."""
+    from paper_2209_09848_gb300 import synth
+    g = _rng(4)
+    T, H, W = 14, 30, 34
+    tau = np.sort(g.choice(np.arange(40), size=T, replace=False)).astype(float)
+    jit = g.uniform(-0.3, 0.3, size=(T, 2))
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    lam = oracle.inverse_variance(sigma)
+    vx, vy = np.array([0.21, -0.13]), np.array([-0.08, 0.17])
+    shifts, taps = oracle.trajectory_table_frames(vx, vy, T, times=tau, jitter=jit)
+    py, px, f = 15, 16, 3.0
+    for k in range(2):
+        res = np.zeros((T, H, W))
+        for t in range(T):
+            cy = py + vy[k] * tau[t] + jit[t, 1]
+            cx = px + vx[k] * tau[t] + jit[t, 0]
+            res[t] = synth.render_movers_np(1, H, W, [(cy, cx, 0.0, 0.0, f)])[0]
+        N, D = oracle.search_points(res.astype(np.float32), lam, shifts, taps, [py], [px], [k])
+        assert abs(N[0] / D[0] - f) < 1e-6 * f
+        # the linear table without times and jitter misses part of the flux
+        s_lin, t_lin = oracle.trajectory_table(vx, vy, T)
+        N2, D2 = oracle.search_points(res.astype(np.float32), lam, s_lin, t_lin, [py], [px], [k])
+        assert N2[0] / D2[0] < 0.9 * f
