@@ -57,7 +57,7 @@ def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (OpenMP over output pixels)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp,
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-o", tmp,
                                _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
