@@ -165,6 +165,29 @@ mf_status mf_prf_table_create_ex(const mf_prf_params *prf, const double *vx, con
                                  int32_t K, int32_t T, const mf_plan_opts *opts,
                                  mf_prf_table **out);
 
+/* Frame times and pointing jitter (Section 2.1: the pointing jitters by a
+ * fraction of a pixel and the filter follows the trajectory including it;
+ * Fig. 3: time jumps where frames are missing while TESS downlinks).  A
+ * source at start pixel p appears at c = p + v * times[t] + jitter[t] in
+ * frame t; base pixel and phase follow from c as for the linear table.
+ *   times   host double[T], frame times in frame cadences (any finite
+ *           values: gaps, fractional mid-exposure times); NULL: 0..T-1;
+ *   jitter  host double[T][2], (x, y) pointing offset in pixels; NULL: 0. */
+typedef struct {
+    const double *times;
+    const double *jitter;
+} mf_frames;
+
+/* mf_prf_table_create_ex with a frame model (frames NULL = the linear
+ * table).  The arrays are read during the call only.  Trajectories that
+ * share v_x still share the row pass of the factored numerator (the jitter
+ * is common to all of them).
+ * Errors as mf_prf_table_create_ex, plus MF_EINVAL for a non-finite time or
+ * jitter or a position beyond 2^20 pixels. */
+mf_status mf_prf_table_create_frames(const mf_prf_params *prf, const double *vx, const double *vy,
+                                     int32_t K, int32_t T, const mf_frames *frames,
+                                     const mf_plan_opts *opts, mf_prf_table **out);
+
 /* Build a filter bank from explicit per-(k, t) shifts and footprints (host
  * arrays): shifts[(k*T + t)*2 + 0] = s_x, [.. + 1] = s_y;
  * taps[(k*T + t)*25 + (b + 2)*5 + (a + 2)] = W_{k,t}(a, b), a = column offset,

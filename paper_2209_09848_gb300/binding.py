@@ -46,6 +46,10 @@ class Candidate(ctypes.Structure):
 CANDIDATE_BYTES = ctypes.sizeof(Candidate)
 
 
+class Frames(ctypes.Structure):
+    _fields_ = [("times", ctypes.c_void_p), ("jitter", ctypes.c_void_p)]
+
+
 class DetectOpts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int32), ("subtract_mean", ctypes.c_int32), ("threshold", ctypes.c_double)]
 
@@ -124,6 +128,8 @@ def load():
             "mf_prf_table_create_ex": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(PlanOpts), pp],
                                        ctypes.c_int),
             "mf_prf_table_create_custom": ([P, P, I32, I32, pp], ctypes.c_int),
+            "mf_prf_table_create_frames": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(Frames),
+                                            ctypes.POINTER(PlanOpts), pp], ctypes.c_int),
             "mf_prf_table_destroy": ([P], None),
             "mf_prf_table_dims": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
             "mf_prf_table_export": ([P, P, P], ctypes.c_int),
@@ -221,11 +227,13 @@ class PrfTable:
             pass
 
 
-def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> PrfTable:
+def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, **layout) -> PrfTable:
     """mf_prf_table_create, or mf_prf_table_create_ex when layout options are
     given: shape, vec, lockstep (general numerator), kernel (1 general,
     2 factored), group, tile_h, tile_w, stages, segments (factored
-    numerator); None or absent = automatic."""
+    numerator); None or absent = automatic.  times ([T] frame times in
+    cadences) and jitter ([T, 2] (x, y) pointing offsets in pixels) select
+    mf_prf_table_create_frames."""
     import numpy as np
     bad = set(layout) - set(_LAYOUT_KEYS)
     if bad:
@@ -237,7 +245,19 @@ def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> PrfTable:
     prm = PrfParams(int(kind), 0, float(sigma_px))
     h = ctypes.c_void_p()
     opts = _opts(**layout)
-    if opts is None:
+    if times is not None or jitter is not None:
+        tm = None if times is None else np.ascontiguousarray(times, np.float64)
+        jt = None if jitter is None else np.ascontiguousarray(jitter, np.float64)
+        if tm is not None and tm.shape != (int(T),):
+            raise ValueError("times must have shape (T,)")
+        if jt is not None and jt.shape != (int(T), 2):
+            raise ValueError("jitter must have shape (T, 2)")
+        fr = Frames(None if tm is None else tm.ctypes.data_as(ctypes.c_void_p),
+                    None if jt is None else jt.ctypes.data_as(ctypes.c_void_p))
+        _check(load().mf_prf_table_create_frames(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                                                 vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+                                                 ctypes.byref(fr), opts, ctypes.byref(h)))
+    elif opts is None:
         _check(load().mf_prf_table_create(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
                                           vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
                                           ctypes.byref(h)))

@@ -947,16 +947,29 @@ WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_tabl
 extern "C" {
 
 static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
-                                  int32_t T, mf_prf_table **out_t) {
+                                  int32_t T, mf_prf_table **out_t, const mf_frames *frames = nullptr) {
     if (!prf || !vx || !vy) return fail(MF_EINVAL, "NULL argument");
     if (K < 1 || T < 1) return fail(MF_EINVAL, "K=%d and T=%d must be >= 1", K, T);
     if (T > (1 << 20) || K > (1 << 22)) return fail(MF_EINVAL, "K or T too large");
     if (prf->kind != 0 && prf->kind != 1) return fail(MF_EINVAL, "unknown PRF kind %d", prf->kind);
     if (!(prf->sigma_px > 0.0) || !std::isfinite(prf->sigma_px))
         return fail(MF_EINVAL, "sigma_px must be finite and > 0");
+    const double *times = frames ? frames->times : nullptr;
+    const double *jitter = frames ? frames->jitter : nullptr;
+    // the frame model: time and (x, y) pointing offset of frame f
+    auto tau = [&](int f) { return times ? times[f] : (double)f; };
+    auto jit = [&](int f, int axis) { return jitter ? jitter[(size_t)f * 2 + axis] : 0.0; };
+    double tmax = 0.0, jmax = 0.0;
+    for (int f = 0; f < T; f++) {
+        if (!std::isfinite(tau(f)) || !std::isfinite(jit(f, 0)) || !std::isfinite(jit(f, 1)))
+            return fail(MF_EINVAL, "frame %d: time or jitter not finite", f);
+        tmax = std::max(tmax, std::fabs(tau(f)));
+        jmax = std::max({jmax, std::fabs(jit(f, 0)), std::fabs(jit(f, 1))});
+    }
     for (int k = 0; k < K; k++) {
         if (!std::isfinite(vx[k]) || !std::isfinite(vy[k])) return fail(MF_EINVAL, "velocity %d not finite", k);
-        if (std::fabs(vx[k]) * T > (1 << 20) || std::fabs(vy[k]) * T > (1 << 20))
+        if (std::fabs(vx[k]) * std::max(tmax, (double)T) + jmax > (1 << 20) ||
+            std::fabs(vy[k]) * std::max(tmax, (double)T) + jmax > (1 << 20))
             return fail(MF_EINVAL, "velocity %d moves more than 2^20 pixels", k);
     }
     auto *t = new mf_prf_table;
@@ -969,27 +982,28 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
     t->vx.assign(vx, vx + K);
     t->vy.assign(vy, vy + K);
     // the x profile depends on (v_x, frame) only and the y profile on (v_y,
-    // frame): evaluate each once per distinct velocity component
-    auto profiles = [&](const double *v, std::vector<int> &idx, std::vector<double> &prof) {
+    // frame) -- the jitter is common to all trajectories: evaluate each once
+    // per distinct velocity component
+    auto profiles = [&](const double *v, int axis, std::vector<int> &idx, std::vector<double> &prof) {
         std::map<double, int> distinct;
         idx.resize(K);
         for (int k = 0; k < K; k++) idx[k] = distinct.emplace(v[k], (int)distinct.size()).first->second;
         prof.resize(distinct.size() * (size_t)T * 5);
         for (const auto &d : distinct)
             for (int f = 0; f < T; f++) {
-                const double c = d.first * (double)f;
+                const double c = d.first * tau(f) + jit(f, axis);
                 axis_profile(prf->kind, prf->sigma_px, c - std::floor(c + 0.5), &prof[((size_t)d.second * T + f) * 5]);
             }
     };
     std::vector<int> ix, iy;
     std::vector<double> px, py;
-    profiles(vx, ix, px);
-    profiles(vy, iy, py);
+    profiles(vx, 0, ix, px);
+    profiles(vy, 1, iy, py);
     for (int k = 0; k < K; k++) {
         for (int f = 0; f < T; f++) {
-            // position after f frames, base pixel floor(c + 1/2), phase c - s
-            const double cx = vx[k] * (double)f;
-            const double cy = vy[k] * (double)f;
+            // position in frame f, base pixel floor(c + 1/2), phase c - s
+            const double cx = vx[k] * tau(f) + jit(f, 0);
+            const double cy = vy[k] * tau(f) + jit(f, 1);
             const size_t kt = (size_t)k * T + f;
             t->shifts[kt * 2 + 0] = (int32_t)std::floor(cx + 0.5);
             t->shifts[kt * 2 + 1] = (int32_t)std::floor(cy + 0.5);
@@ -1045,6 +1059,18 @@ mf_status mf_prf_table_create_ex(const mf_prf_params *prf, const double *vx, con
     *out = nullptr;
     mf_prf_table *t = nullptr;
     mf_status s = build_gauss_host(prf, vx, vy, K, T, &t);
+    if (s != MF_OK) return s;
+    if ((s = apply_opts(t, opts)) != MF_OK) return s;
+    return create_common(t, out);
+}
+
+mf_status mf_prf_table_create_frames(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                                     int32_t T, const mf_frames *frames, const mf_plan_opts *opts,
+                                     mf_prf_table **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    mf_prf_table *t = nullptr;
+    mf_status s = build_gauss_host(prf, vx, vy, K, T, &t, frames);
     if (s != MF_OK) return s;
     if ((s = apply_opts(t, opts)) != MF_OK) return s;
     return create_common(t, out);

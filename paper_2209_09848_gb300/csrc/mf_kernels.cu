@@ -1160,13 +1160,16 @@ __global__ void k_sel_hist(const unsigned long long *__restrict__ keys, int64_t 
     }
 }
 
-// One CTA: walk the 65536 bins from the top, find the bin holding the
-// `need`-th largest key, extend the prefix, and clear the histogram.
+// One CTA: find, from the top, the bin holding the `need`-th largest key,
+// extend the prefix, and clear the histogram.  Thread t sums the 64 bins
+// 65535 - 64 t .. 65472 - 64 t; a block scan of those sums gives each thread
+// the count above its bins, and the one thread whose range holds the
+// need-th key walks its 64 bins.
 __global__ void __launch_bounds__(1024) k_sel_pick(unsigned int *__restrict__ hist, int pass, SelState *st,
                                                    unsigned int k_top) {
-    __shared__ unsigned int part[1024];
+    __shared__ unsigned int warp_sum[32];
     __shared__ unsigned int chosen_bin, above;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (pass == 0) {
         if (tid == 0) {
             st->need = st->total < k_top ? st->total : k_top;
@@ -1175,31 +1178,44 @@ __global__ void __launch_bounds__(1024) k_sel_pick(unsigned int *__restrict__ hi
         __syncthreads();
     }
     const unsigned int need = st->need;
-    // each thread sums 64 consecutive bins; thread 0 holds the highest bins
     unsigned int sum = 0;
     for (int j = 0; j < 64; j++) sum += hist[65535 - (tid * 64 + j)];
-    part[tid] = sum;
-    __syncthreads();
+    // inclusive scan over the block, thread order = bins from the top
+    unsigned int inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned int o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) warp_sum[warp] = inc;
     if (tid == 0) {
-        unsigned int acc = 0;
-        int blk = 0;
-        for (; blk < 1024; blk++) {
-            if (acc + part[blk] >= need) break;
-            acc += part[blk];
+        chosen_bin = 0;
+        above = 0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned int w = warp_sum[lane];
+        unsigned int wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned int o = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += o;
         }
-        unsigned int bin = 0;
-        if (blk < 1024) {
-            for (int j = 0; j < 64; j++) {
-                const unsigned int b = 65535 - (blk * 64 + j);
-                if (acc + hist[b] >= need) {
-                    bin = b;
-                    break;
-                }
-                acc += hist[b];
+        warp_sum[lane] = wi - w;  // keys in the bins of earlier warps
+    }
+    __syncthreads();
+    const unsigned int before = warp_sum[warp] + inc - sum;  // keys in bins above this thread's
+    if (need > 0 && before < need && before + sum >= need) {
+        unsigned int acc = before;
+        for (int j = 0; j < 64; j++) {
+            const unsigned int b = 65535 - (tid * 64 + j);
+            if (acc + hist[b] >= need) {
+                chosen_bin = b;
+                above = acc;
+                break;
             }
+            acc += hist[b];
         }
-        chosen_bin = bin;
-        above = acc;
     }
     __syncthreads();
     for (int j = tid; j < 65536; j += blockDim.x) hist[j] = 0u;
