@@ -239,3 +239,55 @@ def score_map(H, W, seed, K=100, mask_frac=0.01, n_sources=200, level=2.5, sprea
         s[m] = 0.0
         a[m] = -1
     return s.astype(np.float32), a
+
+
+# ------------------------------------------------------ background scenes --
+
+def background_case(T, H, W, seed, n=64, noise=1.0, jitter_amp=0.15, n_movers=0, outlier_frac=0.002):
+    """Raw frames for the per-pixel background re-fit (Section 3.1, Eq. 1):
+    D_t = scattered light + B + B_theta theta_t^k + noise (+ movers and rare
+    outliers).  The scattered light is a smooth field (a few low-frequency
+    waves whose amplitudes drift with t) evaluated at the pixel centres; S
+    holds the same field sampled on an n x n grid of cell centres, so the
+    low-resolution model misses it slightly, as it would on sky data.  The
+    jitter theta_t = (x_t, y_t) is a bounded random walk of `jitter_amp` px.
+    Returns dict(D float32 [T,H,W], S float32 [T,n,n], jitter float64 [T,2],
+    coef float64 [H,W,6] (B and the five Taylor terms))."""
+    rng = np.random.default_rng(seed)
+    steps = rng.normal(0.0, jitter_amp / 4, size=(T, 2))
+    jit = np.clip(np.cumsum(steps, axis=0), -jitter_amp, jitter_amp)
+    waves = rng.uniform(0.2, 1.0, size=(4, 2))
+    phase = rng.uniform(0, 2 * np.pi, size=4)
+    amp0 = rng.uniform(5, 20, size=4)
+    drift = rng.normal(0, 0.2, size=(T, 4)).cumsum(axis=0) * 0.05
+
+    def field(yy, xx, t):
+        a = amp0 * (1 + drift[t])
+        return sum(a[i] * np.cos(2 * np.pi * (waves[i, 0] * yy + waves[i, 1] * xx) + phase[i]) for i in range(4))
+
+    py = (np.arange(H) + 0.5) / H
+    px = (np.arange(W) + 0.5) / W
+    gy = (np.arange(n) + 0.5) / n
+    YY, XX = np.meshgrid(py, px, indexing="ij")
+    GY, GX = np.meshgrid(gy, gy, indexing="ij")
+    coef = np.zeros((H, W, 6))
+    coef[..., 0] = 100 + 20 * rng.standard_normal((H, W))
+    coef[..., 1:3] = 5 * rng.standard_normal((H, W, 2))
+    coef[..., 3:] = 2 * rng.standard_normal((H, W, 3))
+    x, y = jit[:, 0], jit[:, 1]
+    phi = np.stack([np.ones(T), x, y, x * x, y * y, x * y], axis=1)
+    D = np.empty((T, H, W), np.float32)
+    S = np.empty((T, n, n), np.float32)
+    for t in range(T):
+        D[t] = field(YY, XX, t) + coef @ phi[t] + noise * rng.standard_normal((H, W))
+        S[t] = field(GY, GX, t)
+    if outlier_frac > 0:
+        m = rng.random((T, H, W)) < outlier_frac
+        D[m] += rng.uniform(20, 200, size=int(m.sum())) * noise
+    if n_movers:
+        ys = rng.uniform(0, H, n_movers)
+        xs = rng.uniform(0, W, n_movers)
+        vs = rng.uniform(-0.1, 0.1, size=(n_movers, 2))
+        movers = [(ys[i], xs[i], vs[i, 0], vs[i, 1], rng.uniform(2, 10) * noise) for i in range(n_movers)]
+        D += render_movers_np(T, H, W, movers).astype(np.float32)
+    return {"D": D, "S": S, "jitter": jit, "coef": coef}
