@@ -396,6 +396,47 @@ mf_status mf_detect(const float *snr_max, const int32_t *argmax, int64_t H, int6
                     const mf_detect_opts *opts, float *z_out, mf_detection *out, int32_t max_out,
                     int32_t *n_out, void *workspace, size_t workspace_bytes, mf_stream stream);
 
+/* Per-pixel background re-fit (Section 3.1: with the low-resolution
+ * scattered light S_t fixed, the model D_t = U(S_t) + B + B_theta theta_t^k
+ * (Eq. 1) separates into one regression per pixel on the same six basis
+ * values phi_t = (1, x_t, y_t, x_t^2, y_t^2, x_t y_t) of the jitter theta_t =
+ * (x_t, y_t), under the Huber loss (Eqs. 2-4); the fit is reached by
+ * least-squares solves with clipped residuals sharing one Gram inverse).
+ *
+ * Per pixel: y_t = D_t - U(S_t) with U bilinear from the n x n grid (pixel
+ * centres aligned: row i sits at grid coordinate (i + 1/2) n / H - 1/2,
+ * clamped to the grid); beta starts at the least-squares fit and takes
+ * `iterations` steps beta <- beta + G^-1 sum_t phi_t psi(y_t - phi_t . beta),
+ * psi(a) = min(max(a, -delta), delta), G = sum_t phi_t phi_t^T; the output
+ * residual is r_t = y_t - phi_t . beta (the matched filter's input).  The
+ * library applies G^-1 through an orthonormal basis Q = Phi R^-1 (G = R^T R,
+ * built on the host in FP64); FP32 sums in blocks of 32 frames. */
+typedef struct {
+    int32_t iterations;    /* clipped steps after the least-squares start, 0..1000 */
+    int32_t reserved;
+    double delta;          /* Huber threshold, > 0 (data units); +inf: least squares */
+} mf_refit_opts;
+
+/* Bytes of workspace mf_background_refit needs for T frames. */
+mf_status mf_refit_workspace_size(int64_t T, size_t *bytes);
+
+/* data     device float[T][H][W], raw frames (contiguous);
+ * scatter  device float[T][n][n], low-resolution scattered light, or NULL
+ *          (U = 0; n ignored);
+ * jitter   HOST double[T][2], (x_t, y_t) in pixels, read during the call;
+ * resid    device float[T][H][W] for r, may be `data` itself (in place);
+ * coef     device float[H][W][6] for (B, B_x, B_y, B_xx, B_yy, B_xy), or NULL.
+ * Asynchronous on `stream` (the basis is copied from pageable host memory
+ * into the workspace first); allocates nothing.
+ * Errors: MF_EINVAL (NULL pointers, T < 6, H or W < 1, n < 1 with scatter,
+ * non-finite jitter, delta <= 0 or NaN, iterations out of range, jitter that
+ * does not determine the six coefficients (a singular Gram matrix), small
+ * workspace); nothing is enqueued on an error. */
+mf_status mf_background_refit(const float *data, int64_t T, int64_t H, int64_t W,
+                              const float *scatter, int32_t n, const double *jitter,
+                              const mf_refit_opts *opts, float *resid, float *coef,
+                              void *workspace, size_t workspace_bytes, mf_stream stream);
+
 /* Per-kernel accounting of the library's own launches (for benchmarks and
  * roofline reports; not in the paper).  Launch counts are always kept; device
  * times are recorded with CUDA events on the launching stream only while

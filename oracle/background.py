@@ -27,13 +27,14 @@ clipped residuals (Huber 1977, "modified residuals").  Readings:
   grid points in each direction; no scattered light (S absent) means U = 0.
 
 Functions: ``basis`` (phi), ``upsample`` (U), ``refit`` (coefficients and
-residuals), ``huber_loss`` (the objective, for the pins).
+residuals), ``refit_points`` (the same for sampled pixels of a large
+image), ``huber_loss`` (the objective, for the pins).
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["basis", "upsample", "refit", "huber_loss"]
+__all__ = ["basis", "upsample", "refit", "refit_points", "huber_loss"]
 
 
 def basis(jitter):
@@ -85,3 +86,27 @@ def refit(D, jitter, delta: float, iterations: int, S=None):
         beta = beta + Ginv @ (Phi.T @ np.clip(E, -delta, delta))
     R = Yf - Phi @ beta
     return beta.T.reshape(H, W, 6), R.reshape(T, H, W)
+
+
+def refit_points(D_pts, ys, xs, H: int, W: int, jitter, delta: float, iterations: int, S=None):
+    """``refit`` for the pixels (ys[m], xs[m]) of an H x W image: D_pts
+    [T, m] their time series; U evaluated at those pixels only."""
+    D_pts = np.asarray(D_pts, dtype=np.float64)
+    ys = np.asarray(ys)
+    xs = np.asarray(xs)
+    if S is not None:
+        S = np.asarray(S, dtype=np.float64)
+        n_y, n_x = S.shape[1], S.shape[2]
+        u = np.clip((ys + 0.5) * n_y / H - 0.5, 0.0, n_y - 1)
+        v = np.clip((xs + 0.5) * n_x / W - 0.5, 0.0, n_x - 1)
+        y0 = np.floor(u).astype(np.int64)
+        x0 = np.floor(v).astype(np.int64)
+        y1 = np.minimum(y0 + 1, n_y - 1)
+        x1 = np.minimum(x0 + 1, n_x - 1)
+        fy, fx = u - y0, v - x0
+        top = S[:, y0, x0] * (1 - fx) + S[:, y0, x1] * fx
+        bot = S[:, y1, x0] * (1 - fx) + S[:, y1, x1] * fx
+        D_pts = D_pts - (top * (1 - fy) + bot * fy)
+    T, m = D_pts.shape
+    coef, R = refit(D_pts.reshape(T, 1, m), jitter, delta, iterations)
+    return coef.reshape(m, 6), R.reshape(T, m)

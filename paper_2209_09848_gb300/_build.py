@@ -11,7 +11,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmf.so")
-SOURCES = ["mf_kernels.cu", "mf_factored.cu", "mf_detect.cu", "mf_host.cpp", "mf_noalloc.cu"]
+SOURCES = ["mf_kernels.cu", "mf_factored.cu", "mf_detect.cu", "mf_background.cu", "mf_host.cpp", "mf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

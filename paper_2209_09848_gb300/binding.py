@@ -50,6 +50,10 @@ class Frames(ctypes.Structure):
     _fields_ = [("times", ctypes.c_void_p), ("jitter", ctypes.c_void_p)]
 
 
+class RefitOpts(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32), ("delta", ctypes.c_double)]
+
+
 class DetectOpts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int32), ("subtract_mean", ctypes.c_int32), ("threshold", ctypes.c_double)]
 
@@ -143,6 +147,9 @@ def load():
             "mf_rescore_topk": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P], ctypes.c_int),
             "mf_search_host_workspace_size": ([ctypes.POINTER(Stack), P, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_search_host": ([ctypes.POINTER(Stack), P, P, P, P, P, I32, P, P, P, SZ, P, P, P], ctypes.c_int),
+            "mf_refit_workspace_size": ([I64, ctypes.POINTER(SZ)], ctypes.c_int),
+            "mf_background_refit": ([P, I64, I64, I64, P, I32, P, ctypes.POINTER(RefitOpts), P, P, P, SZ, P],
+                                    ctypes.c_int),
             "mf_detect_workspace_size": ([I64, I64, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_detect": ([P, P, I64, I64, ctypes.POINTER(DetectOpts), P, P, I32, P, P, SZ, P], ctypes.c_int),
             "mf_profile_enable": ([I32], ctypes.c_int),
@@ -445,6 +452,37 @@ def decode_candidates(raw: torch.Tensor, n: int):
     dt = np.dtype([("y", "<i4"), ("x", "<i4"), ("k", "<i4"), ("r", "<i4"), ("snr", "<f8"),
                    ("flux", "<f8"), ("snr_search", "<f4"), ("r2", "<f4")])
     return np.frombuffer(buf, dtype=dt, count=n)
+
+
+def refit_workspace_size(T: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load().mf_refit_workspace_size(int(T), ctypes.byref(n)))
+    return n.value
+
+
+def background_refit(data: torch.Tensor, jitter, delta: float, iterations: int = 10,
+                     scatter: torch.Tensor | None = None, resid: torch.Tensor | None = None, want_coef: bool = True,
+                     workspace=None, stream=None):
+    """mf_background_refit: data [T, H, W] float32 (device, contiguous),
+    jitter [T, 2] (x, y) host array, scatter [T, n, n] float32 or None.
+    Returns (residual [T, H, W], coefficients [H, W, 6] or None); pass
+    resid=data to work in place."""
+    import numpy as np
+    T, H, W = data.shape
+    dev = data.device
+    jt = np.ascontiguousarray(jitter, np.float64)
+    if jt.shape != (T, 2):
+        raise ValueError("jitter must have shape (T, 2)")
+    if resid is None:
+        resid = torch.empty_like(data)
+    coef = torch.empty((H, W, 6), dtype=torch.float32, device=dev) if want_coef else None
+    n = 0 if scatter is None else int(scatter.shape[-1])
+    ws = _workspace(refit_workspace_size(T), dev, workspace)
+    opts = RefitOpts(int(iterations), 0, float(delta))
+    _check(load().mf_background_refit(_ptr(data), int(T), int(H), int(W), _ptr(scatter), n,
+                                      jt.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts), _ptr(resid),
+                                      _ptr(coef), _ptr(ws), ws.numel() * ws.element_size(), _stream_ptr(stream)))
+    return resid, coef
 
 
 def detect_workspace_size(H: int, W: int, max_out: int) -> int:

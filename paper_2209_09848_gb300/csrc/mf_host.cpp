@@ -1419,6 +1419,97 @@ mf_status mf_detect(const float *snr_max, const int32_t *argmax, int64_t H, int6
     return ok();
 }
 
+mf_status mf_refit_workspace_size(int64_t T, size_t *bytes) {
+    if (!bytes) return fail(MF_EINVAL, "bytes is NULL");
+    if (T < 6 || T > (1 << 20)) return fail(MF_EINVAL, "T=%lld out of range 6..2^20", (long long)T);
+    *bytes = mf::refit_workspace(T);
+    return ok();
+}
+
+mf_status mf_background_refit(const float *data, int64_t T, int64_t H, int64_t W, const float *scatter, int32_t n,
+                              const double *jitter, const mf_refit_opts *opts, float *resid, float *coef,
+                              void *workspace, size_t workspace_bytes, mf_stream stream) {
+    if (!data || !jitter || !opts || !resid) return fail(MF_EINVAL, "NULL argument");
+    if (T < 6 || T > (1 << 20)) return fail(MF_EINVAL, "T=%lld: the fit needs at least 6 frames", (long long)T);
+    if (H < 1 || W < 1 || H > (1 << 20) || W > (1 << 20) || H * W >= ((int64_t)1 << 31))
+        return fail(MF_EINVAL, "H=%lld W=%lld out of range", (long long)H, (long long)W);
+    if (scatter && (n < 1 || n > 4096)) return fail(MF_EINVAL, "scattered-light grid n=%d out of range", n);
+    if (opts->iterations < 0 || opts->iterations > 1000)
+        return fail(MF_EINVAL, "iterations=%d out of range 0..1000", opts->iterations);
+    if (!(opts->delta > 0.0)) return fail(MF_EINVAL, "delta must be > 0");
+    const size_t need = mf::refit_workspace(T);
+    if (!workspace || workspace_bytes < need)
+        return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", need, workspace_bytes);
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    // basis phi_t = (1, x, y, x^2, y^2, x y) and its Gram matrix, FP64
+    std::vector<double> phi((size_t)T * 6);
+    double G[36] = {0};
+    for (int64_t t = 0; t < T; t++) {
+        const double x = jitter[t * 2], y = jitter[t * 2 + 1];
+        if (!std::isfinite(x) || !std::isfinite(y)) return fail(MF_EINVAL, "jitter of frame %lld not finite", (long long)t);
+        double *f = &phi[(size_t)t * 6];
+        f[0] = 1.0;
+        f[1] = x;
+        f[2] = y;
+        f[3] = x * x;
+        f[4] = y * y;
+        f[5] = x * y;
+        for (int i = 0; i < 6; i++)
+            for (int j = 0; j < 6; j++) G[i * 6 + j] += f[i] * f[j];
+    }
+    // Cholesky G = R^T R (R upper triangular); a pivot that vanishes against
+    // its diagonal means the jitter does not determine the six coefficients
+    double R[36] = {0};
+    for (int i = 0; i < 6; i++) {
+        for (int j = i; j < 6; j++) {
+            double v = G[i * 6 + j];
+            for (int k = 0; k < i; k++) v -= R[k * 6 + i] * R[k * 6 + j];
+            if (j == i) {
+                if (!(v > 1e-12 * G[i * 6 + i]))
+                    return fail(MF_EINVAL, "the jitter does not determine the background model (basis term %d)", i);
+                R[i * 6 + i] = std::sqrt(v);
+            } else {
+                R[i * 6 + j] = v / R[i * 6 + i];
+            }
+        }
+    }
+    // R^-1 (upper triangular), Q = Phi R^-1 and Q^T 1
+    double Rinv[36] = {0};
+    for (int j = 0; j < 6; j++) {
+        Rinv[j * 6 + j] = 1.0 / R[j * 6 + j];
+        for (int i = j - 1; i >= 0; i--) {
+            double v = 0.0;
+            for (int k = i + 1; k <= j; k++) v += R[i * 6 + k] * Rinv[k * 6 + j];
+            Rinv[i * 6 + j] = -v / R[i * 6 + i];
+        }
+    }
+    std::vector<float> Q((size_t)T * mf::kRefitBasisPitch, 0.f);
+    double q1[6] = {0};
+    for (int64_t t = 0; t < T; t++) {
+        const double *f = &phi[(size_t)t * 6];
+        for (int j = 0; j < 6; j++) {
+            double v = 0.0;
+            for (int k = 0; k <= j; k++) v += f[k] * Rinv[k * 6 + j];
+            Q[(size_t)t * mf::kRefitBasisPitch + j] = (float)v;
+            q1[j] += v;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    cudaError_t e = cudaMemcpyAsync(ws + mf::refit_q_off(), Q.data(), Q.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + mf::refit_rinv_off(T), Rinv, sizeof Rinv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + mf::refit_q1_off(T), q1, sizeof q1, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "basis upload: %s", cudaGetErrorString(e));
+    mf::RefitArgs a{data, T, H, W, scatter, scatter ? n : 0, opts->iterations, (float)opts->delta, resid, coef,
+                    ws, stream};
+    char err[256] = {0};
+    const int rc = mf::launch_refit(a, err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
 // ------------------------------------------------- host-buffer search ---
 
 namespace {

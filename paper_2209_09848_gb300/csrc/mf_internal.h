@@ -302,6 +302,27 @@ struct DetectArgs {
 size_t detect_workspace(int64_t H, int64_t W, int32_t max_out);
 int launch_detect(const DetectArgs &a, char *err, size_t errlen);
 
+// Per-pixel background re-fit (mf_background.cu).  The workspace holds the
+// orthonormal basis Q [T][8] (six values, two pad), R^-1 (6 x 6, row-major,
+// FP64) and Q^T 1 (6 doubles), uploaded by the host.
+struct RefitArgs {
+    const float *data;
+    int64_t T, H, W;
+    const float *scatter;
+    int32_t n, iterations;
+    float delta;
+    float *resid, *coef;
+    char *ws;
+    void *stream;
+};
+constexpr int kRefitBasisPitch = 8;
+size_t refit_workspace(int64_t T);
+// Offsets of the basis pieces in the workspace.
+size_t refit_q_off();
+size_t refit_rinv_off(int64_t T);
+size_t refit_q1_off(int64_t T);
+int launch_refit(const RefitArgs &a, char *err, size_t errlen);
+
 int read_device_status(int *status);
 
 // Device address of the status word that bounded waits write on giving up.
@@ -347,7 +368,7 @@ mf_status set_error(mf_status s, const char *msg);
 
 // Launch accounting (mf_profile_*).  Kernel ids index kKernelNames.
 enum KernelId { kKLambda = 0, kKWeight, kKDenominator, kKNumerator, kKFinalize, kKSelect, kKRescore,
-                kKCompact, kKSort, kKDetStats, kKDetComponents, kKDetEmit, kKernelCount };
+                kKCompact, kKSort, kKDetStats, kKDetComponents, kKDetEmit, kKRefit, kKernelCount };
 int profile_enable(int on);
 // Bracket a launch made in another translation unit: prof_begin before it,
 // prof_end after it.

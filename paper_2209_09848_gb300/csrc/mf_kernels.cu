@@ -584,7 +584,8 @@ int grid_for(int64_t n, int threads) {
 
 const char *kKernelNames[kKernelCount] = {"k_lambda",    "k_weight",      "k_denominator", "k_numerator",
                                           "k_finalize",  "k_select",      "k_rescore",     "k_compact",
-                                          "k_sort",      "k_det_stats",   "k_det_cc",      "k_det_emit"};
+                                          "k_sort",      "k_det_stats",   "k_det_cc",      "k_det_emit",
+                                          "k_refit"};
 
 struct ProfPending {
     int kid;

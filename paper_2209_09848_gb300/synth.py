@@ -291,3 +291,51 @@ def background_case(T, H, W, seed, n=64, noise=1.0, jitter_amp=0.15, n_movers=0,
         movers = [(ys[i], xs[i], vs[i, 0], vs[i, 1], rng.uniform(2, 10) * noise) for i in range(n_movers)]
         D += render_movers_np(T, H, W, movers).astype(np.float32)
     return {"D": D, "S": S, "jitter": jit, "coef": coef}
+
+
+def background_case_gpu(T=1000, H=2048, W=2048, seed=1, n=64, noise=1.0, jitter_amp=0.15, outlier_frac=0.001,
+                        device="cuda"):
+    """``background_case`` at full size, generated on the GPU with torch
+    (seeded Philox): D float32 [T, H, W] and S float32 [T, n, n] on the
+    device, jitter float64 [T, 2] on the host.  Same scene model: drifting
+    low-frequency scattered light at the pixel centres (S samples it on the
+    n x n cell centres), a background with jitter Taylor terms, Gaussian
+    noise and rare bright outliers."""
+    import torch
+    rng = np.random.default_rng(seed)
+    steps = rng.normal(0.0, jitter_amp / 4, size=(T, 2))
+    jit = np.clip(np.cumsum(steps, axis=0), -jitter_amp, jitter_amp)
+    waves = rng.uniform(0.2, 1.0, size=(4, 2))
+    phase = rng.uniform(0, 2 * np.pi, size=4)
+    amp0 = rng.uniform(5, 20, size=4)
+    drift = rng.normal(0, 0.2, size=(T, 4)).cumsum(axis=0) * 0.05
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    py = (torch.arange(H, device=device, dtype=torch.float32) + 0.5) / H
+    px = (torch.arange(W, device=device, dtype=torch.float32) + 0.5) / W
+    gy = (torch.arange(n, device=device, dtype=torch.float32) + 0.5) / n
+    modes = [torch.cos(2 * np.pi * (float(waves[i, 0]) * py[:, None] + float(waves[i, 1]) * px[None, :])
+                       + float(phase[i])) for i in range(4)]
+    gmodes = [torch.cos(2 * np.pi * (float(waves[i, 0]) * gy[:, None] + float(waves[i, 1]) * gy[None, :])
+                        + float(phase[i])) for i in range(4)]
+    coef = torch.randn((6, H, W), generator=g, device=device)
+    coef[0] = 100 + 20 * coef[0]
+    coef[1:3] *= 5
+    coef[3:] *= 2
+    D = torch.empty((T, H, W), dtype=torch.float32, device=device)
+    S = torch.empty((T, n, n), dtype=torch.float32, device=device)
+    x, y = jit[:, 0], jit[:, 1]
+    for t in range(T):
+        a = amp0 * (1 + drift[t])
+        ph = (1.0, float(x[t]), float(y[t]), float(x[t] ** 2), float(y[t] ** 2), float(x[t] * y[t]))
+        frame = torch.randn((H, W), generator=g, device=device) * noise
+        for i in range(4):
+            frame.add_(modes[i], alpha=float(a[i]))
+        for k in range(6):
+            frame.add_(coef[k], alpha=ph[k])
+        if outlier_frac > 0:
+            hit = torch.rand((H, W), generator=g, device=device) < outlier_frac
+            frame.add_(hit * (20 + 180 * torch.rand((H, W), generator=g, device=device)) * noise)
+        D[t] = frame
+        S[t] = sum(float(a[i]) * gmodes[i] for i in range(4))
+    return {"D": D, "S": S, "jitter": jit}

@@ -102,3 +102,14 @@ def test_scene_generator_and_refit_end_to_end():
     # strong outlier are still converging after 10 steps
     err = np.abs(coef[4:-4, 4:-4, 0] - c["coef"][4:-4, 4:-4, 0])
     assert np.median(err) < 1.0 and np.mean(err > 3.0) < 0.02
+
+
+def test_points_match_full_image():
+    from paper_2209_09848_gb300 import synth
+    c = synth.background_case(40, 30, 26, seed=6, n=8)
+    coef, R = ob.refit(c["D"], c["jitter"], 1.345, 6, S=c["S"])
+    g = np.random.default_rng(0)
+    ys, xs = g.integers(0, 30, 20), g.integers(0, 26, 20)
+    cp, Rp = ob.refit_points(c["D"][:, ys, xs], ys, xs, 30, 26, c["jitter"], 1.345, 6, S=c["S"])
+    np.testing.assert_allclose(cp, coef[ys, xs], rtol=1e-10, atol=1e-9)
+    np.testing.assert_allclose(Rp, R[:, ys, xs], rtol=1e-10, atol=1e-9)
