@@ -49,7 +49,9 @@ double orc_pixel_integrated_gauss(int a, double phase, double sigma)
  * centre of the base pixel.  taps[(dy + 2) * 5 + (dx + 2)] is the fraction
  * of the flux that lands in the pixel (dx, dy) away from the base pixel.
  * kind 0: pixel-integrated Gaussian; kind 1: Gaussian sampled at pixel
- * centres.  Either way the footprint is divided by its own sum. */
+ * centres; kind 2: the shift-stack filter (Section 3.2, after Rice et al.
+ * 2020): a single value of 1 in the pixel that holds the source's centre
+ * (the base pixel), 0 elsewhere.  The footprint is divided by its own sum. */
 void orc_prf_taps(double phx, double phy, double sigma, int kind, double *taps)
 {
     double total = 0.0;
@@ -59,6 +61,8 @@ void orc_prf_taps(double phx, double phy, double sigma, int kind, double *taps)
             if (kind == 0) {
                 w = orc_pixel_integrated_gauss(dx, phx, sigma) *
                     orc_pixel_integrated_gauss(dy, phy, sigma);
+            } else if (kind == 2) {
+                w = (dx == 0 && dy == 0) ? 1.0 : 0.0;
             } else {
                 double ex = dx - phx, ey = dy - phy;
                 w = exp(-(ex * ex + ey * ey) / (2.0 * sigma * sigma));

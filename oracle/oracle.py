@@ -10,7 +10,9 @@ Functions and the passages they follow:
 * ``prf_taps``, ``trajectory_table`` -- Section 2 (the PRF spreads a point
   source over neighbouring pixels; trajectories are straight lines in pixel
   space) and Section 3.2 (a filter is the trajectory line convolved with the
-  PRF).  Gaussian PRF of width ``sigma_prf``, 5x5 footprint, renormalised.
+  PRF).  Gaussian PRF of width ``sigma_prf``, 5x5 footprint, renormalised;
+  kind 2 is the shift-stack filter (Section 3.2: a single 1 in the pixel
+  holding the source's centre).
 * ``trajectory_table_frames`` -- the same with each frame's time (Fig. 3:
   the downlink gap makes time jump) and the pointing jitter (Section 2.1;
   Section 3.2: the filter follows the trajectory including the jitter).

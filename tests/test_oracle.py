@@ -505,3 +505,32 @@ def test_jittered_gapped_injection_closed_form(oracle):
         s_lin, t_lin = oracle.trajectory_table(vx, vy, T)
         N2, D2 = oracle.search_points(res.astype(np.float32), lam, s_lin, t_lin, [py], [px], [k])
         assert N2[0] / D2[0] < 0.9 * f
+
+
+def test_shift_stack_kind_is_single_tap_shift_and_add(oracle):
+    """Section 3.2: the shift-stack filter of Rice et al. has one value of 1
+    per frame, in the pixel holding the source's centre; N is then the sum of
+    the weighted frames shifted along the trajectory (numpy roll-and-add)."""
+    for ph in [(0.0, 0.0), (0.49, -0.3), (-0.5, 0.2)]:
+        t = oracle.prf_taps(*ph, kind=2)
+        assert t[2, 2] == 1.0 and t.sum() == 1.0
+    g = _rng(12)
+    T, H, W = 9, 30, 34
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    vx, vy = np.array([0.37, -0.61]), np.array([0.22, 0.45])
+    shifts, taps = oracle.trajectory_table(vx, vy, T, kind=2)
+    lam = oracle.inverse_variance(sigma)
+    N, D = oracle.search_full(res, lam, shifts, taps)
+    wr = res.astype(np.float64) * lam[None]
+    for k in range(2):
+        n = np.zeros((H, W))
+        d = np.zeros((H, W))
+        for t in range(T):
+            sx = int(np.floor(vx[k] * t + 0.5))
+            sy = int(np.floor(vy[k] * t + 0.5))
+            n += np.roll(wr[t], (-sy, -sx), axis=(0, 1))
+            d += np.roll(lam, (-sy, -sx), axis=(0, 1))
+        inner = (slice(6, H - 6), slice(6, W - 6))
+        np.testing.assert_allclose(N[k][inner], n[inner], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(D[k][inner], d[inner], rtol=1e-12, atol=1e-12)
