@@ -134,19 +134,19 @@ def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> flo
     return units_per_rank * world / seconds_max
 
 
-def flop_per_unit(kernel: int, vx) -> float:
+def flop_per_unit(kernel: int, vx, taps: int = 5) -> float:
     """Algorithmic FP32 flops per (trajectory, pixel, frame) of the numerator
     form the plan uses.  General 5 x 5 footprint: 25 FMAs.  Factored form
-    (separable footprint): a 5-tap column pass per trajectory, plus a 5-tap
-    row pass shared by all trajectories with the same v_x, i.e. 5 * C / K
-    FMAs per unit for C distinct v_x among K trajectories (halo rows and
-    columns, and classes split over several CTAs, are overhead, not
-    algorithmic work)."""
+    (separable footprint): a `taps`-tap column pass per trajectory, plus a
+    `taps`-tap row pass shared by all trajectories with the same v_x, i.e.
+    taps * C / K FMAs per unit for C distinct v_x among K trajectories (halo
+    rows and columns, and classes split over several CTAs, are overhead, not
+    algorithmic work); taps = 1 for the shift-stack filter."""
     if kernel != 2:
         return float(FLOP_PER_UNIT_GENERAL)
     K = len(vx)
     C = len(set(float(v) for v in vx))
-    return 2.0 * (5.0 + 5.0 * C / K)
+    return 2.0 * (taps + taps * C / K)
 
 
 def _traffic_from_profiles(kernel: int = 2):
@@ -165,7 +165,7 @@ def _traffic_from_profiles(kernel: int = 2):
     return None
 
 
-def cpu_oracle_sample(res_dev, sigma_np, mask_np, vx, vy, T, budget_s=15.0, threads=None):
+def cpu_oracle_sample(res_dev, sigma_np, mask_np, vx, vy, T, budget_s=15.0, threads=None, kind=0):
     """Time the FP64 oracle on host cores over a crop of the same workload:
     all trajectories and frames, start pixels in a centred square sized for
     about `budget_s` seconds of CPU work.  Returns (units/s, cores, sample text,
@@ -176,7 +176,7 @@ def cpu_oracle_sample(res_dev, sigma_np, mask_np, vx, vy, T, budget_s=15.0, thre
     oracle.build()
     cores = threads or oracle.threads()
     H, W = sigma_np.shape
-    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    shifts, taps = oracle.trajectory_table(vx, vy, T, kind=kind)
     halo = int(np.abs(shifts).max()) + 3
 
     def run(side):
@@ -282,7 +282,8 @@ def run_ours(args):
     case = synth.paper_case_gpu(T=T, H=H, W=W, seed=1 + rank, device=dev)
     vx, vy = synth.velocity_grid(NXG, NYG, -args.vmax, args.vmax)
     K = len(vx)
-    table = mf.prf_table_create(vx, vy, T, kernel=args.kernel or None)
+    kind = 2 if args.prf == "shiftstack" else 0
+    table = mf.prf_table_create(vx, vy, T, kind=kind, kernel=args.kernel or None)
     info = table.info()
     res, sigma, mask = case["res"], case["sigma"], case["mask"]
     ws_search = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
@@ -332,9 +333,12 @@ def run_ours(args):
     num_launches, num_ms_total = prof["k_numerator"]
     num_ms = num_ms_total / args.steps
     peak_tf = _fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-    fpu = flop_per_unit(info["kernel"], vx)
+    fpu = flop_per_unit(info["kernel"], vx, info.get("taps", 5))
     achieved_tf = units_rank * fpu / (num_ms * 1e-3) / 1e12
-    traffic = _traffic_from_profiles(info["kernel"])
+    # the committed ncu figure holds for the profiled workload only: the
+    # default paper-shaped search with the Gaussian footprint
+    profiled = (T, H, args.vmax, kind) == (T_FR, HH, VMAX, 0)
+    traffic = _traffic_from_profiles(info["kernel"]) if profiled else None
     kernel_ms = {k: round(v[1] / args.steps, 3) for k, v in prof.items() if k != "_launches" and v[0]}
     launches = int(prof["_launches"])
 
@@ -387,7 +391,7 @@ def run_ours(args):
         sig_np = case["sigma_np"]
         msk_np = case["mask_np"]
         rate, cores, sample, (N, D, (y0, x0), side) = cpu_oracle_sample(res, sig_np, msk_np, vx, vy, T,
-                                                                        budget_s=args.cpu_budget)
+                                                                        budget_s=args.cpu_budget, kind=kind)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
         # the same crop searched on the GPU just above: report the agreement
         import oracle
@@ -405,8 +409,9 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "paper-shaped search: %d frames x %dx%d px float32, %d trajectories "
                                    "(%dx%d grid, |v|<=%.2f px/frame), sigma log-normal, 1%% star mask, "
-                                   "200 movers; search + top-%d FP64 rescore per step" % (
-                                       T, H, W, K, NXG, NYG, args.vmax, K_TOP),
+                                   "200 movers; search + top-%d FP64 rescore per step%s" % (
+                                       T, H, W, K, NXG, NYG, args.vmax, K_TOP,
+                                       "; shift-stack filter (one tap per frame, Section 3.2)" if kind == 2 else ""),
                        "frames": T, "height": H, "width": W, "trajectories": K,
                        "l2": "inputs larger than L2 (%.1f GB stack per step)" % (T * H * W * 4 / 1e9),
                        "plan": {k: info[k] for k in ("kernel", "groups", "warps_per_group", "tile_h", "tile_w",
@@ -890,6 +895,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rescore", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--prf", choices=["gauss", "shiftstack"], default="gauss",
+                    help="filter footprint: the Gaussian PRF, or the single-tap shift-stack filter")
     ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
                     help="numerator: 0 planner's choice, 1 general 5x5, 2 factored")
     ap.add_argument("--workload", choices=["search", "batch", "serve", "precision", "detect", "refit"],

@@ -68,7 +68,10 @@ typedef enum {
  * of width sigma_px stands in).  The footprint is always 5 x 5 pixels around
  * the base pixel and is renormalised to unit sum at each sub-pixel phase.
  *   kind 0: Gaussian integrated over each pixel (erf differences);
- *   kind 1: Gaussian sampled at pixel centres. */
+ *   kind 1: Gaussian sampled at pixel centres;
+ *   kind 2: the shift-stack filter (Section 3.2, after Rice et al. 2020): a
+ *           single 1 in the base pixel, the pixel holding the source's
+ *           centre; sigma_px must still be a finite value > 0 (unused). */
 typedef struct {
     int32_t kind;
     int32_t reserved;
@@ -230,7 +233,8 @@ typedef struct {
     int32_t kernel;           /* numerator: 1 general, 2 factored (see mf_plan_opts) */
     int32_t stages;           /* frame windows in flight per CTA */
     int32_t time_segments;    /* time segments of the factored numerator (1 otherwise) */
-    int32_t reserved;
+    int32_t taps;             /* footprint taps per axis the factored passes run: 5, or 1
+                                 when every footprint is a single centre tap (kind 2) */
 } mf_table_info;
 
 /* Layout of an existing table. */

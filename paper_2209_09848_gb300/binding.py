@@ -97,7 +97,7 @@ class TableInfo(ctypes.Structure):
                 ("max_abs_shift", ctypes.c_int32), ("g_nnz", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("cost", ctypes.c_double), ("vec", ctypes.c_int32),
                 ("lockstep", ctypes.c_int32), ("kernel", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("time_segments", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("time_segments", ctypes.c_int32), ("taps", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

@@ -44,11 +44,12 @@ using namespace dev;
 // the barriers only.  `smem` is the CTA's 1024-aligned dynamic shared memory.
 // One row-pass item: H(row, c0 .. c0 + 15) = sum_a u_x(a) R(row, c0 + M + c + a)
 // for a column phase M known at compile time; src = R(row, c0), 16-aligned,
-// dst = H(row, c0).
-template <int M>
+// dst = H(row, c0).  TAPS = 1 (single-tap footprints: the shift-stack
+// filter) keeps the centre tap only.
+template <int M, int TAPS>
 __device__ __forceinline__ void row_item(const float *__restrict__ src, float *__restrict__ dst, float ux0,
                                          float ux1, float ux2, float ux3, float ux4) {
-    constexpr int NL = (kFacItem + 4 + M + 3) / 4;  // 128-bit loads covering the inputs
+    constexpr int NL = (kFacItem + (TAPS == 1 ? 3 : 4) + M + 3) / 4;  // 128-bit loads covering the inputs
     float v[4 * NL];
 #pragma unroll
     for (int q = 0; q < NL; q++) {
@@ -61,11 +62,15 @@ __device__ __forceinline__ void row_item(const float *__restrict__ src, float *_
     float o[kFacItem];
 #pragma unroll
     for (int c = 0; c < kFacItem; c++) {
-        float h = ux0 * v[M + c];
-        h = fmaf(ux1, v[M + c + 1], h);
-        h = fmaf(ux2, v[M + c + 2], h);
-        h = fmaf(ux3, v[M + c + 3], h);
-        o[c] = fmaf(ux4, v[M + c + 4], h);
+        if (TAPS == 1) {
+            o[c] = ux2 * v[M + c + 2];
+        } else {
+            float h = ux0 * v[M + c];
+            h = fmaf(ux1, v[M + c + 1], h);
+            h = fmaf(ux2, v[M + c + 2], h);
+            h = fmaf(ux3, v[M + c + 3], h);
+            o[c] = fmaf(ux4, v[M + c + 4], h);
+        }
     }
 #pragma unroll
     for (int q = 0; q < kFacItem / 4; q++)
@@ -97,7 +102,7 @@ __device__ __forceinline__ bool fac_locate(const FacParams &p, int tw, long long
     return true;
 }
 
-template <int TW>
+template <int TW, int TAPS>
 __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParams &p, long long cta,
                                          unsigned char *smem) {
     constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / kFacItem;
@@ -188,11 +193,13 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         const float2 u5 = *reinterpret_cast<const float2 *>(fs->uy + 4);  // u_y(2) and the row offset
         const float u[5] = {u4.x, u4.y, u4.z, u4.w, u5.x};
         const float *col = hbuf + (size_t)(f % kFacHBufs) * BH * HP + (32 * sub_y + 16 * rh + __float_as_int(u5.y)) * HP + 32 * sub_x + 2 * cp;
+        // taps b = B0 .. B1 of the footprint (all five, or the centre one)
+        constexpr int B0 = 2 - TAPS / 2, B1 = 2 + TAPS / 2;
 #pragma unroll
-        for (int i = 0; i < 20; i++) {
+        for (int i = B0; i < 16 + B1; i++) {
             const float2 h = *reinterpret_cast<const float2 *>(col + i * HP);
 #pragma unroll
-            for (int b = 0; b < 5; b++) {
+            for (int b = B0; b <= B1; b++) {
                 const int r = i - b;
                 if (r >= 0 && r < 16) {
                     blk[2 * r] = fmaf(u[b], h.x, blk[2 * r]);
@@ -217,10 +224,10 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
             float *dst = hbuf + (size_t)(f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
             const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
             switch (cofs) {
-                case 0: row_item<0>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                case 1: row_item<1>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                case 2: row_item<2>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                default: row_item<3>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                case 0: row_item<0, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                case 1: row_item<1, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                case 2: row_item<2, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                default: row_item<3, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
             }
         }
     };
@@ -300,12 +307,12 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     return true;
 }
 
-template <int TW>
+template <int TW, int TAPS>
 __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant__ CUtensorMap ymap,
                                                           const FacParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    fac_tile<TW>(ymap, p, (long long)blockIdx.x, smem);
+    fac_tile<TW, TAPS>(ymap, p, (long long)blockIdx.x, smem);
 }
 
 // Persistent factored numerator over a batch of searches: one CTA per SM
@@ -338,7 +345,9 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMa
         __syncthreads();
         if (w >= total) break;
         const FacParams &p = items[i].p;
-        if (!fac_tile<TW>(maps[i], p, w - items[i].cta_begin, smem)) break;
+        // the five-tap code: single-tap footprints give the same sums (zero
+        // taps add exact zeros), so a batch of mixed tables needs one kernel
+        if (!fac_tile<TW, 5>(maps[i], p, w - items[i].cta_begin, smem)) break;
         __syncthreads();
     }
 }
@@ -436,11 +445,12 @@ int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, 
     return 0;
 }
 
-int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int warps, size_t smem, long long nblocks,
-                void *stream, char *err, size_t errlen) {
+int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int taps, int warps, size_t smem,
+                long long nblocks, void *stream, char *err, size_t errlen) {
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(tensor_map);
     void (*kern)(const CUtensorMap, const FacParams) =
-        tw == 64 ? k_numerator_fac<64> : k_numerator_fac<32>;
+        tw == 64 ? (taps == 1 ? k_numerator_fac<64, 1> : k_numerator_fac<64, 5>)
+                 : (taps == 1 ? k_numerator_fac<32, 1> : k_numerator_fac<32, 5>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));

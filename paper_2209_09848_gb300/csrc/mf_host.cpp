@@ -47,9 +47,12 @@ int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // One axis of the PRF's 5 x 5 footprint for a source at sub-pixel offset ph
 // from the base pixel, before normalisation (Section 2: the PRF shares a
 // point source's flux between neighbouring pixels).  kind 0 integrates a
-// Gaussian over each pixel, kind 1 samples it at the pixel centre.
+// Gaussian over each pixel, kind 1 samples it at the pixel centre, kind 2 is
+// the shift-stack filter of Section 3.2 (all the weight in the base pixel).
 void axis_profile(int kind, double sigma, double ph, double *g) {
-    if (kind == 0) {
+    if (kind == 2) {
+        for (int i = 0; i < 5; i++) g[i] = i == 2 ? 1.0 : 0.0;
+    } else if (kind == 0) {
         // pixel d spans [d - 1/2, d + 1/2]: six shared boundaries
         const double s = sigma * std::sqrt(2.0);
         double e[6];
@@ -462,6 +465,13 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
     int mxs = 0;
     for (size_t i = 0; i < t.shifts.size(); i++) mxs = std::max(mxs, std::abs(t.shifts[i]));
     out.max_abs_shift = mxs;
+    // single centre tap on both axes for every (trajectory, frame): the
+    // passes need only the centre tap
+    bool single = true;
+    for (size_t i = 0; i < t.fx.size() && single; i += 5)
+        for (int a = 0; a < 5; a++)
+            if (t.fx[i + a] != (a == 2 ? 1.0 : 0.0) || t.fy[i + a] != (a == 2 ? 1.0 : 0.0)) single = false;
+    out.f_taps = single ? 1 : 5;
     return true;
 }
 
@@ -841,6 +851,7 @@ void fill_info(const mf_prf_table *t, mf_table_info *info) {
     info->kernel = t->plan.kernel;
     info->stages = fac ? t->plan.f_ns : mf::kStages;
     info->time_segments = fac ? t->plan.f_seg : 1;
+    info->taps = fac ? t->plan.f_taps : 5;
     info->device_bytes = (int64_t)t->device_bytes;
 }
 
@@ -951,7 +962,7 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
     if (!prf || !vx || !vy) return fail(MF_EINVAL, "NULL argument");
     if (K < 1 || T < 1) return fail(MF_EINVAL, "K=%d and T=%d must be >= 1", K, T);
     if (T > (1 << 20) || K > (1 << 22)) return fail(MF_EINVAL, "K or T too large");
-    if (prf->kind != 0 && prf->kind != 1) return fail(MF_EINVAL, "unknown PRF kind %d", prf->kind);
+    if (prf->kind < 0 || prf->kind > 2) return fail(MF_EINVAL, "unknown PRF kind %d", prf->kind);
     if (!(prf->sigma_px > 0.0) || !std::isfinite(prf->sigma_px))
         return fail(MF_EINVAL, "sigma_px must be finite and > 0");
     const double *times = frames ? frames->times : nullptr;

@@ -138,6 +138,7 @@ struct Plan {
     // smallest s_y of the members at the segment's first frame and the
     // members' spread there; per (group, segment, slot) that member's s_y
     int f_seg = 1;
+    int f_taps = 5;      // factored footprint taps per axis: 5, or 1 (single centre tap)
     std::vector<int32_t> seg_t0;      // f_seg + 1
     std::vector<int32_t> seg_qy;      // G * f_seg * 2: (min s_y, spread)
     std::vector<int32_t> seg_ref;     // G * f_seg * kt, INT32_MIN for an empty slot
@@ -360,8 +361,10 @@ int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen);
 int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, long long total,
                       unsigned long long *counter, int tw, int warps, size_t smem, int grid, void *stream, char *err,
                       size_t errlen);
-int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int warps, size_t smem, long long nblocks,
-                void *stream, char *err, size_t errlen);
+// taps: 5, or 1 when every footprint is a single centre tap (the shift-stack
+// filter), which runs the row and column passes on the centre tap only.
+int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int taps, int warps, size_t smem,
+                long long nblocks, void *stream, char *err, size_t errlen);
 
 // Record an error message for mf_last_error() and return the status.
 mf_status set_error(mf_status s, const char *msg);

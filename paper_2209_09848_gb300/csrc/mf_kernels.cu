@@ -874,7 +874,7 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
         for (int j = 0; j < pl.f_seg; j++) {
             fp.seg = j;
             LaunchScope ls(kKNumerator, stream);
-            rc = fac_enqueue(&map, fp, pl.f_tw, pl.launch_warps(), pl.smem(), fac_ctas(*a.tab, a.stack->H,
+            rc = fac_enqueue(&map, fp, pl.f_tw, pl.f_taps, pl.launch_warps(), pl.smem(), fac_ctas(*a.tab, a.stack->H,
                                                                                        a.stack->W, j),
                              stream, err, errlen);
             if (rc) return rc;

@@ -259,3 +259,50 @@ def test_factored_needs_separable_table(mf):
     assert t.info()["kernel"] == 1
     with pytest.raises(mf.MFError):
         mf.prf_table_create(np.zeros(2), np.zeros(2), 4, kernel=2, group=17)
+
+
+@pytest.mark.parametrize("layout", [{}, {"kernel": 1}, {"kernel": 2, "group": 3, "tile_w": 64},
+                                    {"kernel": 2, "segments": 3}])
+def test_shift_stack_matches_oracle(mf, oracle, layout):
+    """The shift-stack filter (Section 3.2: one 1 per frame in the pixel
+    holding the source): the factored numerator runs its single-tap passes,
+    the general one its 25 taps with 24 zeros; both give the oracle's
+    answer."""
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 36, 133, 150
+    c = synth.small_case(T, H, W, 71, mask_frac=0.02, movers=3)
+    vx, vy = synth.velocity_grid(5, 4, -0.45, 0.45)
+    table = mf.prf_table_create(vx, vy, T, kind=2, **layout)
+    info = table.info()
+    if info["kernel"] == 2:
+        assert info["taps"] == 1
+    sh, tp = oracle.trajectory_table(vx, vy, T, kind=2)
+    sg, tg = table.export()
+    assert np.array_equal(sg, sh) and np.array_equal(tg, tp)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+    check_search(smax, amax, sall, N, D, oracle, label="shift-stack %s" % layout)
+
+
+def test_shift_stack_single_tap_equals_batch(mf):
+    """The batched launch runs the five-tap passes on the same single-tap
+    table; zero taps add exact zeros, so the maps are bit-identical."""
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 24, 96, 112
+    c = synth.small_case(T, H, W, 5, mask_frac=0.01, movers=2)
+    vx, vy = synth.velocity_grid(4, 4, -0.3, 0.3)
+    table = mf.prf_table_create(vx, vy, T, kind=2)
+    assert table.info()["taps"] == 1
+    r = torch.from_numpy(c["res"]).cuda()
+    s = torch.from_numpy(c["sigma"]).cuda()
+    m = torch.from_numpy(c["mask"]).cuda()
+    smax, amax, _ = mf.search(r, s, table, mask=m)
+    b = mf.Batch()
+    b.add(r, s, table, mask=m)
+    b.prepare()
+    b.run()
+    torch.cuda.synchronize()
+    bmax, bamax, _ = b.outputs[0]
+    assert torch.equal(smax, bmax) and torch.equal(amax, bamax)
+    assert mf.prf_table_create(vx, vy, T).info()["taps"] == 5
