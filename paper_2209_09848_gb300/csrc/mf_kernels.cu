@@ -201,9 +201,6 @@ template <int VEC>
 __device__ __forceinline__ int lane_skew(int ty) {
     return VEC == 1 ? ty : (VEC == 2 ? 2 * (ty & 3) : 4 * (ty & 1));
 }
-__host__ __device__ __forceinline__ int skew_of(int vec, int ty) {
-    return vec == 1 ? ty : (vec == 2 ? 2 * (ty & 3) : 4 * (ty & 1));
-}
 
 // The 4 x 8 block of one lane for one (trajectory, frame): 8 window rows of
 // 12 values each, 25 FMAs per output.  `base` is the lane's first window value
