@@ -490,6 +490,10 @@ mf_status mf_batch_add(mf_batch *batch, const mf_stack *stack, const float *sigm
 mf_status mf_batch_workspace_size(const mf_batch *batch, size_t *bytes);
 mf_status mf_batch_prepare(mf_batch *batch, void *workspace, size_t workspace_bytes);
 mf_status mf_batch_run(mf_batch *batch, mf_stream stream);
+/* Whether the work of the latest mf_batch_run has finished on the device,
+ * without waiting: *done = 1 (finished, or never run) or 0 (in flight).
+ * Errors: MF_EINVAL (NULL pointers), MF_ECUDA (a failed launch surfaced). */
+mf_status mf_batch_poll(const mf_batch *batch, int32_t *done);
 /* Number of searches, of persistent numerator launches (one per general
  * CTA shape and one per factored tile width present) and whether the graph
  * has been captured. */

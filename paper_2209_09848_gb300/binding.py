@@ -159,6 +159,7 @@ def load():
             "mf_batch_workspace_size": ([P, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_batch_prepare": ([P, P, SZ], ctypes.c_int),
             "mf_batch_run": ([P, P], ctypes.c_int),
+            "mf_batch_poll": ([P, ctypes.POINTER(I32)], ctypes.c_int),
             "mf_batch_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
             "mf_batch_destroy": ([P], None),
             "mf_last_error": ([], ctypes.c_char_p),
@@ -568,6 +569,12 @@ class Batch:
 
     def run(self, stream=None):
         _check(load().mf_batch_run(self._h, _stream_ptr(stream)))
+
+    def poll(self) -> bool:
+        """True once the latest run has finished on the device (mf_batch_poll)."""
+        d = ctypes.c_int32()
+        _check(load().mf_batch_poll(self._h, ctypes.byref(d)))
+        return bool(d.value)
 
     def info(self) -> dict:
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

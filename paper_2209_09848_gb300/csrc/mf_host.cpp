@@ -1215,6 +1215,8 @@ struct mf_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture = nullptr;  // private stream the graph is captured on
+    cudaEvent_t done = nullptr;      // recorded after every run, for mf_batch_poll
+    bool ran = false;
     bool prepared = false;
 };
 
@@ -1233,6 +1235,9 @@ void batch_release(mf_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->done) cudaEventDestroy(b->done);
+    b->done = nullptr;
+    b->ran = false;
     b->exec = nullptr;
     b->graph = nullptr;
     b->capture = nullptr;
@@ -1338,7 +1343,30 @@ mf_status mf_batch_run(mf_batch *b, mf_stream stream) {
     }
     cudaError_t e = cudaGraphLaunch(b->exec, st);
     if (e != cudaSuccess) return fail(MF_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    if (!b->done && (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(MF_ECUDA, "cudaEventCreateWithFlags: %s", cudaGetErrorString(e));
+    if ((e = cudaEventRecord(b->done, st)) != cudaSuccess)
+        return fail(MF_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    b->ran = true;
     return ok();
+}
+
+mf_status mf_batch_poll(const mf_batch *b, int32_t *done) {
+    if (!b || !done) return fail(MF_EINVAL, "NULL argument");
+    if (!b->ran) {
+        *done = 1;  // nothing launched
+        return ok();
+    }
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaSuccess) {
+        *done = 1;
+        return ok();
+    }
+    if (e == cudaErrorNotReady) {
+        *done = 0;
+        return ok();
+    }
+    return fail(MF_ECUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
 }
 
 mf_status mf_batch_info(const mf_batch *b, int32_t *items, int32_t *shape_groups, int32_t *graph_ready) {

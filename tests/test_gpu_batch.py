@@ -70,6 +70,10 @@ def test_batch_equals_individual_searches(mf, oracle):
             o[1].fill_(-7)
             o[2].fill_(-7.0)
         b.run()
+        for _ in range(200000):  # poll until the device is done (never blocks)
+            if b.poll():
+                break
+        assert b.poll()
         torch.cuda.synchronize()
         assert mf.device_status() == 0
         assert b.info()["graph_ready"]
@@ -87,6 +91,7 @@ def test_batch_equals_individual_searches(mf, oracle):
 
 def test_batch_argument_errors(mf):
     b = mf.Batch()
+    assert b.poll()  # nothing launched yet
     with pytest.raises(mf.MFError):
         b.run()  # not prepared
     with pytest.raises(mf.MFError):
