@@ -96,3 +96,15 @@ def test_segments_shrink_the_window(mf):
     assert mf.prf_plan(vx, vy, 24, kernel=2, segments=3)["time_segments"] == 3
     with pytest.raises(mf.MFError):
         mf.prf_plan(vx, vy, 24, kernel=2, segments=4)
+
+
+def test_shift_stack_plans_single_tap_passes(mf):
+    # PRF kind 2 (one tap of 1 in the base pixel): the factored numerator
+    # runs its single-tap passes; the Gaussian runs five taps
+    vx, vy = _grid(10, 10)
+    info = mf.prf_plan(vx, vy, 400, kind=2)
+    assert info["kernel"] == 2 and info["taps"] == 1
+    assert mf.prf_plan(vx, vy, 400)["taps"] == 5
+    assert mf.prf_plan(vx, vy, 400, kind=1)["taps"] == 5
+    with pytest.raises(mf.MFError):
+        mf.prf_plan(vx, vy, 400, kind=3)
