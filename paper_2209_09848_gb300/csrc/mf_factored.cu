@@ -176,9 +176,11 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     const int ref = kk >= 0 ? p.refs[((size_t)g * p.S + seg) * KT + slot] : 0;
     const int qrow = tile_y0 + 32 * sub_y - ref;
     const bool active = kk >= 0 && qrow + 32 > 0 && qrow < p.H && tile_x0 + 32 * sub_x < p.W;
-    // lane: column pair cp (2 adjacent columns), row half rh (16 rows)
+    // five taps: lane = column pair cp (2 adjacent columns) x row half rh
+    // (16 rows), acc / blk[r * 2 + j] at row 16 rh + r, column 2 cp + j;
+    // single tap: lane = column, acc / blk[r] at row r
     const int cp = lane & 15, rh = lane >> 4;
-    float acc[32], blk[32];  // [r * 2 + j]: row 16 rh + r, column 2 cp + j
+    float acc[32], blk[32];
 #pragma unroll
     for (int r = 0; r < 32; r++) {
         acc[r] = 0.f;
@@ -207,6 +209,20 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
                 }
             }
         }
+    };
+    // single tap (both factors one-hot at the centre, exactly 1): the column
+    // pass adds the window's values at the base pixel straight from the
+    // stage, blk += R(row + oy + 2, column + 2 + cofs) -- the same sums in the
+    // same order as the five-tap passes on such a table (zero taps add exact
+    // zeros), so the results are bit-identical
+    auto column_direct = [&](int f, int st) {
+        if (!active) return;
+        const unsigned char *fblk = record(f);
+        const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
+        const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
+        const float *col = rwin + (size_t)st * SF + (32 * sub_y + fs->oy + 2) * RP + 32 * sub_x + lane + 2 + fh->cofs;
+#pragma unroll
+        for (int r = 0; r < 32; r++) blk[r] += col[r * RP];
     };
     // the row passes of frames f0 (stage s0) and f0 + 1 (stage s1, if it
     // exists) as one list of items: item it < n0 is (row, m) of frame f0
@@ -241,7 +257,16 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
         bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
         if (ready && two) ready = mbar_wait(smem_u32(&bars[s1]), par1, 1, p.status);
-        if (ready) row_pair(t, s, s1, two);
+        if (TAPS == 1) {
+            // the column passes read the stages themselves: they run before
+            // the barrier that frees the stages for refilling
+            if (ready) {
+                column_direct(t, s);
+                if (two) column_direct(t + 1, s1);
+            }
+        } else if (ready) {
+            row_pair(t, s, s1, two);
+        }
         if (__syncthreads_or(!ready)) {
             bad = true;
             break;
@@ -258,8 +283,10 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
                 issue(t + 1 + NS, s1, fh->next_roy, fh->next_rox);
             }
         }
-        column(t);
-        if (two) column(t + 1);
+        if (TAPS != 1) {
+            column(t);
+            if (two) column(t + 1);
+        }
         if ((t - t0 + 2) % kFrameBlock == 0) {
 #pragma unroll
             for (int r = 0; r < 32; r++) {
@@ -292,9 +319,8 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         float *plane = p.plane + (size_t)kk * P;
 #pragma unroll
         for (int r = 0; r < 32; r++) {
-            const int rr = r >> 1, jj = r & 1;
-            const int64_t px = tile_x0 + 32 * sub_x + 2 * cp + jj;
-            const int64_t py = (int64_t)tile_y0 + 32 * sub_y + 16 * rh + rr - ref;
+            const int64_t px = tile_x0 + 32 * sub_x + (TAPS == 1 ? lane : 2 * cp + (r & 1));
+            const int64_t py = (int64_t)tile_y0 + 32 * sub_y + (TAPS == 1 ? r : 16 * rh + (r >> 1)) - ref;
             if (py >= 0 && py < p.H && px < p.W) {
                 const int64_t q = py * p.W + px;
                 plane[q] = seg == 0 ? acc[r] + blk[r] : plane[q] + (acc[r] + blk[r]);

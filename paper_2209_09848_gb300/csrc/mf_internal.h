@@ -80,8 +80,8 @@ struct alignas(16) RunRec {
 // v_y) makes the row pass once per frame for all of them.
 //
 // CTA: (slots per CTA) x (tile_h / 32) x (tile_w / 32) warps, each warp one
-// (trajectory slot, 32 x 32 sub-tile); lane = output column, 32 rows per
-// lane.  The staged window R of a frame is a TMA box of fac_rpitch(tile_w)
+// (trajectory slot, 32 x 32 sub-tile); a lane owns 2 columns x 16 rows (five
+// taps) or 1 column x 32 rows (single-tap footprints).  The staged window R of a frame is a TMA box of fac_rpitch(tile_w)
 // columns (the box is as wide as the row pitch) and BH rows.
 struct alignas(16) FacHdr {
     int32_t next_roy, next_rox;  // window origin of frame t + stages, relative to the tile origin
