@@ -31,7 +31,9 @@ from . import binding as mf
 class Request:
     """One search.  Host tensors (pinned for fast uploads): stack [T, H, W]
     float32 / bfloat16 / float16, sigma [H, W] float32, mask [H, W] uint8 or
-    None, frame_scale [T] float32 or None; velocities vx, vy (px/frame)."""
+    None, frame_scale [T] float32 or None; velocities vx, vy (px/frame);
+    optionally the frames' times [T] and pointing jitter [T, 2] (the filter
+    bank then follows them) and the PRF kind (2: shift-stack filter)."""
     stack: torch.Tensor
     sigma: torch.Tensor
     vx: np.ndarray
@@ -41,6 +43,9 @@ class Request:
     k_top: int = 0
     sigma_px: float = 0.7
     tag: object = None
+    times: np.ndarray | None = None
+    jitter: np.ndarray | None = None
+    kind: int = 0
 
 
 @dataclasses.dataclass
@@ -131,7 +136,8 @@ class Server:
     def _plan(self, req: Request):
         torch.cuda.set_device(self.device)
         T = req.stack.shape[0]
-        table = mf.prf_table_create(req.vx, req.vy, T, sigma_px=req.sigma_px)
+        table = mf.prf_table_create(req.vx, req.vy, T, sigma_px=req.sigma_px, kind=req.kind, times=req.times,
+                                    jitter=req.jitter)
         return table, footprint_bytes(req, table)
 
     # ----------------------------------------------------------- admission

@@ -73,3 +73,24 @@ def test_oversized_request_fails_alone():
     assert futs[2].result(timeout=120).snr_max.shape == reqs[0].sigma.shape
     srv.close()
     assert srv.rejected == 1
+
+
+def test_request_with_frame_model_and_shift_stack():
+    # a request carrying frame times, jitter and the shift-stack kind is
+    # searched with that filter bank: its result equals mf.search on a table
+    # built the same way
+    from paper_2209_09848_gb300.serve import Server
+    import paper_2209_09848_gb300 as mf
+    r = _requests(1, seed=3, sides=(192,), frames=(40, 41))[0]
+    T = r.stack.shape[0]
+    g = np.random.default_rng(4)
+    r.times = np.arange(T, dtype=np.float64) + np.where(np.arange(T) >= T // 2, 30.0, 0.0)
+    r.jitter = g.uniform(-0.2, 0.2, size=(T, 2))
+    r.kind = 2
+    srv = Server(budget_bytes=1 << 34, streams=2)
+    res = srv.submit(r).result(timeout=120)
+    srv.close()
+    table = mf.prf_table_create(r.vx, r.vy, T, kind=2, times=r.times, jitter=r.jitter)
+    smax, amax, _ = mf.search(r.stack.cuda(), r.sigma.cuda(), table, mask=r.mask.cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(res.snr_max, smax.cpu().numpy()) and np.array_equal(res.argmax, amax.cpu().numpy())
