@@ -81,6 +81,7 @@ def test_frames_default_equals_linear_table(mf):
 
 def test_frames_rescore_uses_the_frame_model(mf, oracle):
     # the FP64 re-score reads the table's shifts and taps: the jittered ones
+    # (candidates picked from a host-generated score map)
     from paper_2209_09848_gb300 import synth
     T, H, W = 16, 48, 64
     c = synth.small_case(T, H, W, 3, mask_frac=0.01, movers=2)
@@ -90,14 +91,19 @@ def test_frames_rescore_uses_the_frame_model(mf, oracle):
     r = torch.from_numpy(c["res"]).cuda()
     s = torch.from_numpy(c["sigma"]).cuda()
     m = torch.from_numpy(c["mask"]).cuda()
-    smax, amax, _ = mf.search(r, s, table, mask=m)
-    raw, n = mf.rescore_topk(r, s, table, smax, amax, 32, mask=m)
+    s_max, a_max = synth.score_map(H, W, seed=12, K=len(vx), mask_frac=0.0)
+    raw, n = mf.rescore_topk(r, s, table, torch.from_numpy(s_max).cuda(), torch.from_numpy(a_max).cuda(), 32,
+                             mask=m)
     torch.cuda.synchronize()
     cand = mf.decode_candidates(raw, int(n.item()))
+    want = oracle.topk_order(s_max, a_max, 32)
+    assert np.array_equal(cand["y"].astype(np.int64) * W + cand["x"], want)
     sh, tp = oracle.trajectory_table_frames(vx, vy, T, times=tau, jitter=jitter)
     lam = oracle.inverse_variance(c["sigma"], c["mask"])
-    N, D = oracle.search_points(c["res"], lam, sh, tp, cand["y"], cand["x"], cand["k"])
-    np.testing.assert_allclose(cand["snr"], N / np.sqrt(D), rtol=1e-9, atol=1e-12)
+    N, D = oracle.search_points(c["res"], lam, sh, tp, (want // W).astype(np.int32), (want % W).astype(np.int32),
+                                a_max.ravel()[want])
+    ok = D > 0
+    np.testing.assert_allclose(cand["snr"][ok], N[ok] / np.sqrt(D[ok]), rtol=1e-9, atol=1e-12)
 
 
 def test_frames_rejects_bad_models(mf):
