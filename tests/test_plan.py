@@ -108,3 +108,17 @@ def test_shift_stack_plans_single_tap_passes(mf):
     assert mf.prf_plan(vx, vy, 400, kind=1)["taps"] == 5
     with pytest.raises(mf.MFError):
         mf.prf_plan(vx, vy, 400, kind=3)
+
+
+def test_measured_workloads_keep_their_plans(mf):
+    # the layouts behind the measured numbers (1000 frames, |v| <= 0.1
+    # px/frame): a change of the cost model that moves them must be measured
+    vx, vy = _grid(10, 10)
+    info = mf.prf_plan(vx, vy, 1000)
+    got = {k: info[k] for k in ("kernel", "groups", "warps_per_group", "tile_h", "tile_w", "window_rows",
+                                "stages", "time_segments", "taps")}
+    assert got == {"kernel": 2, "groups": 20, "warps_per_group": 5, "tile_h": 96, "tile_w": 32,
+                   "window_rows": 130, "stages": 6, "time_segments": 3, "taps": 5}
+    vx, vy = _grid(40, 25)
+    info = mf.prf_plan(vx, vy, 1000)
+    assert (info["groups"], info["warps_per_group"], info["tile_h"], info["time_segments"]) == (80, 13, 32, 2)
