@@ -96,6 +96,31 @@ void orc_trajectory_table(int K, int T, const double *vx, const double *vy,
     }
 }
 
+/* The filter bank of a phase-quantised search (the precompute-then-gather
+ * form of a sparse matched filter: each frame is correlated once with the
+ * footprints of Q x Q sub-pixel phases, and every trajectory then gathers the
+ * image of its phase).  Its value is the plain matched filter with the
+ * footprint of frame t evaluated at the phase rounded to a multiple of 1/Q
+ * pixel, phi_q = floor(phi Q + 1/2) / Q per axis (halves round up, as for the
+ * base pixel); the base pixel is unchanged. */
+void orc_trajectory_table_quantised(int K, int T, const double *vx, const double *vy, double sigma, int kind,
+                                    int Q, int32_t *shifts, double *taps)
+{
+    for (int k = 0; k < K; k++) {
+        for (int t = 0; t < T; t++) {
+            double cx = vx[k] * (double)t;
+            double cy = vy[k] * (double)t;
+            double sx = floor(cx + 0.5);
+            double sy = floor(cy + 0.5);
+            double qx = floor((cx - sx) * Q + 0.5) / Q;
+            double qy = floor((cy - sy) * Q + 0.5) / Q;
+            shifts[((size_t)k * T + t) * 2 + 0] = (int32_t)sx;
+            shifts[((size_t)k * T + t) * 2 + 1] = (int32_t)sy;
+            orc_prf_taps(qx, qy, sigma, kind, taps + ((size_t)k * T + t) * 25);
+        }
+    }
+}
+
 /* The same table with the frames' times and the pointing jitter (Section
  * 2.1: the spacecraft's pointing jitters by a fraction of a pixel, and the
  * filter follows the trajectory line including that jitter; Fig. 3: frames

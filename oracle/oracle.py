@@ -13,6 +13,9 @@ Functions and the passages they follow:
   PRF).  Gaussian PRF of width ``sigma_prf``, 5x5 footprint, renormalised;
   kind 2 is the shift-stack filter (Section 3.2: a single 1 in the pixel
   holding the source's centre).
+* ``trajectory_table_quantised`` -- the filter bank of a phase-quantised
+  precompute-then-gather search (Section 3.2 expects a sparse formulation
+  to be much faster): footprints at phases rounded to multiples of 1/Q.
 * ``trajectory_table_frames`` -- the same with each frame's time (Fig. 3:
   the downlink gap makes time jump) and the pointing jitter (Section 2.1;
   Section 3.2: the filter follows the trajectory including the jitter).
@@ -49,7 +52,8 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = [
-    "build", "prf_taps", "trajectory_table", "trajectory_table_frames", "inverse_variance", "search_full",
+    "build", "prf_taps", "trajectory_table", "trajectory_table_frames", "trajectory_table_quantised",
+    "inverse_variance", "search_full",
     "search_points", "snr_and_best", "dense_template", "search_dense", "inject",
     "search_numpy", "topk_order", "threads",
 ]
@@ -78,6 +82,7 @@ def _load():
             lib.orc_pixel_integrated_gauss.restype = d
             lib.orc_trajectory_table.argtypes = [i, i, P, P, d, i, P, P]
             lib.orc_trajectory_table_frames.argtypes = [i, i, P, P, P, P, P, d, i, P, P]
+            lib.orc_trajectory_table_quantised.argtypes = [i, i, P, P, d, i, i, P, P]
             lib.orc_inverse_variance.argtypes = [i, i, P, P, P]
             lib.orc_search_full.argtypes = [i, i, i, P, P, P, i, P, P, P, P]
             lib.orc_search_points.argtypes = [i, i, i, P, P, P, P, P, ctypes.c_long,
@@ -139,6 +144,19 @@ def trajectory_table_frames(vx, vy, T: int, times=None, jitter=None, sigma: floa
     taps = np.zeros((K, T, 5, 5), np.float64)
     _load().orc_trajectory_table_frames(K, int(T), _ptr(vx), _ptr(vy), _ptr(tm), _ptr(jx), _ptr(jy),
                                         float(sigma), int(kind), _ptr(shifts), _ptr(taps))
+    return shifts, taps
+
+
+def trajectory_table_quantised(vx, vy, T: int, Q: int, sigma: float = 0.7, kind: int = 0):
+    """The filter bank of the phase-quantised search: as ``trajectory_table``
+    with each footprint's sub-pixel phase rounded to a multiple of 1/Q."""
+    vx = np.ascontiguousarray(vx, np.float64)
+    vy = np.ascontiguousarray(vy, np.float64)
+    K = vx.shape[0]
+    shifts = np.zeros((K, T, 2), np.int32)
+    taps = np.zeros((K, T, 5, 5), np.float64)
+    _load().orc_trajectory_table_quantised(K, int(T), _ptr(vx), _ptr(vy), float(sigma), int(kind), int(Q),
+                                           _ptr(shifts), _ptr(taps))
     return shifts, taps
 
 

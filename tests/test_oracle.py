@@ -534,3 +534,57 @@ def test_shift_stack_kind_is_single_tap_shift_and_add(oracle):
         inner = (slice(6, H - 6), slice(6, W - 6))
         np.testing.assert_allclose(N[k][inner], n[inner], rtol=1e-12, atol=1e-12)
         np.testing.assert_allclose(D[k][inner], d[inner], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------ phase-quantised (NEXT) --
+
+def test_quantised_table_hand_worked(oracle):
+    # v = 0.3, Q = 4: phases 0, 0.3, -0.4, -0.1, 0.2 round to 0, 0.25, -0.5,
+    # 0, 0.25 (halves up); base pixels as for the exact table
+    sh, tp = oracle.trajectory_table_quantised([0.3], [0.0], 5, 4)
+    assert list(sh[0, :, 0]) == [0, 0, 1, 1, 1]
+    for t, ph in enumerate([0.0, 0.25, -0.5, 0.0, 0.25]):
+        np.testing.assert_allclose(tp[0, t], oracle.prf_taps(ph, 0.0), atol=1e-15)
+
+
+def test_quantised_table_on_grid_and_converging(oracle):
+    # phases already on the 1/Q grid: the exact table; otherwise the taps
+    # approach the exact ones as 1/Q
+    s0, t0 = oracle.trajectory_table([0.25, -0.125], [0.5, 0.375], 16)
+    s1, t1 = oracle.trajectory_table_quantised([0.25, -0.125], [0.5, 0.375], 16, 8)
+    assert np.array_equal(s0, s1) and np.array_equal(t0, t1)
+    g = _rng(21)
+    vx, vy = g.uniform(-0.5, 0.5, 6), g.uniform(-0.5, 0.5, 6)
+    s0, t0 = oracle.trajectory_table(vx, vy, 40)
+    errs = []
+    for Q in (2, 4, 8, 16, 32):
+        sq, tq = oracle.trajectory_table_quantised(vx, vy, 40, Q)
+        assert np.array_equal(sq, s0)
+        errs.append(np.abs(tq - t0).max())
+        assert errs[-1] <= 0.5 / Q  # |dW/dphase| < 1 for the sigma = 0.7 footprint
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_quantised_filter_never_beats_exact_on_injection(oracle):
+    """A noiseless source injected with the exact filter: a mismatched
+    (quantised) template gives N_q / sqrt(D_q) <= f sqrt(D) (Cauchy-Schwarz),
+    and loses little at Q = 4."""
+    g = _rng(22)
+    T, H, W = 30, 24, 28
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    lam = oracle.inverse_variance(sigma)
+    vx, vy = np.array([0.23, -0.31]), np.array([0.17, 0.05])
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    py, px, f = 11, 13, 2.0
+    for k in range(2):
+        res = np.zeros((T, H, W))
+        oracle.inject(res, sh[k], tp[k], py, px, f)
+        N, D = oracle.search_points(res.astype(np.float32), lam, sh, tp, [py], [px], [k])
+        exact = N[0] / np.sqrt(D[0])
+        for Q in (2, 4, 8):
+            sq, tq = oracle.trajectory_table_quantised(vx, vy, T, Q)
+            Nq, Dq = oracle.search_points(res.astype(np.float32), lam, sq, tq, [py], [px], [k])
+            snr_q = Nq[0] / np.sqrt(Dq[0])
+            assert snr_q <= exact * (1 + 1e-6)
+            if Q >= 4:
+                assert snr_q >= 0.97 * exact
