@@ -245,6 +245,11 @@ mf_status mf_prf_table_info(const mf_prf_table *table, mf_table_info *info);
  * and needs no GPU.  device_bytes is what mf_prf_table_create would allocate. */
 mf_status mf_prf_plan(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
                       int32_t T, const mf_plan_opts *opts, mf_table_info *info);
+/* mf_prf_plan for a filter bank with a frame model (mf_prf_table_create_frames):
+ * the same layout, host only, no device needed.  frames may be NULL. */
+mf_status mf_prf_plan_frames(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
+                             int32_t T, const mf_frames *frames, const mf_plan_opts *opts,
+                             mf_table_info *info);
 
 /* Bytes of workspace mf_search needs for this stack shape and table. */
 mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *table,

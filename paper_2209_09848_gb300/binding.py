@@ -140,6 +140,8 @@ def load():
             "mf_prf_table_info": ([P, ctypes.POINTER(TableInfo)], ctypes.c_int),
             "mf_prf_plan": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(PlanOpts),
                              ctypes.POINTER(TableInfo)], ctypes.c_int),
+            "mf_prf_plan_frames": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(Frames),
+                                    ctypes.POINTER(PlanOpts), ctypes.POINTER(TableInfo)], ctypes.c_int),
             "mf_search_workspace_size": ([ctypes.POINTER(Stack), P, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_search": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P, SZ, P], ctypes.c_int),
             "mf_search_noalloc": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P], ctypes.c_int),
@@ -276,8 +278,9 @@ def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, *
     return PrfTable(h)
 
 
-def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> dict:
-    """mf_prf_plan: host-only layout of a Gaussian-PRF filter bank (no GPU needed)."""
+def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, **layout) -> dict:
+    """mf_prf_plan (mf_prf_plan_frames with times / jitter): host-only layout
+    of a Gaussian-PRF filter bank (no GPU needed)."""
     import numpy as np
     bad = set(layout) - set(_LAYOUT_KEYS)
     if bad:
@@ -286,9 +289,22 @@ def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, **layout) -> dict:
     vy = np.ascontiguousarray(vy, np.float64)
     prm = PrfParams(int(kind), 0, float(sigma_px))
     inf = TableInfo()
-    _check(load().mf_prf_plan(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                              vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T), _opts(**layout),
-                              ctypes.byref(inf)))
+    if times is not None or jitter is not None:
+        tm = None if times is None else np.ascontiguousarray(times, np.float64)
+        jt = None if jitter is None else np.ascontiguousarray(jitter, np.float64)
+        if tm is not None and tm.shape != (int(T),):
+            raise ValueError("times must have shape (T,)")
+        if jt is not None and jt.shape != (int(T), 2):
+            raise ValueError("jitter must have shape (T, 2)")
+        fr = Frames(None if tm is None else tm.ctypes.data_as(ctypes.c_void_p),
+                    None if jt is None else jt.ctypes.data_as(ctypes.c_void_p))
+        _check(load().mf_prf_plan_frames(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                                         vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+                                         ctypes.byref(fr), _opts(**layout), ctypes.byref(inf)))
+    else:
+        _check(load().mf_prf_plan(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
+                                  vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T), _opts(**layout),
+                                  ctypes.byref(inf)))
     return inf.as_dict()
 
 

@@ -1094,9 +1094,14 @@ mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const 
 
 mf_status mf_prf_plan(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K, int32_t T,
                       const mf_plan_opts *opts, mf_table_info *info) {
+    return mf_prf_plan_frames(prf, vx, vy, K, T, nullptr, opts, info);
+}
+
+mf_status mf_prf_plan_frames(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K, int32_t T,
+                             const mf_frames *frames, const mf_plan_opts *opts, mf_table_info *info) {
     if (!info) return fail(MF_EINVAL, "info is NULL");
     mf_prf_table *t = nullptr;
-    mf_status s = build_gauss_host(prf, vx, vy, K, T, &t);
+    mf_status s = build_gauss_host(prf, vx, vy, K, T, &t, frames);
     if (s != MF_OK) return s;
     if ((s = apply_opts(t, opts)) != MF_OK) return s;
     HostLayouts h;

@@ -122,3 +122,23 @@ def test_measured_workloads_keep_their_plans(mf):
     vx, vy = _grid(40, 25)
     info = mf.prf_plan(vx, vy, 1000)
     assert (info["groups"], info["warps_per_group"], info["tile_h"], info["time_segments"]) == (80, 13, 32, 2)
+
+
+def test_plan_with_frame_model(mf):
+    # a frame model moves the base pixels, so the window rows and segments
+    # follow it; the identity model is the linear plan
+    vx, vy = _grid(10, 10)
+    T = 400
+    base = mf.prf_plan(vx, vy, T)
+    same = mf.prf_plan(vx, vy, T, times=np.arange(T, dtype=float), jitter=np.zeros((T, 2)))
+    assert same == base
+    g = np.random.default_rng(3)
+    jit = g.uniform(-1.5, 1.5, size=(T, 2))
+    tau = np.arange(T, dtype=float) + np.where(np.arange(T) >= T // 2, 300.0, 0.0)
+    info = mf.prf_plan(vx, vy, T, times=tau, jitter=jit)
+    assert info["kernel"] == 2 and info["taps"] == 5
+    assert info["max_abs_shift"] > base["max_abs_shift"]  # 700 cadences of motion instead of 400
+    with pytest.raises(mf.MFError):
+        mf.prf_plan(vx, vy, T, jitter=np.full((T, 2), np.nan))
+    with pytest.raises(ValueError):
+        mf.prf_plan(vx, vy, T, times=np.zeros(T + 1))
