@@ -15,7 +15,9 @@ Functions and the passages they follow:
   holding the source's centre).
 * ``trajectory_table_quantised`` -- the filter bank of a phase-quantised
   precompute-then-gather search (Section 3.2 expects a sparse formulation
-  to be much faster): footprints at phases rounded to multiples of 1/Q.
+  to be much faster): footprints at phases rounded to multiples of 1/Q;
+  ``search_quantised_gather`` computes that search in its own order (each
+  frame correlated once per rounded phase, then one gather per trajectory).
 * ``trajectory_table_frames`` -- the same with each frame's time (Fig. 3:
   the downlink gap makes time jump) and the pointing jitter (Section 2.1;
   Section 3.2: the filter follows the trajectory including the jitter).
@@ -55,7 +57,7 @@ __all__ = [
     "build", "prf_taps", "trajectory_table", "trajectory_table_frames", "trajectory_table_quantised",
     "inverse_variance", "search_full",
     "search_points", "snr_and_best", "dense_template", "search_dense", "inject",
-    "search_numpy", "topk_order", "threads",
+    "search_numpy", "search_quantised_gather", "topk_order", "threads",
 ]
 
 
@@ -305,6 +307,63 @@ def search_numpy(res, lam, shifts, taps, frame_scale=None):
                     N[k] += w * _shifted(yt, sy + dy, sx + dx)
                     D[k] += w * w * _shifted(lam, sy + dy, sx + dx)
     return N, D
+
+
+def search_quantised_gather(res, lam, vx, vy, Q: int, sigma: float = 0.7, kind: int = 0, frame_scale=None):
+    """The phase-quantised search in its own order, precompute then gather:
+    frame t is correlated once with the footprint of every rounded phase
+    n / Q (n = floor(phi Q + 1/2) per axis) that some trajectory takes in
+    that frame, over the frame plus a 2-pixel halo (the footprint still
+    overlaps the frame there), for the numerator (lambda r) and the
+    denominator (lambda, with squared taps); every trajectory then adds the
+    plane of its phase at its start pixel plus its base shift.  Returns
+    N, D [K, H, W]; the same sums as ``search_full`` on
+    ``trajectory_table_quantised``, in another order."""
+    res = np.asarray(res, np.float64)
+    if frame_scale is not None:
+        res = res * np.asarray(frame_scale, np.float64)[:, None, None]
+    T, H, W = res.shape
+    lam = np.asarray(lam, np.float64)
+    vx = np.asarray(vx, np.float64)
+    vy = np.asarray(vy, np.float64)
+    K = vx.shape[0]
+    N = np.zeros((K, H, W))
+    D = np.zeros((K, H, W))
+    lam_p = np.pad(lam, 4)
+    for t in range(T):
+        y_p = np.pad(res[t] * lam, 4)
+        planes = {}
+        for k in range(K):
+            cx, cy = vx[k] * t, vy[k] * t
+            sx, sy = np.floor(cx + 0.5), np.floor(cy + 0.5)
+            n = (np.floor((cx - sx) * Q + 0.5), np.floor((cy - sy) * Q + 0.5))
+            if n not in planes:
+                w = prf_taps(n[0] / Q, n[1] / Q, sigma, kind)
+                # plane index i holds position i - 2: rows -2 .. H + 1
+                C = np.zeros((H + 4, W + 4))
+                E = np.zeros((H + 4, W + 4))
+                for b in range(-2, 3):
+                    for a in range(-2, 3):
+                        wab = w[b + 2, a + 2]
+                        C += wab * y_p[2 + b:2 + b + H + 4, 2 + a:2 + a + W + 4]
+                        E += wab * wab * lam_p[2 + b:2 + b + H + 4, 2 + a:2 + a + W + 4]
+                planes[n] = (C, E)
+            C, E = planes[n]
+            N[k] += _window(C, int(sy) + 2, int(sx) + 2, H, W)
+            D[k] += _window(E, int(sy) + 2, int(sx) + 2, H, W)
+    return N, D
+
+
+def _window(plane, oy, ox, H, W):
+    """out[y, x] = plane[y + oy, x + ox] for an H x W output, zero where that
+    falls outside the plane."""
+    out = np.zeros((H, W))
+    Hp, Wp = plane.shape
+    y0, y1 = max(0, -oy), min(H, Hp - oy)
+    x0, x1 = max(0, -ox), min(W, Wp - ox)
+    if y0 < y1 and x0 < x1:
+        out[y0:y1, x0:x1] = plane[y0 + oy:y1 + oy, x0 + ox:x1 + ox]
+    return out
 
 
 def inject(res, shifts_k, taps_k, py, px, flux):

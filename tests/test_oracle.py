@@ -588,3 +588,40 @@ def test_quantised_filter_never_beats_exact_on_injection(oracle):
             assert snr_q <= exact * (1 + 1e-6)
             if Q >= 4:
                 assert snr_q >= 0.97 * exact
+
+
+@pytest.mark.parametrize("T,H,W,Q,vmax,masked", [
+    (7, 13, 17, 4, 0.4, False),
+    (9, 11, 9, 3, 1.6, True),     # odd Q; shifts that carry start pixels out of the frame
+    (5, 6, 21, 8, 0.9, True),
+])
+def test_quantised_gather_equals_quantised_bank(oracle, T, H, W, Q, vmax, masked):
+    # precompute-then-gather (planes per rounded phase, one gather per
+    # trajectory) against the plain loops on the quantised filter bank
+    g = _rng(T * 31 + W)
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.1).astype(np.uint8) if masked else None
+    lam = oracle.inverse_variance(sigma, mask)
+    vx, vy = g.uniform(-vmax, vmax, 6), g.uniform(-vmax, vmax, 6)
+    vx[0], vy[0] = 0.0, 0.0
+    sh, tp = oracle.trajectory_table_quantised(vx, vy, T, Q)
+    N0, D0 = oracle.search_full(res, lam, sh, tp)
+    N1, D1 = oracle.search_quantised_gather(res, lam, vx, vy, Q)
+    np.testing.assert_allclose(N1, N0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D1, D0, rtol=1e-12, atol=1e-12)
+    assert (D0 > 0).any()
+
+
+def test_quantised_gather_on_grid_is_exact_search(oracle):
+    # velocities whose phases all lie on the 1/Q grid: the exact search
+    g = _rng(23)
+    T, H, W = 12, 10, 14
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    lam = oracle.inverse_variance(np.ones((H, W), np.float32))
+    vx, vy = np.array([0.25, -0.5, 0.125]), np.array([0.375, 0.0, -0.25])
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    N0, D0 = oracle.search_numpy(res, lam, sh, tp)
+    N1, D1 = oracle.search_quantised_gather(res, lam, vx, vy, 8)
+    np.testing.assert_allclose(N1, N0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D1, D0, rtol=1e-12, atol=1e-12)
