@@ -428,7 +428,11 @@ def run_ours(args):
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s)" % (
                              float(peaks.get("sm_max_mhz", 2070.0)), peak_src),
-                         "flop_per_unit": fpu, "numerator_ms_per_step": num_ms,
+                         "flop_per_unit": fpu,
+                         # the same launches counted at the general 5 x 5 form's
+                         # 50 flop per unit: a rate of the search, not of the FP32 pipe
+                         "general_form_equivalent_tflops": units_rank * FLOP_PER_UNIT_GENERAL / (num_ms * 1e-3) / 1e12,
+                         "numerator_ms_per_step": num_ms,
                          "numerator_launches_per_step": num_launches // args.steps},
             "kernel_ms_per_step": kernel_ms,
             "cpu_baseline": cpu,
