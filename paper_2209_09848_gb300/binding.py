@@ -199,6 +199,27 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _device_arg(name, t, device=None, dtype=None, shape=None, contiguous=True, optional=True):
+    """Check a tensor the library takes as a device pointer: a CUDA tensor
+    (on `device` when given) of `dtype` and `shape`, contiguous.  The library
+    cannot tell a host pointer from a device one, so this is where such a
+    mistake becomes a ValueError instead of a kernel reading host memory."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError("%s is required" % name)
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if device is not None and t.device != device:
+        raise ValueError("%s must be on %s, not %s" % (name, device, t.device))
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s, not %s" % (name, dtype, t.dtype))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, not %s" % (name, tuple(shape), tuple(t.shape)))
+    if contiguous and not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
 class PrfTable:
     """Filter bank handle (mf_prf_table)."""
 
@@ -351,6 +372,26 @@ def _workspace(nbytes, device, workspace):
     return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
 
 
+def _check_search_inputs(stack, sigma, mask, frame_scale, device=None):
+    """The device arguments of a search: stack [T, H, W] (rows contiguous,
+    any frame and row stride), sigma float32 and mask uint8 [H, W] and
+    frame_scale float32 [T] on the stack's device (`device` for a host
+    stack)."""
+    T, H, W = stack.shape
+    if device is None:
+        _device_arg("stack", stack, contiguous=False)
+        device = stack.device
+    _device_arg("sigma", sigma, device, torch.float32, (H, W), optional=False)
+    _device_arg("mask", mask, device, torch.uint8, (H, W))
+    _device_arg("frame_scale", frame_scale, device, torch.float32, (T,))
+
+
+def _check_search_outputs(snr_max, argmax, snr_all, table, H, W, device):
+    _device_arg("snr_max", snr_max, device, torch.float32, (H, W), optional=False)
+    _device_arg("argmax", argmax, device, torch.int32, (H, W), optional=False)
+    _device_arg("snr_all", snr_all, device, torch.float32, (table.K, H, W))
+
+
 def search(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torch.Tensor | None = None,
            frame_scale: torch.Tensor | None = None, want_all: bool = False, workspace=None, out=None,
            stream=None):
@@ -358,19 +399,15 @@ def search(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torc
     st = make_stack(stack, frame_scale)
     T, H, W = stack.shape
     dev = stack.device
-    for name, t in (("sigma", sigma), ("mask", mask)):
-        if t is not None and (t.device != dev or not t.is_contiguous() or t.shape != (H, W)):
-            raise ValueError("%s must be a contiguous [H, W] tensor on the stack's device" % name)
-    if sigma.dtype != torch.float32:
-        raise ValueError("sigma must be float32")
-    if mask is not None and mask.dtype != torch.uint8:
-        raise ValueError("mask must be uint8")
+    _check_search_inputs(stack, sigma, mask, frame_scale)
     if out is None:
         snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
         argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
         snr_all = torch.empty((table.K, H, W), dtype=torch.float32, device=dev) if want_all else None
     else:
         snr_max, argmax, snr_all = out
+        _check_search_outputs(snr_max, argmax, snr_all, table, H, W, dev)
+    _device_arg("workspace", workspace, dev)
     nbytes = search_workspace_size((T, H, W), table)
     ws = _workspace(nbytes, dev, workspace)
     _check(load().mf_search(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
@@ -385,12 +422,14 @@ def search_noalloc(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, ma
     st = make_stack(stack, frame_scale)
     T, H, W = stack.shape
     dev = stack.device
+    _check_search_inputs(stack, sigma, mask, frame_scale)
     if out is None:
         snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
         argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
         snr_all = torch.empty((table.K, H, W), dtype=torch.float32, device=dev) if want_all else None
     else:
         snr_max, argmax, snr_all = out
+        _check_search_outputs(snr_max, argmax, snr_all, table, H, W, dev)
     _check(load().mf_search_noalloc(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
                                     _ptr(argmax), _ptr(snr_all), _stream_ptr(stream)))
     return snr_max, argmax, snr_all
@@ -418,7 +457,10 @@ def search_host(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask:
         raise ValueError("search_host takes a CPU stack; use search for device stacks")
     st = make_stack(stack, frame_scale)
     T, H, W = stack.shape
+    _device_arg("sigma", sigma, optional=False)
     dev = sigma.device
+    _check_search_inputs(stack, sigma, mask, frame_scale, device=dev)
+    _device_arg("workspace", workspace, dev)
     if out is None:
         pin = stack.is_pinned()
         smax = torch.empty((H, W), dtype=torch.float32, pin_memory=pin)
@@ -452,6 +494,10 @@ def rescore_topk(master: torch.Tensor, sigma: torch.Tensor, table: PrfTable, snr
     st = make_stack(master, frame_scale)
     T, H, W = master.shape
     dev = master.device
+    _check_search_inputs(master, sigma, mask, frame_scale)
+    _device_arg("snr_max", snr_max, dev, torch.float32, (H, W), optional=False)
+    _device_arg("argmax", argmax, dev, torch.int32, (H, W), optional=False)
+    _device_arg("workspace", workspace, dev)
     out = torch.zeros((k_top, CANDIDATE_BYTES), dtype=torch.uint8, device=dev)
     n_out = torch.zeros(1, dtype=torch.int32, device=dev)
     nbytes = rescore_workspace_size(H, W, k_top)
@@ -485,8 +531,16 @@ def background_refit(data: torch.Tensor, jitter, delta: float, iterations: int =
     Returns (residual [T, H, W], coefficients [H, W, 6] or None); pass
     resid=data to work in place."""
     import numpy as np
+    if data.dim() != 3:
+        raise ValueError("data must be [T, H, W]")
     T, H, W = data.shape
+    _device_arg("data", data, dtype=torch.float32, optional=False)
     dev = data.device
+    if scatter is not None:
+        n_s = scatter.shape[-1] if scatter.dim() == 3 else 0
+        _device_arg("scatter", scatter, dev, torch.float32, (T, n_s, n_s))
+    _device_arg("resid", resid, dev, torch.float32, (T, H, W))
+    _device_arg("workspace", workspace, dev)
     jt = np.ascontiguousarray(jitter, np.float64)
     if jt.shape != (T, 2):
         raise ValueError("jitter must have shape (T, 2)")
@@ -513,8 +567,14 @@ def detect(snr_max: torch.Tensor, argmax: torch.Tensor, window: int = 255, thres
            stream=None):
     """mf_detect: returns (detections as a uint8 tensor of max_out records,
     n_out int32 [2] = (found, written)), both on the device."""
+    if snr_max.dim() != 2:
+        raise ValueError("snr_max must be [H, W]")
     H, W = snr_max.shape
+    _device_arg("snr_max", snr_max, dtype=torch.float32, optional=False)
     dev = snr_max.device
+    _device_arg("argmax", argmax, dev, torch.int32, (H, W), optional=False)
+    _device_arg("z_out", z_out, dev, torch.float32, (H, W))
+    _device_arg("workspace", workspace, dev)
     out = torch.zeros((max(max_out, 1), DETECTION_BYTES), dtype=torch.uint8, device=dev)
     n_out = torch.zeros(2, dtype=torch.int32, device=dev)
     ws = _workspace(detect_workspace_size(H, W, max_out), dev, workspace)
@@ -563,6 +623,7 @@ class Batch:
         st = make_stack(stack, frame_scale)
         T, H, W = stack.shape
         dev = stack.device
+        _check_search_inputs(stack, sigma, mask, frame_scale)
         snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
         argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
         snr_all = torch.empty((table.K, H, W), dtype=torch.float32, device=dev) if want_all else None
@@ -580,6 +641,7 @@ class Batch:
 
     def prepare(self, workspace=None, device="cuda"):
         n = self.workspace_size()
+        _device_arg("workspace", workspace)
         self._ws = workspace if workspace is not None else torch.empty(max(n, 1), dtype=torch.uint8, device=device)
         _check(load().mf_batch_prepare(self._h, _ptr(self._ws), self._ws.numel() * self._ws.element_size()))
 
