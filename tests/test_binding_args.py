@@ -126,3 +126,44 @@ def test_search_argument_rules_before_the_library():
     with pytest.raises(ValueError, match=r"snr_all must have shape \(3, 8, 10\)"):
         out(s, _cuda_like(torch.zeros((H, W), dtype=torch.int32)), _cuda_like(torch.zeros((2, H, W))), _Bank(), H,
             W, torch.device("cuda", 0))
+
+
+class _StubLib:
+    """Records the library calls a binding function makes (returns MF_OK)."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def call(*args):
+            self.calls.append(name)
+            return 0
+        return call
+
+
+class _Stream:
+    cuda_stream = 0
+
+
+def test_valid_calls_reach_the_library(monkeypatch):
+    # arguments shaped like the bench's and the tests' GPU calls pass every
+    # check and reach the library (stubbed: nothing runs)
+    stub = _StubLib()
+    monkeypatch.setattr(mf.binding, "load", lambda: stub)
+    r = _cuda_like(torch.zeros((T, H, W)))
+    s = _cuda_like(torch.ones((H, W)))
+    m = _cuda_like(torch.zeros((H, W), dtype=torch.uint8))
+    fs = _cuda_like(torch.ones(T))
+    ws = _cuda_like(torch.zeros(64, dtype=torch.uint8))
+    out = (_cuda_like(torch.zeros((H, W))), _cuda_like(torch.zeros((H, W), dtype=torch.int32)), None)
+    mf.search(r, s, _Bank(), mask=m, frame_scale=fs, workspace=ws, out=out, stream=_Stream())
+    # a strided stack (rows contiguous) is accepted as the ABI allows
+    big = _cuda_like(torch.zeros((T, H + 2, W + 3)))[:, 1:H + 1, 1:W + 1]
+    mf.search(big, s, _Bank(), workspace=ws, out=out, stream=_Stream())
+    mf.search_noalloc(r, s, _Bank(), mask=m, out=out, stream=_Stream())
+    D = _cuda_like(torch.zeros((8, H, W)))
+    S = _cuda_like(torch.zeros((8, 4, 4)))
+    jit = np.random.default_rng(0).uniform(-0.1, 0.1, (8, 2))
+    mf.background_refit(D, jit, 1.0, 2, scatter=S, resid=D, want_coef=False, workspace=ws, stream=_Stream())
+    assert stub.calls == ["mf_search_workspace_size", "mf_search", "mf_search_workspace_size", "mf_search",
+                          "mf_search_noalloc", "mf_refit_workspace_size", "mf_background_refit"]
