@@ -71,10 +71,17 @@ typedef enum {
  *   kind 1: Gaussian sampled at pixel centres;
  *   kind 2: the shift-stack filter (Section 3.2, after Rice et al. 2020): a
  *           single 1 in the base pixel, the pixel holding the source's
- *           centre; sigma_px must still be a finite value > 0 (unused). */
+ *           centre; sigma_px must still be a finite value > 0 (unused).
+ * phase_steps: 0 evaluates the footprint at the exact sub-pixel phase;
+ * Q in 1 .. 4096 rounds each axis's phase to the nearest multiple of 1/Q
+ * (halves up, as for the base pixel; the base pixel is unchanged).  Not in
+ * the paper: the filter bank of a phase-quantised search, in which every
+ * frame would be correlated once per rounded phase and each trajectory
+ * would gather the result of its own (one route to the faster sparse
+ * evaluation Section 3.2 anticipates); the search runs it exactly. */
 typedef struct {
     int32_t kind;
-    int32_t reserved;
+    int32_t phase_steps;
     double sigma_px;
 } mf_prf_params;
 
@@ -116,7 +123,8 @@ typedef struct mf_prf_table mf_prf_table;
  * c - s; footprint = the PRF at that phase.  Allocates device memory for the
  * table (the only allocation the library makes) on the current device.
  * Errors: MF_EINVAL (K < 1, T < 1, NULL pointers, non-finite velocity,
- * sigma_px <= 0, unknown kind, |v| * T beyond 2^20 pixels), MF_ENOMEM. */
+ * sigma_px <= 0, unknown kind, phase_steps outside 0 .. 4096, |v| * T beyond
+ * 2^20 pixels), MF_ENOMEM. */
 mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const double *vy,
                               int32_t K, int32_t T, mf_prf_table **out);
 
@@ -250,6 +258,15 @@ mf_status mf_prf_plan(const mf_prf_params *prf, const double *vx, const double *
 mf_status mf_prf_plan_frames(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K,
                              int32_t T, const mf_frames *frames, const mf_plan_opts *opts,
                              mf_table_info *info);
+
+/* The filter bank itself, built on the host only (no device needed): the
+ * base shifts and FP64 footprints that mf_prf_table_create_frames would
+ * build, in mf_prf_table_export's layout (Section 3.2: the trajectory line
+ * convolved with the PRF).  frames may be NULL (the linear table).  shifts:
+ * host int32[K][T][2] or NULL; taps: host double[K][T][25] or NULL.  Errors
+ * as mf_prf_table_create_frames. */
+mf_status mf_prf_bank(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K, int32_t T,
+                      const mf_frames *frames, int32_t *shifts, double *taps);
 
 /* Bytes of workspace mf_search needs for this stack shape and table. */
 mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *table,

@@ -27,7 +27,7 @@ class MFError(RuntimeError):
 
 
 class PrfParams(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sigma_px", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int32), ("phase_steps", ctypes.c_int32), ("sigma_px", ctypes.c_double)]
 
 
 class Stack(ctypes.Structure):
@@ -142,6 +142,8 @@ def load():
                              ctypes.POINTER(TableInfo)], ctypes.c_int),
             "mf_prf_plan_frames": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(Frames),
                                     ctypes.POINTER(PlanOpts), ctypes.POINTER(TableInfo)], ctypes.c_int),
+            "mf_prf_bank": ([ctypes.POINTER(PrfParams), P, P, I32, I32, ctypes.POINTER(Frames), P, P],
+                            ctypes.c_int),
             "mf_search_workspace_size": ([ctypes.POINTER(Stack), P, ctypes.POINTER(SZ)], ctypes.c_int),
             "mf_search": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P, SZ, P], ctypes.c_int),
             "mf_search_noalloc": ([ctypes.POINTER(Stack), P, P, P, P, P, P, P], ctypes.c_int),
@@ -258,75 +260,87 @@ class PrfTable:
             pass
 
 
-def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, **layout) -> PrfTable:
+def _bank_args(vx, vy, T, sigma_px, kind, phase_steps, times, jitter):
+    """Marshal a velocity filter bank's arguments: (PrfParams, vx, vy, Frames
+    or None, arrays to keep alive during the call)."""
+    import numpy as np
+    vx = np.ascontiguousarray(vx, np.float64)
+    vy = np.ascontiguousarray(vy, np.float64)
+    if vx.shape != vy.shape or vx.ndim != 1:
+        raise ValueError("vx and vy must be 1-D of equal length")
+    prm = PrfParams(int(kind), int(phase_steps), float(sigma_px))
+    if times is None and jitter is None:
+        return prm, vx, vy, None, ()
+    tm = None if times is None else np.ascontiguousarray(times, np.float64)
+    jt = None if jitter is None else np.ascontiguousarray(jitter, np.float64)
+    if tm is not None and tm.shape != (int(T),):
+        raise ValueError("times must have shape (T,)")
+    if jt is not None and jt.shape != (int(T), 2):
+        raise ValueError("jitter must have shape (T, 2)")
+    fr = Frames(None if tm is None else tm.ctypes.data_as(ctypes.c_void_p),
+                None if jt is None else jt.ctypes.data_as(ctypes.c_void_p))
+    return prm, vx, vy, fr, (tm, jt)
+
+
+def _vptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def prf_table_create(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, phase_steps=0,
+                     **layout) -> PrfTable:
     """mf_prf_table_create, or mf_prf_table_create_ex when layout options are
     given: shape, vec, lockstep (general numerator), kernel (1 general,
     2 factored), group, tile_h, tile_w, stages, segments (factored
     numerator); None or absent = automatic.  times ([T] frame times in
     cadences) and jitter ([T, 2] (x, y) pointing offsets in pixels) select
-    mf_prf_table_create_frames."""
-    import numpy as np
+    mf_prf_table_create_frames.  phase_steps = Q > 0 builds the
+    phase-quantised bank (phases rounded to multiples of 1/Q)."""
     bad = set(layout) - set(_LAYOUT_KEYS)
     if bad:
         raise TypeError("unknown layout option(s) %s" % sorted(bad))
-    vx = np.ascontiguousarray(vx, np.float64)
-    vy = np.ascontiguousarray(vy, np.float64)
-    if vx.shape != vy.shape or vx.ndim != 1:
-        raise ValueError("vx and vy must be 1-D of equal length")
-    prm = PrfParams(int(kind), 0, float(sigma_px))
+    prm, vx, vy, fr, _keep = _bank_args(vx, vy, T, sigma_px, kind, phase_steps, times, jitter)
     h = ctypes.c_void_p()
     opts = _opts(**layout)
-    if times is not None or jitter is not None:
-        tm = None if times is None else np.ascontiguousarray(times, np.float64)
-        jt = None if jitter is None else np.ascontiguousarray(jitter, np.float64)
-        if tm is not None and tm.shape != (int(T),):
-            raise ValueError("times must have shape (T,)")
-        if jt is not None and jt.shape != (int(T), 2):
-            raise ValueError("jitter must have shape (T, 2)")
-        fr = Frames(None if tm is None else tm.ctypes.data_as(ctypes.c_void_p),
-                    None if jt is None else jt.ctypes.data_as(ctypes.c_void_p))
-        _check(load().mf_prf_table_create_frames(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                                                 vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+    if fr is not None:
+        _check(load().mf_prf_table_create_frames(ctypes.byref(prm), _vptr(vx), _vptr(vy), vx.shape[0], int(T),
                                                  ctypes.byref(fr), opts, ctypes.byref(h)))
     elif opts is None:
-        _check(load().mf_prf_table_create(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                                          vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+        _check(load().mf_prf_table_create(ctypes.byref(prm), _vptr(vx), _vptr(vy), vx.shape[0], int(T),
                                           ctypes.byref(h)))
     else:
-        _check(load().mf_prf_table_create_ex(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                                             vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+        _check(load().mf_prf_table_create_ex(ctypes.byref(prm), _vptr(vx), _vptr(vy), vx.shape[0], int(T),
                                              opts, ctypes.byref(h)))
     return PrfTable(h)
 
 
-def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, **layout) -> dict:
+def prf_plan(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, phase_steps=0, **layout) -> dict:
     """mf_prf_plan (mf_prf_plan_frames with times / jitter): host-only layout
     of a Gaussian-PRF filter bank (no GPU needed)."""
-    import numpy as np
     bad = set(layout) - set(_LAYOUT_KEYS)
     if bad:
         raise TypeError("unknown layout option(s) %s" % sorted(bad))
-    vx = np.ascontiguousarray(vx, np.float64)
-    vy = np.ascontiguousarray(vy, np.float64)
-    prm = PrfParams(int(kind), 0, float(sigma_px))
+    prm, vx, vy, fr, _keep = _bank_args(vx, vy, T, sigma_px, kind, phase_steps, times, jitter)
     inf = TableInfo()
-    if times is not None or jitter is not None:
-        tm = None if times is None else np.ascontiguousarray(times, np.float64)
-        jt = None if jitter is None else np.ascontiguousarray(jitter, np.float64)
-        if tm is not None and tm.shape != (int(T),):
-            raise ValueError("times must have shape (T,)")
-        if jt is not None and jt.shape != (int(T), 2):
-            raise ValueError("jitter must have shape (T, 2)")
-        fr = Frames(None if tm is None else tm.ctypes.data_as(ctypes.c_void_p),
-                    None if jt is None else jt.ctypes.data_as(ctypes.c_void_p))
-        _check(load().mf_prf_plan_frames(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                                         vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T),
+    if fr is not None:
+        _check(load().mf_prf_plan_frames(ctypes.byref(prm), _vptr(vx), _vptr(vy), vx.shape[0], int(T),
                                          ctypes.byref(fr), _opts(**layout), ctypes.byref(inf)))
     else:
-        _check(load().mf_prf_plan(ctypes.byref(prm), vx.ctypes.data_as(ctypes.c_void_p),
-                                  vy.ctypes.data_as(ctypes.c_void_p), vx.shape[0], int(T), _opts(**layout),
+        _check(load().mf_prf_plan(ctypes.byref(prm), _vptr(vx), _vptr(vy), vx.shape[0], int(T), _opts(**layout),
                                   ctypes.byref(inf)))
     return inf.as_dict()
+
+
+def prf_bank(vx, vy, T, sigma_px=0.7, kind=0, times=None, jitter=None, phase_steps=0):
+    """mf_prf_bank: the filter bank's base shifts int32 [K, T, 2] and FP64
+    footprints [K, T, 5, 5], built on the host (no GPU needed)."""
+    import numpy as np
+    prm, vx, vy, fr, _keep = _bank_args(vx, vy, T, sigma_px, kind, phase_steps, times, jitter)
+    K = vx.shape[0]
+    shifts = np.zeros((K, int(T), 2), np.int32)
+    taps = np.zeros((K, int(T), 5, 5), np.float64)
+    _check(load().mf_prf_bank(ctypes.byref(prm), _vptr(vx), _vptr(vy), K, int(T),
+                              None if fr is None else ctypes.byref(fr), _vptr(shifts), _vptr(taps)))
+    return shifts, taps
 
 
 def prf_table_create_custom(shifts, taps) -> PrfTable:

@@ -965,6 +965,9 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
     if (prf->kind < 0 || prf->kind > 2) return fail(MF_EINVAL, "unknown PRF kind %d", prf->kind);
     if (!(prf->sigma_px > 0.0) || !std::isfinite(prf->sigma_px))
         return fail(MF_EINVAL, "sigma_px must be finite and > 0");
+    if (prf->phase_steps < 0 || prf->phase_steps > 4096)
+        return fail(MF_EINVAL, "phase_steps=%d out of range 0..4096", prf->phase_steps);
+    const double Q = (double)prf->phase_steps;
     const double *times = frames ? frames->times : nullptr;
     const double *jitter = frames ? frames->jitter : nullptr;
     // the frame model: time and (x, y) pointing offset of frame f
@@ -1003,7 +1006,9 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
         for (const auto &d : distinct)
             for (int f = 0; f < T; f++) {
                 const double c = d.first * tau(f) + jit(f, axis);
-                axis_profile(prf->kind, prf->sigma_px, c - std::floor(c + 0.5), &prof[((size_t)d.second * T + f) * 5]);
+                double ph = c - std::floor(c + 0.5);
+                if (Q > 0.0) ph = std::floor(ph * Q + 0.5) / Q;  // the phase-quantised bank
+                axis_profile(prf->kind, prf->sigma_px, ph, &prof[((size_t)d.second * T + f) * 5]);
             }
     };
     std::vector<int> ix, iy;
@@ -1112,6 +1117,17 @@ mf_status mf_prf_plan_frames(const mf_prf_params *prf, const double *vx, const d
     }
     delete t;
     return s == MF_OK ? ok() : s;
+}
+
+mf_status mf_prf_bank(const mf_prf_params *prf, const double *vx, const double *vy, int32_t K, int32_t T,
+                      const mf_frames *frames, int32_t *shifts, double *taps) {
+    mf_prf_table *t = nullptr;
+    const mf_status s = build_gauss_host(prf, vx, vy, K, T, &t, frames);
+    if (s != MF_OK) return s;
+    if (shifts) std::memcpy(shifts, t->shifts.data(), t->shifts.size() * sizeof(int32_t));
+    if (taps) std::memcpy(taps, t->taps.data(), t->taps.size() * sizeof(double));
+    delete t;
+    return ok();
 }
 
 mf_status mf_prf_table_info(const mf_prf_table *table, mf_table_info *info) {
