@@ -33,7 +33,8 @@ class Request:
     float32 / bfloat16 / float16, sigma [H, W] float32, mask [H, W] uint8 or
     None, frame_scale [T] float32 or None; velocities vx, vy (px/frame);
     optionally the frames' times [T] and pointing jitter [T, 2] (the filter
-    bank then follows them) and the PRF kind (2: shift-stack filter)."""
+    bank then follows them), the PRF kind (2: shift-stack filter) and
+    phase_steps (Q > 0: the phase-quantised bank)."""
     stack: torch.Tensor
     sigma: torch.Tensor
     vx: np.ndarray
@@ -46,6 +47,7 @@ class Request:
     times: np.ndarray | None = None
     jitter: np.ndarray | None = None
     kind: int = 0
+    phase_steps: int = 0
 
 
 @dataclasses.dataclass
@@ -137,7 +139,7 @@ class Server:
         torch.cuda.set_device(self.device)
         T = req.stack.shape[0]
         table = mf.prf_table_create(req.vx, req.vy, T, sigma_px=req.sigma_px, kind=req.kind, times=req.times,
-                                    jitter=req.jitter)
+                                    jitter=req.jitter, phase_steps=req.phase_steps)
         return table, footprint_bytes(req, table)
 
     # ----------------------------------------------------------- admission
