@@ -127,9 +127,10 @@ void orc_trajectory_table_quantised(int K, int T, const double *vx, const double
  * are missing while TESS downlinks, so time jumps).  Frame t is taken at
  * time times[t] (in frame cadences; NULL: t) and every source appears
  * displaced by (jx[t], jy[t]) pixels (NULL: 0), so the position is
- * c = v * times[t] + j[t]. */
+ * c = v * times[t] + j[t].  Q > 0 rounds the phases to multiples of 1/Q as
+ * orc_trajectory_table_quantised does (Q = 0: exact phases). */
 void orc_trajectory_table_frames(int K, int T, const double *vx, const double *vy, const double *times,
-                                 const double *jx, const double *jy, double sigma, int kind,
+                                 const double *jx, const double *jy, double sigma, int kind, int Q,
                                  int32_t *shifts, double *taps)
 {
     for (int k = 0; k < K; k++) {
@@ -139,10 +140,14 @@ void orc_trajectory_table_frames(int K, int T, const double *vx, const double *v
             double cy = vy[k] * tau + (jy ? jy[t] : 0.0);
             double sx = floor(cx + 0.5);
             double sy = floor(cy + 0.5);
+            double px = cx - sx, py = cy - sy;
+            if (Q > 0) {
+                px = floor(px * Q + 0.5) / Q;
+                py = floor(py * Q + 0.5) / Q;
+            }
             shifts[((size_t)k * T + t) * 2 + 0] = (int32_t)sx;
             shifts[((size_t)k * T + t) * 2 + 1] = (int32_t)sy;
-            orc_prf_taps(cx - sx, cy - sy, sigma, kind,
-                         taps + ((size_t)k * T + t) * 25);
+            orc_prf_taps(px, py, sigma, kind, taps + ((size_t)k * T + t) * 25);
         }
     }
 }

@@ -83,7 +83,7 @@ def _load():
             lib.orc_pixel_integrated_gauss.argtypes = [i, d, d]
             lib.orc_pixel_integrated_gauss.restype = d
             lib.orc_trajectory_table.argtypes = [i, i, P, P, d, i, P, P]
-            lib.orc_trajectory_table_frames.argtypes = [i, i, P, P, P, P, P, d, i, P, P]
+            lib.orc_trajectory_table_frames.argtypes = [i, i, P, P, P, P, P, d, i, i, P, P]
             lib.orc_trajectory_table_quantised.argtypes = [i, i, P, P, d, i, i, P, P]
             lib.orc_inverse_variance.argtypes = [i, i, P, P, P]
             lib.orc_search_full.argtypes = [i, i, i, P, P, P, i, P, P, P, P]
@@ -129,11 +129,13 @@ def trajectory_table(vx, vy, T: int, sigma: float = 0.7, kind: int = 0):
     return shifts, taps
 
 
-def trajectory_table_frames(vx, vy, T: int, times=None, jitter=None, sigma: float = 0.7, kind: int = 0):
+def trajectory_table_frames(vx, vy, T: int, times=None, jitter=None, sigma: float = 0.7, kind: int = 0,
+                            Q: int = 0):
     """As ``trajectory_table`` with frame times and pointing jitter (Section
     2.1 and Fig. 3): position c = v * times[t] + jitter[t].  ``times`` [T]
     in frame cadences (None: 0..T-1); ``jitter`` [T, 2] as (x, y) pixels
-    (None: 0)."""
+    (None: 0); Q > 0: phases rounded to multiples of 1/Q as in
+    ``trajectory_table_quantised``."""
     vx = np.ascontiguousarray(vx, np.float64)
     vy = np.ascontiguousarray(vy, np.float64)
     K = vx.shape[0]
@@ -145,7 +147,7 @@ def trajectory_table_frames(vx, vy, T: int, times=None, jitter=None, sigma: floa
     shifts = np.zeros((K, T, 2), np.int32)
     taps = np.zeros((K, T, 5, 5), np.float64)
     _load().orc_trajectory_table_frames(K, int(T), _ptr(vx), _ptr(vy), _ptr(tm), _ptr(jx), _ptr(jy),
-                                        float(sigma), int(kind), _ptr(shifts), _ptr(taps))
+                                        float(sigma), int(kind), int(Q), _ptr(shifts), _ptr(taps))
     return shifts, taps
 
 

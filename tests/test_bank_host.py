@@ -100,3 +100,16 @@ def test_bank_arguments_rejected():
     # the outputs are optional at the C level
     assert mf.load().mf_prf_bank(mf.binding.PrfParams(0, 0, 0.7), vx.ctypes.data_as(mf.binding.ctypes.c_void_p),
                                  vy.ctypes.data_as(mf.binding.ctypes.c_void_p), 2, 3, None, None, None) == 0
+
+
+@pytest.mark.parametrize("Q", [2, 4, 7])
+def test_quantised_frame_model_bank_equals_oracle(oracle, Q):
+    T = 48
+    g = np.random.default_rng(Q)
+    tau = np.arange(T, dtype=np.float64) + np.where(np.arange(T) >= T // 3, 55.0, 0.0) + g.uniform(-0.2, 0.2, T)
+    jitter = g.uniform(-0.8, 0.8, size=(T, 2))
+    vx, vy = _vel(Q + 100, 8, 0.5)
+    s0, t0 = oracle.trajectory_table_frames(vx, vy, T, times=tau, jitter=jitter, Q=Q)
+    s1, t1 = mf.prf_bank(vx, vy, T, times=tau, jitter=jitter, phase_steps=Q)
+    assert np.array_equal(s0, s1)
+    np.testing.assert_allclose(t1, t0, rtol=0, atol=TAP_TOL)

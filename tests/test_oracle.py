@@ -625,3 +625,23 @@ def test_quantised_gather_on_grid_is_exact_search(oracle):
     N1, D1 = oracle.search_quantised_gather(res, lam, vx, vy, 8)
     np.testing.assert_allclose(N1, N0, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(D1, D0, rtol=1e-12, atol=1e-12)
+
+
+def test_quantised_frames_reduce_to_quantised_table(oracle):
+    # the frame model with quantised phases: no times and no jitter is the
+    # linear quantised bank, zero jitter and times 0..T-1 likewise
+    g = _rng(24)
+    vx, vy = g.uniform(-0.6, 0.6, 7), g.uniform(-0.6, 0.6, 7)
+    T = 33
+    for Q in (1, 3, 4):
+        s0, t0 = oracle.trajectory_table_quantised(vx, vy, T, Q)
+        s1, t1 = oracle.trajectory_table_frames(vx, vy, T, Q=Q)
+        s2, t2 = oracle.trajectory_table_frames(vx, vy, T, times=np.arange(T, dtype=float),
+                                                jitter=np.zeros((T, 2)), Q=Q)
+        assert np.array_equal(s0, s1) and np.array_equal(t0, t1)
+        assert np.array_equal(s0, s2) and np.array_equal(t0, t2)
+    # integer jitter moves the base pixel and leaves the rounded phase alone
+    s0, t0 = oracle.trajectory_table_frames(vx, vy, T, Q=4)
+    j = np.tile([[2.0, -3.0]], (T, 1))
+    s1, t1 = oracle.trajectory_table_frames(vx, vy, T, jitter=j, Q=4)
+    assert np.array_equal(s1 - s0, np.broadcast_to([2, -3], s0.shape)) and np.array_equal(t0, t1)
