@@ -22,7 +22,9 @@
  *
  * Conventions for every entry point:
  *   - Device pointers are CUDA device memory on the current device, owned by
- *     the caller.  The library owns only the table handle it creates.
+ *     the caller.  The library owns only the table and batch handles it
+ *     creates.  The host-only calls (mf_prf_plan, mf_prf_plan_frames,
+ *     mf_prf_bank) touch no device and need no GPU.
  *   - Work is enqueued on the given stream and is asynchronous; results are
  *     valid once the caller synchronises that stream.  NULL stream means the
  *     legacy default stream.
