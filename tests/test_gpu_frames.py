@@ -117,13 +117,3 @@ def test_frames_rejects_bad_models(mf):
     with pytest.raises(ValueError):
         mf.prf_table_create(vx, vy, 3, times=np.zeros(4))
 
-
-def test_host_plan_equals_created_table(mf):
-    # mf_prf_plan_frames (host only) describes the layout that
-    # mf_prf_table_create_frames builds on the device
-    from paper_2209_09848_gb300 import synth
-    T = 60
-    vx, vy = synth.velocity_grid(4, 3, -0.3, 0.3)
-    tau, jitter = _frames(T, 5, gap=90, jit=0.6, frac=True)
-    for kw in ({}, {"times": tau, "jitter": jitter}, {"times": tau, "jitter": jitter, "kernel": 1}):
-        assert mf.prf_plan(vx, vy, T, **kw) == mf.prf_table_create(vx, vy, T, **kw).info()

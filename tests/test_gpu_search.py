@@ -307,24 +307,3 @@ def test_shift_stack_single_tap_equals_batch(mf):
     assert torch.equal(smax, bmax) and torch.equal(amax, bamax)
     assert mf.prf_table_create(vx, vy, T).info()["taps"] == 5
 
-
-@pytest.mark.parametrize("Q,layout", [(4, {}), (2, {"kernel": 1}), (8, {"kernel": 2, "tile_w": 64, "segments": 2})])
-def test_phase_quantised_bank_matches_oracle(mf, oracle, Q, layout):
-    """The phase-quantised filter bank (footprints at phases rounded to
-    multiples of 1/Q) searched exactly: the table equals the oracle's
-    quantised table and the maps match the oracle's search over it."""
-    from paper_2209_09848_gb300 import synth
-    T, H, W = 20, 70, 90
-    c = synth.small_case(T, H, W, 17 + Q, mask_frac=0.02, movers=2)
-    vx, vy = synth.velocity_grid(4, 3, -0.45, 0.45)
-    table = mf.prf_table_create(vx, vy, T, phase_steps=Q, **layout)
-    if layout.get("kernel"):
-        assert table.info()["kernel"] == layout["kernel"]
-    sh, tp = oracle.trajectory_table_quantised(vx, vy, T, Q)
-    sg, tg = table.export()
-    assert np.array_equal(sg, sh)
-    np.testing.assert_allclose(tg, tp, rtol=0, atol=1e-15)
-    lam = oracle.inverse_variance(c["sigma"], c["mask"])
-    N, D = oracle.search_full(c["res"], lam, sh, tp)
-    smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
-    check_search(smax, amax, sall, N, D, oracle, label="quantised Q=%d %s" % (Q, layout))
