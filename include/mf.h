@@ -531,6 +531,15 @@ const char *mf_last_error(void);
  * the device).  MF_OK, or MF_ETIMEOUT if a kernel's bounded wait gave up. */
 mf_status mf_device_status(void);
 
+/* Exercise the failure path of the bounded device waits (no counterpart in
+ * the paper): enqueue on `stream` one CTA that waits on an mbarrier nothing
+ * completes, with the same bound as every wait in the kernels (about one
+ * second).  The wait gives up and records code 4 in the device status word,
+ * so the next mf_device_status() returns MF_ETIMEOUT and clears it.  Nothing
+ * faults, traps or hangs, and the context stays usable.  For tests of the
+ * error path; searches enqueued before the word is cleared return at once. */
+mf_status mf_wait_probe(mf_stream stream);
+
 /* Library version string. */
 const char *mf_version(void);
 

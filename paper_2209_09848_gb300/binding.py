@@ -168,6 +168,7 @@ def load():
             "mf_batch_destroy": ([P], None),
             "mf_last_error": ([], ctypes.c_char_p),
             "mf_device_status": ([], ctypes.c_int),
+            "mf_wait_probe": ([P], ctypes.c_int),
             "mf_version": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -686,4 +687,12 @@ class Batch:
 
 
 def device_status() -> int:
+    """mf_device_status: synchronise, then read and clear the device status
+    word (0, or MF_ETIMEOUT with the wait's code in last_error())."""
     return load().mf_device_status()
+
+
+def wait_probe(stream=None):
+    """mf_wait_probe: one CTA whose bounded wait runs out (about a second);
+    the next device_status() returns MF_ETIMEOUT and clears the word."""
+    _check(load().mf_wait_probe(_stream_ptr(stream)))

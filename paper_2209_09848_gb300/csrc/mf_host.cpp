@@ -1719,6 +1719,13 @@ mf_status mf_device_status(void) {
     return ok();
 }
 
+mf_status mf_wait_probe(mf_stream stream) {
+    char err[256] = {0};
+    const int rc = mf::launch_wait_probe(stream, err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
 const char *mf_version(void) { return "libmf 0.1 (sm_103a)"; }
 
 }  // extern "C"

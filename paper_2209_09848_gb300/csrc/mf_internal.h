@@ -325,6 +325,9 @@ size_t refit_q1_off(int64_t T);
 int launch_refit(const RefitArgs &a, char *err, size_t errlen);
 
 int read_device_status(int *status);
+// Status code a wait probe records (the kernels' waits use 1 to 3).
+constexpr int kWaitProbeCode = 4;
+int launch_wait_probe(void *stream, char *err, size_t errlen);
 
 // Device address of the status word that bounded waits write on giving up.
 int *status_word(char *err, size_t errlen);

@@ -1437,6 +1437,37 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
     return 0;
 }
 
+namespace {
+
+// One CTA whose thread 0 waits on an mbarrier that nothing arrives at, with
+// the same bounded wait as every kernel of the library: the wait gives up,
+// records `code` in the status word and returns, and the CTA exits.  It
+// exercises the failure path of the search kernels on purpose; nothing
+// faults, traps or hangs.
+__global__ void k_wait_probe(int code) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0u, code);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(smem_u32(&bar));
+}
+
+}  // namespace
+
+int launch_wait_probe(void *stream, char *err, size_t errlen) {
+    k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(kWaitProbeCode);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "k_wait_probe: %s", cudaGetErrorString(e));
+        return (int)e;
+    }
+    return 0;
+}
+
 int *status_word(char *err, size_t errlen) {
     static std::mutex mu;
     static std::vector<int *> addr;
