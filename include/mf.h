@@ -56,7 +56,7 @@ typedef enum {
     MF_ENOMEM = 2,        /* table creation could not allocate device memory */
     MF_ECUDA = 3,         /* a CUDA runtime call failed (text in mf_last_error) */
     MF_ETIMEOUT = 4,      /* a bounded device wait gave up (see mf_device_status) */
-    MF_EUNSUPPORTED = 5   /* valid request this build does not handle */
+    MF_EUNSUPPORTED = 5   /* valid request the library does not handle */
 } mf_status;
 
 typedef enum {
