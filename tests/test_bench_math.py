@@ -30,3 +30,16 @@ def test_peak_and_paper_rate(bench):
     assert bench._fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
     assert bench.PAPER_RATE == pytest.approx(100 * 1000 * 2048 * 2048 / 300.0)
     assert bench.job_throughput(10.0, 4, 2.0) == 20.0
+
+
+def test_traffic_comes_from_the_committed_summaries(bench):
+    # the bench's roofline.traffic is the DRAM bytes per step recorded in the
+    # ncu summary of the kernel the plan uses
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for kernel, name in ((2, "k_numerator_fac_paper_shaped.md"), (1, "k_numerator_paper_shaped.md")):
+        text = open(os.path.join(root, "profiles", name)).read()
+        m = re.search(r"^traffic_bytes_per_step:\s*(\S+)", text, re.M)
+        want = None if m is None or m.group(1) == "null" else float(m.group(1))
+        assert bench._traffic_from_profiles(kernel) == want
+    assert bench._traffic_from_profiles(2) == pytest.approx(57.03e9)
