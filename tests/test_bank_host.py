@@ -5,6 +5,8 @@ times with gaps and fractional values, pointing jitter; Section 2.1, Fig. 3)
 and the phase-quantised bank.  Shifts are integers and must be identical;
 footprints agree to FP64 rounding (the two sides normalise in different
 orders)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -113,3 +115,29 @@ def test_quantised_frame_model_bank_equals_oracle(oracle, Q):
     s1, t1 = mf.prf_bank(vx, vy, T, times=tau, jitter=jitter, phase_steps=Q)
     assert np.array_equal(s0, s1)
     np.testing.assert_allclose(t1, t0, rtol=0, atol=TAP_TOL)
+
+
+def _quantised_golden():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "trajectory_quantised.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            v, t, q, s, ph = line.split()
+            rows.append((float(v), int(t), int(q), int(s), float(ph)))
+    return rows
+
+
+def test_quantised_golden(oracle):
+    # hand-worked base pixels and rounded phases, both axes, on the oracle
+    # and on the library's host-built bank
+    for v, t, Q, s, ph in _quantised_golden():
+        want = oracle.prf_taps(ph, 0.0)
+        for build in (lambda a, b: oracle.trajectory_table_quantised(a, b, t + 1, Q),
+                      lambda a, b: mf.prf_bank(a, b, t + 1, phase_steps=Q)):
+            sh, tp = build([v], [0.0])
+            assert sh[0, t, 0] == s and sh[0, t, 1] == 0, (v, t, Q)
+            np.testing.assert_allclose(tp[0, t], want, rtol=0, atol=1e-15)
+            sh, tp = build([0.0], [v])
+            assert sh[0, t, 1] == s and sh[0, t, 0] == 0, (v, t, Q)
+            np.testing.assert_allclose(tp[0, t], want.T, rtol=0, atol=1e-15)
