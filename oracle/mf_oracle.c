@@ -153,14 +153,18 @@ void orc_trajectory_table_frames(int K, int T, const double *vx, const double *v
 }
 
 /* Inverse variance per pixel (Section 3.2: Gaussian noise of known width;
- * bright pixels are clipped).  Masked pixels get weight 0. */
+ * bright pixels are clipped).  Masked pixels get weight 0.  A pixel whose
+ * noise is not a finite positive number carries no usable measurement
+ * (Section 3.2 weighs each pixel by its known noise), so it is excluded the
+ * same way: sigma <= 0, NaN or infinite gives weight 0. */
 void orc_inverse_variance(int H, int W, const float *sigma, const uint8_t *mask,
                           double *lam)
 {
     for (size_t i = 0; i < (size_t)H * W; i++) {
         double s = (double)sigma[i];
         int masked = mask ? (mask[i] != 0) : 0;
-        lam[i] = masked ? 0.0 : 1.0 / (s * s);
+        int usable = s > 0.0 && isfinite(s);
+        lam[i] = (masked || !usable) ? 0.0 : 1.0 / (s * s);
     }
 }
 

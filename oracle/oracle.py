@@ -22,7 +22,8 @@ Functions and the passages they follow:
   the downlink gap makes time jump) and the pointing jitter (Section 2.1;
   Section 3.2: the filter follows the trajectory including the jitter).
 * ``inverse_variance`` -- Section 3.2 (Gaussian noise of known width; bright
-  pixels are clipped, read here as excluded: weight 0).
+  pixels are clipped, read here as excluded: weight 0).  A pixel whose noise
+  is not a finite number above 0 is excluded the same way.
 * ``search_full`` / ``search_points`` -- Section 3.2, Eq. 5 (dot product of
   the filter with the data at every pixel location), in the C oracle.
 * ``snr_and_best`` -- Section 3.2 (maximum score over the filter bank gives

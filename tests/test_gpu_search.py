@@ -121,6 +121,44 @@ def test_fully_masked_gives_minus_one(mf):
     assert np.all(amax == -1) and np.all(smax == 0) and np.all(sall == 0)
 
 
+def test_unusable_sigma_is_masked(mf, oracle):
+    # sigma of 0, -1, NaN, +-inf at unmasked pixels: excluded like masked
+    # pixels on both sides (the oracle's rule is pinned without a GPU)
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 14, 57, 83
+    c = synth.small_case(T, H, W, 13, mask_frac=0.02, movers=2)
+    sigma = c["sigma"].copy()
+    g = np.random.default_rng(77)
+    flat = g.choice(H * W, size=60, replace=False)
+    vals = np.array([0.0, -1.0, np.nan, np.inf, -np.inf, -0.0], np.float32)
+    sigma.reshape(-1)[flat] = vals[np.arange(flat.size) % vals.size]
+    vx, vy = synth.velocity_grid(3, 4, -0.3, 0.3)
+    table = mf.prf_table_create(vx, vy, T)
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma, c["mask"])
+    assert np.all(np.isfinite(lam))
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    smax, amax, sall = _run(mf, c["res"], sigma, c["mask"], table)
+    assert np.all(np.isfinite(smax)) and np.all(np.isfinite(sall))
+    check_search(smax, amax, sall, N, D, oracle, label="unusable sigma")
+    # and with the general kernel
+    table_g = mf.prf_table_create(vx, vy, T, kernel=1)
+    smax, amax, sall = _run(mf, c["res"], sigma, c["mask"], table_g)
+    check_search(smax, amax, sall, N, D, oracle, label="unusable sigma, general kernel")
+    # the FP64 re-score applies the same rule
+    dev = "cuda"
+    raw, n = mf.rescore_topk(torch.from_numpy(c["res"]).to(dev), torch.from_numpy(sigma).to(dev), table,
+                             torch.from_numpy(smax).to(dev), torch.from_numpy(amax).to(dev), 200,
+                             mask=torch.from_numpy(c["mask"]).to(dev))
+    torch.cuda.synchronize()
+    assert mf.device_status() == 0
+    cands = mf.decode_candidates(raw, int(n.item()))
+    Nc, Dc = oracle.search_points(c["res"], lam, sh, tp, cands["y"].astype(np.int32), cands["x"].astype(np.int32),
+                                  cands["k"].astype(np.int32))
+    ok = Dc > 0
+    np.testing.assert_allclose(cands["snr"][ok], Nc[ok] / np.sqrt(Dc[ok]), rtol=1e-9, atol=1e-12)
+
+
 def test_empty_frame_is_a_no_op(mf):
     table = mf.prf_table_create([0.1], [0.0], 3)
     r = torch.zeros((3, 0, 7), device="cuda")

@@ -348,6 +348,47 @@ def test_linearity_scaling_mask_translation(oracle):
                                rtol=1e-13)
 
 
+def test_unusable_sigma_counts_as_masked(oracle):
+    """A pixel whose noise is 0, negative, NaN or infinite carries no usable
+    measurement: it weighs 0 in N and D, exactly as if it were masked (the
+    mask excludes pixels, Section 3.2).  Hand-built map: the bad values are
+    planted at known pixels and the search is compared with a plain run in
+    which those pixels hold sigma = 1 and are masked instead."""
+    g = _rng(31)
+    T, H, W = 6, 14, 16
+    res = g.standard_normal((T, H, W)).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.05).astype(np.uint8)
+    bad = {(3, 4): 0.0, (7, 9): -1.0, (10, 2): np.nan, (5, 13): np.inf, (0, 0): -np.inf, (12, 15): -0.0}
+    sig_bad = sigma.copy()
+    sig_ok = sigma.copy()
+    mask_ok = mask.copy()
+    for (y, x), v in bad.items():
+        sig_bad[y, x] = v
+        sig_ok[y, x] = 1.0
+        mask_ok[y, x] = 1
+    lam_bad = oracle.inverse_variance(sig_bad, mask)
+    lam_ok = oracle.inverse_variance(sig_ok, mask_ok)
+    for (y, x) in bad:
+        assert lam_bad[y, x] == 0.0
+    assert np.all(np.isfinite(lam_bad))
+    np.testing.assert_array_equal(lam_bad, lam_ok)
+    # every other pixel keeps 1 / sigma^2 (or 0 where masked)
+    keep = np.ones((H, W), bool)
+    for (y, x) in bad:
+        keep[y, x] = False
+    want = np.where(mask.astype(bool), 0.0, 1.0 / sigma.astype(np.float64) ** 2)
+    np.testing.assert_array_equal(lam_bad[keep], want[keep])
+    vx = np.array([0.3, -0.2])
+    vy = np.array([0.15, 0.4])
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    N1, D1 = oracle.search_full(res, lam_bad, shifts, taps)
+    N2, D2 = oracle.search_full(res, lam_ok, shifts, taps)
+    np.testing.assert_array_equal(N1, N2)
+    np.testing.assert_array_equal(D1, D2)
+    assert np.all(np.isfinite(N1)) and np.all(np.isfinite(D1))
+
+
 # ------------------------------------------------------------ statistics --
 
 def test_pure_noise_snr_is_standard_normal(oracle):
