@@ -305,11 +305,15 @@ mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *ma
  * call cudaMalloc (it can synchronise the device and stall other streams).
  * Arguments, outputs, arithmetic and errors are those of mf_search minus the
  * workspace: the scratch is a static device array of 64 MiB inside libmf,
- * which every GPU that loads the library holds until the process exits.
+ * which a GPU holds from the first use of the array there (with CUDA's
+ * default lazy module loading: this entry point's first call on that device;
+ * with eager loading: when the library loads) until the process exits.
  * A search needing more scratch than that (mf_search_workspace_size) is
  * rejected with MF_EINVAL and nothing is enqueued.  The first call on a
  * device looks the array's device address up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
+ * that device current; make that first call before any stream capture.  The
+ * address is kept for the process and does not survive cudaDeviceReset: do
+ * not call this entry point after resetting the device.  All
  * calls share the one array and it keeps the previous call's contents (the
  * search clears what it needs cleared), so calls whose work overlaps on the
  * GPU (different streams, no ordering between them) race on it: serialise

@@ -2,11 +2,17 @@
 // allocate device memory themselves.  Its scratch memory is one file-scope
 // device array of fixed size; the search itself is mf_search, unchanged.
 //
-// The array belongs to the library image: every GPU that loads libmf holds it
-// (kNoAllocScratchBytes) until the process exits.  Host code cannot pass the
+// The array belongs to the library image: a GPU holds it (kNoAllocScratchBytes)
+// from the moment the library's device code is loaded there -- with CUDA's
+// default lazy module loading, on the first use of the array, i.e. the first
+// call of this entry point on that device; with eager loading, when the
+// library is loaded -- until the process exits.  Host code cannot pass the
 // array's name to a kernel (on the host it names a stand-in, not device
 // memory), so the device address is looked up with cudaGetSymbolAddress once
-// per device, with that device current, on the first call made there.
+// per device, with that device current, on the first call made there.  The
+// cached address belongs to the device's primary context: it does not
+// survive cudaDeviceReset, after which this entry point must not be called
+// again in the same process.
 #include <cuda_runtime.h>
 
 #include <cstdio>
