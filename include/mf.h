@@ -33,9 +33,13 @@
  *     were; mf_last_error() then describes the problem.
  *   - mf_search and mf_rescore_topk allocate nothing: scratch memory is the
  *     caller's workspace, sized by the matching *_workspace_size call.
- *   - A device-side wait that runs out of its iteration budget records
- *     MF_ETIMEOUT in a device status word instead of hanging or trapping;
- *     mf_device_status() reads it.
+ *   - A device-side wait that runs out of its iteration budget gives up
+ *     instead of hanging or trapping.  A search records the failure in its
+ *     own status slot (the first bytes of its workspace, read with
+ *     mf_search_status without synchronising anything); the search's
+ *     finalisation copies it into a device-wide status word, which
+ *     mf_device_status() reads.  A failure in one search does not stop
+ *     others, on the same or other streams.
  */
 #ifndef MF_H
 #define MF_H
@@ -535,14 +539,38 @@ const char *mf_last_error(void);
  * the device).  MF_OK, or MF_ETIMEOUT if a kernel's bounded wait gave up. */
 mf_status mf_device_status(void);
 
+/* The status of one search (not in the paper): enqueue on `stream` a copy
+ * of the 4-byte status slot at the start of `workspace` -- the workspace
+ * given to mf_search, or the one given to mf_search_host (whose search
+ * workspace starts at the same address) -- into `out` (host memory, pinned
+ * for an asynchronous copy, or device memory).  Once `stream` has reached
+ * the copy, *out is 0 if every bounded wait of that search completed, or the
+ * code of the wait that gave up (1-3 from the search kernels, 4 from
+ * mf_wait_probe_search); a nonzero code means the search's maps are not
+ * valid (MF_ETIMEOUT).  Enqueue it after the search on the same stream: the
+ * search clears the slot when it starts.  Synchronises nothing, so a server
+ * can attribute a failure to the request that met it.
+ * Errors: MF_EINVAL (NULL pointers, workspace not 256-byte aligned),
+ * MF_ECUDA (the copy could not be enqueued). */
+mf_status mf_search_status(const void *workspace, int32_t *out, mf_stream stream);
+
 /* Exercise the failure path of the bounded device waits (no counterpart in
  * the paper): enqueue on `stream` one CTA that waits on an mbarrier nothing
  * completes, with the same bound as every wait in the kernels (about one
  * second).  The wait gives up and records code 4 in the device status word,
  * so the next mf_device_status() returns MF_ETIMEOUT and clears it.  Nothing
  * faults, traps or hangs, and the context stays usable.  For tests of the
- * error path; searches enqueued before the word is cleared return at once. */
+ * error path; searches read their own status slots, so they are unaffected. */
 mf_status mf_wait_probe(mf_stream stream);
+
+/* mf_wait_probe aimed at one search (not in the paper): the wait's code (4)
+ * goes into the status slot of `workspace` (a search workspace, as for
+ * mf_search_status) as well as the device status word.  Enqueued after that
+ * search on the same stream, it makes the search report MF_ETIMEOUT through
+ * mf_search_status, as if one of its own waits had run out; for tests of how
+ * a caller handles a failed search.  Errors: MF_EINVAL (NULL or unaligned
+ * workspace), MF_ECUDA. */
+mf_status mf_wait_probe_search(void *workspace, mf_stream stream);
 
 /* Library version string. */
 const char *mf_version(void);

@@ -11,5 +11,5 @@ from .binding import (  # noqa: F401
     rescore_topk, rescore_workspace_size, device_status, last_error, version, load, library_path,
     profile_enable, profile_read, decode_candidates, prf_plan, prf_bank, Batch,
     detect, detect_workspace_size, decode_detections, DETECTION_BYTES,
-    background_refit, refit_workspace_size, wait_probe,
+    background_refit, refit_workspace_size, wait_probe, wait_probe_search, search_status, MF_ETIMEOUT,
 )

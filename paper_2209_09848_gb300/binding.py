@@ -169,6 +169,8 @@ def load():
             "mf_last_error": ([], ctypes.c_char_p),
             "mf_device_status": ([], ctypes.c_int),
             "mf_wait_probe": ([P], ctypes.c_int),
+            "mf_wait_probe_search": ([P, P], ctypes.c_int),
+            "mf_search_status": ([P, P, P], ctypes.c_int),
             "mf_version": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -696,3 +698,23 @@ def wait_probe(stream=None):
     """mf_wait_probe: one CTA whose bounded wait runs out (about a second);
     the next device_status() returns MF_ETIMEOUT and clears the word."""
     _check(load().mf_wait_probe(_stream_ptr(stream)))
+
+
+def wait_probe_search(workspace: torch.Tensor, stream=None):
+    """mf_wait_probe_search: a bounded wait that runs out and records its code
+    (4) in the status slot of this search workspace (and the device word)."""
+    _device_arg("workspace", workspace, optional=False)
+    _check(load().mf_wait_probe_search(_ptr(workspace), _stream_ptr(stream)))
+
+
+def search_status(workspace: torch.Tensor, out: torch.Tensor, stream=None):
+    """mf_search_status: enqueue a copy of the search's status slot (at the
+    start of `workspace`) into `out`, an int32 tensor of one element (pinned
+    host memory or device memory).  Nonzero once the copy has run: a bounded
+    wait of that search gave up (MF_ETIMEOUT)."""
+    _device_arg("workspace", workspace, optional=False)
+    if out.dtype != torch.int32 or out.numel() < 1 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int32 tensor with at least one element")
+    if not out.is_cuda and not out.is_pinned():
+        raise ValueError("a host `out` must be pinned memory")
+    _check(load().mf_search_status(_ptr(workspace), _ptr(out), _stream_ptr(stream)))

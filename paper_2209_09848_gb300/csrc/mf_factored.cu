@@ -385,8 +385,13 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMa
 template <int V>
 __global__ void k_finalize_planes(const float *__restrict__ plane, const float *__restrict__ isd, int K, int64_t P,
                                   float *__restrict__ snr_max, int32_t *__restrict__ argmax,
-                                  float *__restrict__ snr_all) {
+                                  float *__restrict__ snr_all, const int *slot, int *global_status) {
     using VecT = typename std::conditional<V == 4, float4, float>::type;
+    // a failure of this search also goes into the device-wide word
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int s = *(const volatile int *)slot;
+        if (s != 0) atomicCAS(global_status, 0, s);
+    }
     const int64_t n = P / V;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float best[V];
@@ -424,7 +429,8 @@ __global__ void k_finalize_planes(const float *__restrict__ plane, const float *
 }  // namespace
 
 int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P, float *snr_max, int32_t *argmax,
-                         float *snr_all, void *stream, char *err, size_t errlen) {
+                         float *snr_all, const int *slot, int *global_status, void *stream, char *err,
+                         size_t errlen) {
     if (P <= 0) return 0;
     const bool vec = P % 4 == 0 && (uintptr_t)snr_all % 16 == 0;
     const int64_t items = vec ? P / 4 : P;
@@ -432,10 +438,10 @@ int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P,
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (vec)
         k_finalize_planes<4><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(plane, isd, K, P, snr_max, argmax,
-                                                                                 snr_all);
+                                                                                 snr_all, slot, global_status);
     else
         k_finalize_planes<1><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(plane, isd, K, P, snr_max, argmax,
-                                                                                 snr_all);
+                                                                                 snr_all, slot, global_status);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(err, errlen, "k_finalize_planes: %s", cudaGetErrorString(e));

@@ -944,6 +944,7 @@ WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_tabl
         off = (size_t)round_up((int64_t)(off + bytes), 256);
         return o;
     };
+    L.status_off = take(sizeof(int));  // offset 0 (mf_search_status reads it there)
     L.lam_off = take((size_t)L.lam_w * L.lam_h * sizeof(float));
     L.y_off = take((size_t)T * H * L.y_pitch * sizeof(float));
     L.isd_off = take((size_t)tab->K * H * W * sizeof(float));
@@ -1585,6 +1586,11 @@ HostSearchLayout host_search_layout(const mf_stack *st, const mf_prf_table *tabl
     HostSearchLayout L{};
     const int64_t T = st->T, H = st->H, W = st->W;
     size_t off = 0;
+    // the search's own workspace first: its status slot is then at offset 0
+    // of this workspace too (mf_search_status)
+    L.search_bytes = mf::search_layout(T, H, W, table).total;
+    L.search_off = off;
+    off = align256(off + L.search_bytes);
     L.stack_off = off;
     off = align256(off + (size_t)T * H * W * elem_size(st->dtype));
     L.smax_off = off;
@@ -1595,9 +1601,6 @@ HostSearchLayout host_search_layout(const mf_stack *st, const mf_prf_table *tabl
     off = align256(off + (size_t)(k_top > 0 ? k_top : 0) * sizeof(mf_candidate));
     L.n_off = off;
     off = align256(off + sizeof(int32_t));
-    L.search_bytes = mf::search_layout(T, H, W, table).total;
-    L.search_off = off;
-    off = align256(off + L.search_bytes);
     L.rescore_bytes = k_top > 0 ? mf::rescore_workspace(H, W, k_top) : 0;
     L.rescore_off = off;
     off = align256(off + L.rescore_bytes);
@@ -1721,8 +1724,25 @@ mf_status mf_device_status(void) {
 
 mf_status mf_wait_probe(mf_stream stream) {
     char err[256] = {0};
-    const int rc = mf::launch_wait_probe(stream, err, sizeof err);
+    const int rc = mf::launch_wait_probe(stream, nullptr, err, sizeof err);
     if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
+mf_status mf_wait_probe_search(void *workspace, mf_stream stream) {
+    if (!workspace) return fail(MF_EINVAL, "workspace is NULL");
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    char err[256] = {0};
+    const int rc = mf::launch_wait_probe(stream, static_cast<int *>(workspace), err, sizeof err);
+    if (rc != 0) return fail(MF_ECUDA, "%s", err);
+    return ok();
+}
+
+mf_status mf_search_status(const void *workspace, int32_t *out, mf_stream stream) {
+    if (!workspace || !out) return fail(MF_EINVAL, "NULL argument");
+    if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
+    const cudaError_t e = cudaMemcpyAsync(out, workspace, sizeof(int32_t), cudaMemcpyDefault, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "status copy: %s", cudaGetErrorString(e));
     return ok();
 }
 

@@ -212,8 +212,11 @@ struct mf_prf_table {
 
 namespace mf {
 
+// The first 256 bytes of a search workspace hold the search's status slot:
+// 0, or the code of a bounded wait of that search that gave up (its kernels
+// write and read this slot only, so a failure stays with its own search).
 struct WorkspaceLayout {
-    size_t lam_off, y_off, isd_off, keys_off, planes_off, total;
+    size_t status_off, lam_off, y_off, isd_off, keys_off, planes_off, total;
     int64_t pad;       // zero border of the padded lambda image
     int64_t lam_w;     // padded lambda row pitch
     int64_t lam_h;
@@ -327,7 +330,8 @@ int launch_refit(const RefitArgs &a, char *err, size_t errlen);
 int read_device_status(int *status);
 // Status code a wait probe records (the kernels' waits use 1 to 3).
 constexpr int kWaitProbeCode = 4;
-int launch_wait_probe(void *stream, char *err, size_t errlen);
+// slot: a search's status slot to record the probe's code in as well, or null.
+int launch_wait_probe(void *stream, int *slot, char *err, size_t errlen);
 
 // Device address of the status word that bounded waits write on giving up.
 int *status_word(char *err, size_t errlen);
@@ -350,8 +354,11 @@ struct FacParams {
 };
 // SNR with 1 / sqrt(D) from the numerator plane, per-pixel max over k
 // (smallest k on ties) and the optional SNR cube.
+// The search's status slot is copied into the device-wide status word (first
+// failure wins) by the finalisation.
 int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P, float *snr_max, int32_t *argmax,
-                         float *snr_all, void *stream, char *err, size_t errlen);
+                         float *snr_all, const int *slot, int *global_status, void *stream, char *err,
+                         size_t errlen);
 // CTAs of segment `seg` of a factored search: groups x tile columns x tile
 // rows ceil((H + spread) / tile_h), spread the widest of the segment's groups.
 long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W, int seg);

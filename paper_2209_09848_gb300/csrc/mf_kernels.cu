@@ -58,8 +58,11 @@ __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(
 // ------------------------------------------------------------- lambda ---
 
 __global__ void k_lambda(const float *__restrict__ sigma, const uint8_t *__restrict__ mask, int64_t H,
-                         int64_t W, int64_t pad, int64_t lw, int64_t lh, float *__restrict__ lam) {
+                         int64_t W, int64_t pad, int64_t lw, int64_t lh, float *__restrict__ lam, int *status) {
     const int64_t n = lw * lh;
+    // the search's status slot starts clear (the kernels after this one in
+    // stream order write it only on a failure)
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t yy = i / lw - pad, xx = i % lw - pad;
         float v = 0.f;
@@ -186,6 +189,7 @@ struct NumParams {
     const float *isd;             // [K][H][W]
     unsigned long long *keys;     // [H][W]
     float *snr_all;               // [K][H][W] or null
+    int *status;                  // the search's status slot
     int T, G;
     int64_t H, W;
     int tiles_x;
@@ -300,7 +304,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
             cnt[s] = 0;
             last_issued[s] = -1;
         }
-        *bad_flag = status_now();  // an earlier CTA gave up: do not start
+        *bad_flag = dev::status_now(p.status);  // an earlier CTA of this search gave up: do not start
         fence_barrier_init();
     }
     __syncthreads();
@@ -349,7 +353,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
     for (int t = 0; t < p.T; t++) {
         const int s1 = (s + 1 == NS) ? 0 : s + 1;            // stage and phase of frame t + 1
         const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
-        const bool ready = next_ready || mbar_wait(smem_u32(&bars[s]), par, 1);
+        const bool ready = next_ready || dev::mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
         if (!ready && !p.lockstep) {
             bad = true;
             break;
@@ -424,7 +428,7 @@ __device__ __forceinline__ bool numerator_tile(const CUtensorMap *ymap, const Nu
         if (threadIdx.x == 0) {
             for (int s = 0; s < NS; s++) {
                 const int f = last_issued[s];
-                if (f >= 0) mbar_wait(smem_u32(&bars[s]), (uint32_t)((f / NS) & 1), 2);
+                if (f >= 0) dev::mbar_wait(smem_u32(&bars[s]), (uint32_t)((f / NS) & 1), 2, p.status);
             }
         }
         return false;
@@ -524,7 +528,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numerator_batch(const CUtens
 // ----------------------------------------------------------- finalize ---
 
 __global__ void k_finalize(const unsigned long long *__restrict__ keys, int64_t P, float *__restrict__ snr_max,
-                           int32_t *__restrict__ argmax) {
+                           int32_t *__restrict__ argmax, const int *slot, int *global_status) {
+    // a failure of this search also goes into the device-wide word
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int s = *(const volatile int *)slot;
+        if (s != 0) atomicCAS(global_status, 0, s);
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long key = keys[i];
         if (key == 0ull) {
@@ -674,8 +683,8 @@ int enqueue_pre(const SearchArgs &a, cudaStream_t stream, char *err, size_t errl
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
     {
         LaunchScope ls(kKLambda, stream);
-        k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(a.sigma, a.mask, H, W, L.pad, L.lam_w,
-                                                                        L.lam_h, lam);
+        k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(
+            a.sigma, a.mask, H, W, L.pad, L.lam_w, L.lam_h, lam, reinterpret_cast<int *>(a.ws + L.status_off));
     }
     MF_CHECK_LAUNCH("k_lambda");
 
@@ -746,6 +755,7 @@ int numerator_params(const SearchArgs &a, CUtensorMap *map, NumParams *np, int *
     np->isd = reinterpret_cast<float *>(a.ws + L.isd_off);
     np->keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
     np->snr_all = a.snr_all;
+    np->status = reinterpret_cast<int *>(a.ws + L.status_off);
     np->T = (int)T;
     np->G = pl.G;
     np->H = H;
@@ -768,8 +778,7 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     const int64_t T = st.T, H = st.H, W = st.W;
     int rc = get_encode(err, errlen);
     if (rc) return rc;
-    int *status = status_word(err, errlen);
-    if (!status) return (int)cudaErrorInvalidSymbol;
+    int *status = reinterpret_cast<int *>(a.ws + L.status_off);
     float *y = reinterpret_cast<float *>(a.ws + L.y_off);
     cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
     cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * 4, (cuuint64_t)(H * L.y_pitch * 4)};
@@ -838,16 +847,19 @@ NumBatchKernel pick_numerator_batch(int shape) {
 
 int enqueue_finalize(const SearchArgs &a, cudaStream_t stream, char *err, size_t errlen) {
     const int64_t P = a.stack->H * a.stack->W;
+    const int *slot = reinterpret_cast<const int *>(a.ws + a.L.status_off);
+    int *gstatus = status_word(err, errlen);
+    if (!gstatus) return (int)cudaErrorInvalidSymbol;
     if (a.tab->plan.kernel == 2) {
         LaunchScope ls(kKFinalize, stream);
         return fac_finalize_enqueue(reinterpret_cast<const float *>(a.ws + a.L.planes_off),
                                     reinterpret_cast<const float *>(a.ws + a.L.isd_off), a.tab->K, P, a.snr_max,
-                                    a.argmax, a.snr_all, stream, err, errlen);
+                                    a.argmax, a.snr_all, slot, gstatus, stream, err, errlen);
     }
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + a.L.keys_off);
     {
         LaunchScope ls(kKFinalize, stream);
-        k_finalize<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, a.snr_max, a.argmax);
+        k_finalize<<<grid_for(P, 256), 256, 0, stream>>>(keys, P, a.snr_max, a.argmax, slot, gstatus);
     }
     MF_CHECK_LAUNCH("k_finalize");
     return 0;
@@ -1441,25 +1453,25 @@ namespace {
 
 // One CTA whose thread 0 waits on an mbarrier that nothing arrives at, with
 // the same bounded wait as every kernel of the library: the wait gives up,
-// records `code` in the status word and returns, and the CTA exits.  It
-// exercises the failure path of the search kernels on purpose; nothing
-// faults, traps or hangs.
-__global__ void k_wait_probe(int code) {
+// records `code` in the status word (and in a search's status slot, if one is
+// given) and returns, and the CTA exits.  It exercises the failure path of
+// the search kernels on purpose; nothing faults, traps or hangs.
+__global__ void k_wait_probe(int code, int *slot) {
     __shared__ __align__(8) unsigned long long bar;
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&bar), 1);
         fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0u, code);
+    if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0u, code) && slot) atomicCAS(slot, 0, code);
     __syncthreads();
     if (threadIdx.x == 0) mbar_inval(smem_u32(&bar));
 }
 
 }  // namespace
 
-int launch_wait_probe(void *stream, char *err, size_t errlen) {
-    k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(kWaitProbeCode);
+int launch_wait_probe(void *stream, int *slot, char *err, size_t errlen) {
+    k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(kWaitProbeCode, slot);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(err, errlen, "k_wait_probe: %s", cudaGetErrorString(e));

@@ -12,6 +12,11 @@ mf_rescore_topk); this module only schedules.
 
 Latency of a request = time from arrival (submit) to its results being in
 host memory.
+
+Each search reports whether all of its bounded device waits completed
+through its own status slot (mf_search_status), copied back with its
+results; a request whose search gave up is failed with MFError(MF_ETIMEOUT)
+while the requests around it complete normally.
 """
 from __future__ import annotations
 
@@ -48,6 +53,10 @@ class Request:
     jitter: np.ndarray | None = None
     kind: int = 0
     phase_steps: int = 0
+    # for tests of the failure path: enqueue, after this request's search, a
+    # bounded device wait that runs out and records its code in the search's
+    # status slot, so the request must come back failed (MF_ETIMEOUT)
+    probe_timeout: bool = False
 
 
 @dataclasses.dataclass
@@ -62,6 +71,8 @@ class Result:
     tag: object = None
     gpu_start_ms: float = 0.0  # device timeline of the request's work, from the server's start event
     gpu_end_ms: float = 0.0
+    kernel_start_ms: float = 0.0  # the same for its kernels alone (after its uploads, before its downloads)
+    kernel_end_ms: float = 0.0
 
     @property
     def latency(self) -> float:
@@ -111,6 +122,7 @@ class Server:
         self._t0 = torch.cuda.Event(enable_timing=True)  # origin of the device timeline
         self._t0.record(torch.cuda.current_stream(self.device))
         self.rejected = 0
+        self.failed = 0  # requests whose search reported a device wait that gave up
         self._sched = threading.Thread(target=self._schedule_loop, daemon=True)
         self._done = threading.Thread(target=self._complete_loop, daemon=True)
         self._sched.start()
@@ -212,13 +224,21 @@ class Server:
             ws = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
             snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
             argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
+            evk0 = torch.cuda.Event(enable_timing=True)
+            evk0.record(stream)
             mf.search(stack, sigma, table, mask=mask, frame_scale=fs, workspace=ws, out=(snr_max, argmax, None),
                       stream=stream)
+            if req.probe_timeout:
+                mf.wait_probe_search(ws, stream=stream)
             cand = None
             if req.k_top:
                 raw, n = mf.rescore_topk(stack, sigma, table, snr_max, argmax, req.k_top, mask=mask,
                                          frame_scale=fs, stream=stream)
                 cand = (raw, n)
+            evk1 = torch.cuda.Event(enable_timing=True)
+            evk1.record(stream)
+            status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+            mf.search_status(ws, status, stream=stream)
             out_max = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
             out_arg = torch.empty((H, W), dtype=torch.int32, pin_memory=True)
             out_max.copy_(snr_max, non_blocking=True)
@@ -226,8 +246,8 @@ class Server:
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
         # device tensors stay referenced until the job completes
-        return dict(ev=ev, ev0=ev0, keep=(stack, sigma, mask, fs, ws, snr_max, argmax, table), out=(out_max, out_arg),
-                    cand=cand)
+        return dict(ev=ev, ev0=ev0, evk=(evk0, evk1), keep=(stack, sigma, mask, fs, ws, snr_max, argmax, table),
+                    out=(out_max, out_arg), cand=cand, status=status)
 
     # ---------------------------------------------------------- completion
     def _complete_loop(self):
@@ -249,19 +269,32 @@ class Server:
                 continue
             job, fut, arrival, admitted, fp, sidx, tag = item
             done = time.perf_counter()
-            cands = None
-            if job["cand"] is not None:
-                raw, n = job["cand"]
-                cands = mf.decode_candidates(raw, int(n.item()))
-            res = Result(job["out"][0].numpy().copy(), job["out"][1].numpy().copy(), cands, arrival, admitted,
-                         done, fp, tag, self._t0.elapsed_time(job["ev0"]), self._t0.elapsed_time(job["ev"]))
+            code = int(job["status"][0])
+            res = err = None
+            if code != 0:
+                # a bounded wait of this request's search gave up: its maps
+                # are not valid; the other requests are not affected
+                self.failed += 1
+                err = mf.MFError(mf.MF_ETIMEOUT, "request %r: a device wait of its search gave up (code %d)"
+                                 % (tag, code))
+            else:
+                cands = None
+                if job["cand"] is not None:
+                    raw, n = job["cand"]
+                    cands = mf.decode_candidates(raw, int(n.item()))
+                res = Result(job["out"][0].numpy().copy(), job["out"][1].numpy().copy(), cands, arrival, admitted,
+                             done, fp, tag, self._t0.elapsed_time(job["ev0"]), self._t0.elapsed_time(job["ev"]),
+                             self._t0.elapsed_time(job["evk"][0]), self._t0.elapsed_time(job["evk"][1]))
             del job
             with self._cv:
                 self.used -= fp
                 self._active -= 1
                 self._free_streams.append(sidx)
                 self._cv.notify_all()
-            fut.set_result(res)
+            if err is not None:
+                fut.set_exception(err)
+            else:
+                fut.set_result(res)
 
 
 def percentile(xs, q):
