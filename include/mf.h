@@ -95,7 +95,8 @@ typedef struct {
  * data + t * frame_stride + y * row_stride + x (strides in elements).
  * frame_scale is a device array of T floats (NULL means all 1); the residual
  * used by the filter is frame_scale[t] * element.  Scaled bf16/fp16 storage
- * is not in the paper; it halves the bytes of the stack. */
+ * is not in the paper; it halves the bytes of the stack, and of the weighted
+ * stack the search keeps (see mf_search). */
 typedef struct {
     const void *data;
     int32_t dtype;            /* mf_dtype */
@@ -141,9 +142,14 @@ mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const 
  * separable footprints W(a, b) = u_x(a) u_y(b) (every table built by
  * mf_prf_table_create is separable): a 5-tap pass along rows, shared by the
  * trajectories of a CTA that have the same v_x, then a 5-tap pass down
- * columns per trajectory; 0 = automatic (factored whenever the table is
- * separable and the frame windows fit).  Both give the same sums up to FP32
- * rounding.
+ * columns per trajectory; 3 = the factored kernel with phase planes, for
+ * phase-quantised banks (phase_steps > 0; the precompute-then-gather form
+ * of a sparse matched filter): per frame, one 5-tap column pass per rounded
+ * y-phase present among the CTA's trajectories over the whole window, then
+ * one add per (trajectory, pixel) gathered from its phase's plane (FP32
+ * stacks; bf16 / fp16 ones are weighted in FP32; not in batches);
+ * 0 = automatic (factored whenever the table is separable and the frame
+ * windows fit).  All give the same sums up to FP32 rounding.
  *
  * General kernel: shape selects how a CTA's 16 warps split between
  * trajectories and 32 x 32 sub-tiles: 0: 16 trajectories x 1 sub-tile,
@@ -249,6 +255,12 @@ typedef struct {
     int32_t time_segments;    /* time segments of the factored numerator (1 otherwise) */
     int32_t taps;             /* footprint taps per axis the factored passes run: 5, or 1
                                  when every footprint is a single centre tap (kind 2) */
+    int32_t den_tile_h;       /* denominator: rows of start pixels per CTA when each CTA
+                                 stages the lambda box its trajectory reaches in shared
+                                 memory; 0 when the largest box does not fit (the
+                                 denominator then reads lambda through the L1 cache) */
+    int32_t phase_planes;     /* factored numerator with phase planes (kernel 3): planes a
+                                 CTA holds per frame; 0: a column pass per trajectory */
 } mf_table_info;
 
 /* Layout of an existing table. */
@@ -295,7 +307,15 @@ mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *ta
  * workspace: device memory of at least mf_search_workspace_size bytes,
  * 256-byte aligned; its contents on entry do not matter.
  * Arithmetic: numerator in FP32 with blocked accumulation over frames;
- * denominator from FP32 products accumulated in FP64.
+ * denominator from FP32 products accumulated in FP64.  Precision form (a
+ * bf16 / fp16 stack searched by the factored numerator, i.e. any table built
+ * from velocities unless the general kernel is forced): the weighted
+ * residual lambda * frame_scale[t] * value is formed in FP32 and stored in
+ * the stack's own 16-bit type -- bf16 as it is, fp16 divided by the power of
+ * two at or above max(lambda) * frame_scale[t] -- which the numerator reads
+ * (half the bytes of an FP32 weighted stack); that adds one rounding to
+ * each weighted value (relative 2^-8 for bf16, 2^-11 for fp16).  The general
+ * numerator weighs bf16 / fp16 stacks in FP32.
  * Errors: MF_EINVAL on shape/stride/pointer problems (nothing enqueued),
  * MF_ECUDA if a launch fails. */
 mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *mask,

@@ -32,6 +32,10 @@ Functions and the passages they follow:
   implementation for tiny inputs: it builds each filter as a full T x H x W
   tensor (Section 3.2: F in R^{R x C x T}) and takes the dot product.
 * ``inject`` -- Section 4.1 (injection adds a filter times a flux).
+* ``weighted_stack16`` / ``search_weighted`` -- the precision form (not in
+  the paper; 16-bit storage of the stack): the inverse-variance weighted
+  residual of Section 3.2 formed in FP32 and rounded to the stack's 16-bit
+  type, then the matched filter on it.
 * ``search_numpy`` -- a third implementation of the same definition, with
   numpy slicing over whole frames (used to cross-check the C loops).
 
@@ -58,7 +62,8 @@ __all__ = [
     "build", "prf_taps", "trajectory_table", "trajectory_table_frames", "trajectory_table_quantised",
     "inverse_variance", "search_full",
     "search_points", "snr_and_best", "dense_template", "search_dense", "inject",
-    "search_numpy", "search_quantised_gather", "topk_order", "threads",
+    "search_numpy", "search_quantised_gather", "topk_order", "threads", "round_to_bf16", "weighted_stack16",
+    "search_weighted", "search_weighted_points",
 ]
 
 
@@ -207,6 +212,79 @@ def search_points(res, lam, shifts, taps, ys, xs, ks, frame_scale=None):
     D = np.zeros(n, np.float64)
     _load().orc_search_points(T, H, W, _ptr(res), _ptr(fs), _ptr(lam), _ptr(shifts),
                               _ptr(taps), n, _ptr(ys), _ptr(xs), _ptr(ks), _ptr(N), _ptr(D))
+    return N, D
+
+
+def round_to_bf16(x) -> np.ndarray:
+    """FP32 values rounded to the nearest bfloat16 (the upper 16 bits of an
+    FP32), ties to even, returned as FP32.  From the definition: add half
+    of the dropped part's unit (0x7FFF, plus 1 when the kept part is odd) and
+    truncate the low 16 bits."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    keep_odd = (b >> 16) & 1
+    r = ((b + 0x7FFF + keep_odd) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def weighted_stack16(stored, sigma, mask=None, frame_scale=None, dtype="bf16"):
+    """The precision form's weighted stack (not in the paper: residuals
+    stored in 16 bits to halve the stack's bytes, spec extension).
+
+    The inverse-variance weighted residual y_t = lambda * (alpha_t * r_t) of
+    Section 3.2's noise model is formed in FP32 -- lambda = 1 / sigma^2
+    rounded to FP32 (0 where masked or sigma unusable), alpha_t the frame
+    scale, r_t the stored 16-bit value -- and stored in the stack's own
+    16-bit type: bf16 as it is (scale beta_t = 1); fp16 divided by beta_t,
+    the power of two at or above lambda_max * alpha_t (lambda_max the largest
+    lambda), which keeps every stored value within fp16's range and makes
+    the division exact.  Rounding is to nearest, ties to even.
+
+    Returns (q, beta): q [T, H, W] float32 holding the 16-bit values,
+    beta [T] float64, so that the weighted residual is beta_t * q_t.  The
+    matched filter of the precision form is then N = sum W beta q (weights
+    already applied) and D = sum W^2 lambda as usual (``search_weighted``)."""
+    stored = np.ascontiguousarray(stored, np.float32)
+    T = stored.shape[0]
+    s = np.asarray(sigma, np.float64)
+    usable = (s > 0) & np.isfinite(s)
+    if mask is not None:
+        usable &= np.asarray(mask) == 0
+    lam = np.where(usable, 1.0 / np.where(usable, s * s, 1.0), 0.0).astype(np.float32)
+    alpha = np.ones(T, np.float32) if frame_scale is None else np.asarray(frame_scale, np.float32)
+    y = lam[None] * (alpha[:, None, None] * stored)  # FP32 products, in this order
+    if dtype == "bf16":
+        return round_to_bf16(y), np.ones(T, np.float64)
+    if dtype != "fp16":
+        raise ValueError(dtype)
+    lmax = np.float32(lam.max())
+    x = (lmax * alpha).astype(np.float32)
+    e = np.minimum((x.view(np.uint32) >> 23) & 0xFF, 253).astype(np.int64)  # x = 1.m 2^(e - 127)
+    beta = np.where(x > 0, np.ldexp(1.0, e - 126), 1.0)
+    inv = np.where(x > 0, np.ldexp(1.0, 126 - e), 1.0).astype(np.float32)
+    q = (y * inv[:, None, None]).astype(np.float16).astype(np.float32)
+    return q, beta
+
+
+def search_weighted(q, beta, lam, shifts, taps):
+    """Matched filter on a weighted stack whose values already carry lambda:
+    N = sum_t sum_{a,b} W beta_t q_t(q) over the footprint pixels inside the
+    frame (lambda is not applied again), D = sum W^2 lambda (Section 3.2,
+    Eq. 5 with the weights moved into the stored stack)."""
+    q = np.ascontiguousarray(q, np.float32)
+    T, H, W = q.shape
+    ones = np.ones((H, W), np.float64)
+    N, _ = search_full(q, ones, shifts, taps, frame_scale=np.asarray(beta, np.float64))
+    _, D = search_full(q, lam, shifts, taps)  # D does not depend on the stack's values
+    return N, D
+
+
+def search_weighted_points(q, beta, lam, shifts, taps, ys, xs, ks):
+    """``search_weighted`` at the listed (y, x, k) triples."""
+    q = np.ascontiguousarray(q, np.float32)
+    T, H, W = q.shape
+    ones = np.ones((H, W), np.float64)
+    N, _ = search_points(q, ones, shifts, taps, ys, xs, ks, frame_scale=np.asarray(beta, np.float64))
+    _, D = search_points(q, lam, shifts, taps, ys, xs, ks)  # D does not depend on the stack's values
     return N, D
 
 

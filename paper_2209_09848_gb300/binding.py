@@ -97,7 +97,8 @@ class TableInfo(ctypes.Structure):
                 ("max_abs_shift", ctypes.c_int32), ("g_nnz", ctypes.c_int64), ("smem_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("cost", ctypes.c_double), ("vec", ctypes.c_int32),
                 ("lockstep", ctypes.c_int32), ("kernel", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("time_segments", ctypes.c_int32), ("taps", ctypes.c_int32)]
+                ("time_segments", ctypes.c_int32), ("taps", ctypes.c_int32), ("den_tile_h", ctypes.c_int32),
+                ("phase_planes", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -375,9 +376,11 @@ def make_stack(data: torch.Tensor, frame_scale: torch.Tensor | None = None) -> S
                  None if frame_scale is None else frame_scale.data_ptr())
 
 
-def search_workspace_size(shape, table: PrfTable) -> int:
+def search_workspace_size(shape, table: PrfTable, dtype=torch.float32) -> int:
+    """mf_search_workspace_size for a stack of this shape and dtype (a bf16 /
+    fp16 stack may need less: its weighted stack can be 16-bit)."""
     T, H, W = shape
-    st = Stack(None, MF_F32, 0, T, H, W, H * W, W, None)
+    st = Stack(None, _DTYPES[dtype], 0, T, H, W, H * W, W, None)
     n = ctypes.c_size_t()
     _check(load().mf_search_workspace_size(ctypes.byref(st), table.handle, ctypes.byref(n)))
     return n.value
@@ -425,7 +428,7 @@ def search(stack: torch.Tensor, sigma: torch.Tensor, table: PrfTable, mask: torc
         snr_max, argmax, snr_all = out
         _check_search_outputs(snr_max, argmax, snr_all, table, H, W, dev)
     _device_arg("workspace", workspace, dev)
-    nbytes = search_workspace_size((T, H, W), table)
+    nbytes = search_workspace_size((T, H, W), table, stack.dtype)
     ws = _workspace(nbytes, dev, workspace)
     _check(load().mf_search(ctypes.byref(st), _ptr(sigma), _ptr(mask), table.handle, _ptr(snr_max),
                             _ptr(argmax), _ptr(snr_all), _ptr(ws), ws.numel() * ws.element_size(),

@@ -24,6 +24,8 @@
 // writes and their reuse.  FP32 throughout, with the blocked accumulation of
 // the general kernel (partials over 16 frames).
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -42,23 +44,64 @@ using namespace dev;
 // why).  The CTA may have more warps than the search's layout uses (batched
 // searches share one launch): the extra warps take part in the row pass and
 // the barriers only.  `smem` is the CTA's 1024-aligned dynamic shared memory.
-// One row-pass item: H(row, c0 .. c0 + 15) = sum_a u_x(a) R(row, c0 + M + c + a)
-// for a column phase M known at compile time; src = R(row, c0), 16-aligned,
-// dst = H(row, c0).  TAPS = 1 (single-tap footprints: the shift-stack
-// filter) keeps the centre tap only.
-template <int M, int TAPS>
-__device__ __forceinline__ void row_item(const float *__restrict__ src, float *__restrict__ dst, float ux0,
-                                         float ux1, float ux2, float ux3, float ux4) {
-    constexpr int NL = (kFacItem + (TAPS == 1 ? 3 : 4) + M + 3) / 4;  // 128-bit loads covering the inputs
-    float v[4 * NL];
-#pragma unroll
-    for (int q = 0; q < NL; q++) {
-        const float4 x = reinterpret_cast<const float4 *>(src)[q];
-        v[4 * q] = x.x;
-        v[4 * q + 1] = x.y;
-        v[4 * q + 2] = x.z;
-        v[4 * q + 3] = x.w;
+// Values of a staged window: FP32, or the 16-bit types of a bf16 / fp16
+// weighted stack, converted exactly to FP32 as they are read.
+template <typename E>
+struct Win;
+template <>
+struct Win<float> {
+    static constexpr int kPer = 4;  // values per 128-bit load
+    static __device__ __forceinline__ void load(const void *p, float *v) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
     }
+    static __device__ __forceinline__ float one(const float *p) { return *p; }
+};
+template <>
+struct Win<__nv_bfloat16> {
+    static constexpr int kPer = 8;
+    static __device__ __forceinline__ void load(const void *p, float *v) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {  // a bf16 is the high half of the FP32 with the same value
+            v[2 * i] = __uint_as_float(w[i] << 16);
+            v[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+    }
+    static __device__ __forceinline__ float one(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+};
+template <>
+struct Win<__half> {
+    static constexpr int kPer = 8;
+    static __device__ __forceinline__ void load(const void *p, float *v) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    static __device__ __forceinline__ float one(const __half *p) { return __half2float(*p); }
+};
+
+// One row-pass item: H(row, c0 .. c0 + 15) = sum_a u_x(a) R(row, c0 + M + c + a)
+// for a column phase M known at compile time; src = R(row, c0), 16-byte
+// aligned, dst = H(row, c0).  TAPS = 1 (single-tap footprints: the
+// shift-stack filter) keeps the centre tap only.
+template <int M, int TAPS, typename E>
+__device__ __forceinline__ void row_item(const E *__restrict__ src, float *__restrict__ dst, float ux0,
+                                         float ux1, float ux2, float ux3, float ux4) {
+    constexpr int PER = Win<E>::kPer;
+    constexpr int NL = (kFacItem + (TAPS == 1 ? 3 : 4) + M + PER - 1) / PER;  // 128-bit loads covering the inputs
+    float v[PER * NL];
+#pragma unroll
+    for (int q = 0; q < NL; q++) Win<E>::load(src + PER * q, v + PER * q);
     float o[kFacItem];
 #pragma unroll
     for (int c = 0; c < kFacItem; c++) {
@@ -102,10 +145,17 @@ __device__ __forceinline__ bool fac_locate(const FacParams &p, int tw, long long
     return true;
 }
 
-template <int TW, int TAPS>
+// QG: the phase-plane form (phase-quantised banks, five taps, FP32 stacks):
+// per frame the row pass, then one column pass per rounded y-phase present
+// (a plane over the whole window), then one add per (trajectory, pixel)
+// gathered from its phase's plane.
+template <int TW, int TAPS, typename E, bool QG = false>
 __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParams &p, long long cta,
                                          unsigned char *smem) {
-    constexpr int RP = fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / kFacItem;
+    static_assert(!QG || (TAPS == 5 && sizeof(E) == 4), "phase planes: five taps, FP32 stacks");
+    constexpr bool k16 = sizeof(E) == 2;
+    // window pitch (values) and row-pass layout
+    constexpr int RP = k16 ? fac_rpitch16(TW) : fac_rpitch(TW), HP = fac_hpitch(TW), NI = fac_hcols(TW) / kFacItem;
     constexpr int R = kFacRecordChunk;
     constexpr int NSUBX = TW / 32;
 
@@ -130,12 +180,14 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     // schedulers and an empty slot leaves every scheduler the same work
     const int slot = warp / nsub, sub = warp % nsub;
     const int sub_y = sub / NSUBX, sub_x = sub % NSUBX;
-    const uint32_t kBB = (uint32_t)fac_block_bytes(KT);
+    const uint32_t kBB = (uint32_t)fac_block_bytes(KT, QG ? p.npl : 0);
 
-    const int SF = fac_stage_floats(TW, BH);                              // stage stride, 128-byte multiple
-    float *rwin = reinterpret_cast<float *>(smem);                       // [NS][SF] windows of BH x RP
-    float *hbuf = rwin + (size_t)NS * SF;                                 // [kFacHBufs][BH][HP]
-    unsigned char *fb = reinterpret_cast<unsigned char *>(hbuf + (size_t)kFacHBufs * BH * HP);  // [2][R] blocks
+    const int SF = fac_stage_floats(TW, BH);                              // stage stride in floats (128-byte multiple)
+    constexpr int EPF = 4 / (int)sizeof(E);                              // window values per float of a stage
+    E *rwin = reinterpret_cast<E *>(smem);                               // [NS] windows of BH x RP values
+    float *hbuf = reinterpret_cast<float *>(smem) + (size_t)NS * SF;     // [kFacHBufs][BH][HP] (QG: [1])
+    float *pbuf = hbuf + (size_t)(QG ? 1 : kFacHBufs) * BH * HP;         // QG: [npl][BH][HP] phase planes
+    unsigned char *fb = reinterpret_cast<unsigned char *>(pbuf + (size_t)(QG ? p.npl : 0) * BH * HP);  // [2][R]
     uint64_t *bars = reinterpret_cast<uint64_t *>(fb + 2 * R * kBB);
     int *last_issued = reinterpret_cast<int *>(bars + NS);
     int *bad_flag = last_issued + NS;
@@ -152,12 +204,16 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     __syncthreads();
     if (*bad_flag != 0) return false;  // same value for every thread of the CTA
 
-    const uint32_t box_bytes = (uint32_t)BH * RP * 4;
+    const uint32_t box_bytes = (uint32_t)BH * RP * sizeof(E);
     auto issue = [&](int f, int s, int roy, int rox) {
         const uint32_t bar = smem_u32(&bars[s]);
         const int nrec = (f % R == 0) ? min(R, p.T - f) : 0;  // the chunk's records ride on its first frame
         mbar_expect_tx(bar, box_bytes + (uint32_t)nrec * kBB);
-        tma_load_3d(smem_u32(rwin + (size_t)s * SF), &ymap, tile_x0 + rox, tile_y0 + roy, f, bar);
+        // a 16-bit window starts at a multiple of 8 columns (16 bytes; the tile
+        // origin is a multiple of 32): one 4-column step left of rox when rox is
+        // an odd multiple of 4, which the row pass's column phase cofs8 absorbs
+        const int x = tile_x0 + (k16 ? (rox & ~7) : rox);
+        tma_load_3d(smem_u32(rwin + (size_t)s * SF * EPF), &ymap, x, tile_y0 + roy, f, bar);
         if (nrec)
             bulk_load(smem_u32(fb + ((f / R) & 1) * R * kBB), gblocks + (size_t)f * kBB, (uint32_t)nrec * kBB, bar);
         last_issued[s] = f;
@@ -220,9 +276,16 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         const unsigned char *fblk = record(f);
         const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
         const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
-        const float *col = rwin + (size_t)st * SF + (32 * sub_y + fs->oy + 2) * RP + 32 * sub_x + lane + 2 + fh->cofs;
+        const E *col = rwin + (size_t)st * SF * EPF + (32 * sub_y + fs->oy + 2) * RP + 32 * sub_x + lane + 2 +
+                       (k16 ? fh->cofs8 : fh->cofs);
+        if constexpr (k16) {
+            const float bt = p.beta ? p.beta[f] : 1.f;  // a power of two: the products are exact
 #pragma unroll
-        for (int r = 0; r < 32; r++) blk[r] += col[r * RP];
+            for (int r = 0; r < 32; r++) blk[r] += bt * Win<E>::one(col + r * RP);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; r++) blk[r] += Win<E>::one(col + r * RP);
+        }
     };
     // the row passes of frames f0 (stage s0) and f0 + 1 (stage s1, if it
     // exists) as one list of items: item it < n0 is (row, m) of frame f0
@@ -234,24 +297,129 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
             const bool second = it >= n0;
             const FacHdr *fh = second ? h1 : h0;
             const int f = second ? f0 + 1 : f0, st = second ? s1 : s0, j = second ? it - n0 : it;
-            const int nrows = fh->nrows, cofs = fh->cofs;
+            const int nrows = fh->nrows;
             const int m = (int)(((float)j + 0.5f) * fh->inv_nrows), row = j - m * nrows;
-            const float *src = rwin + (size_t)st * SF + row * RP + kFacItem * m;
-            float *dst = hbuf + (size_t)(f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
-            const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
-            switch (cofs) {
-                case 0: row_item<0, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                case 1: row_item<1, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                case 2: row_item<2, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
-                default: row_item<3, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+            const E *src = rwin + (size_t)st * SF * EPF + row * RP + kFacItem * m;
+            float *dst = hbuf + (size_t)(QG ? 0 : f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
+            if constexpr (k16) {
+                // the taps carry the frame's scale of a 16-bit weighted stack
+                // (a power of two: u_x * beta is exact)
+                const float bt = p.beta ? p.beta[f] : 1.f;
+                const float ux0 = fh->ux[0] * bt, ux1 = fh->ux[1] * bt, ux2 = fh->ux[2] * bt,
+                            ux3 = fh->ux[3] * bt, ux4 = fh->ux[4] * bt;
+                switch (fh->cofs8) {
+                    case 0: row_item<0, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 1: row_item<1, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 2: row_item<2, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 3: row_item<3, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 4: row_item<4, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 5: row_item<5, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 6: row_item<6, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    default: row_item<7, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                }
+            } else {
+                const float ux0 = fh->ux[0], ux1 = fh->ux[1], ux2 = fh->ux[2], ux3 = fh->ux[3], ux4 = fh->ux[4];
+                switch (fh->cofs) {
+                    case 0: row_item<0, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 1: row_item<1, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    case 2: row_item<2, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                    default: row_item<3, TAPS>(src, dst, ux0, ux1, ux2, ux3, ux4); break;
+                }
             }
+        }
+    };
+
+    // phase planes of frame f: plane j row i = sum_b u_j(b) H(i + b), rows
+    // 0 .. nrows - 5, items of 8 rows x 2 columns dealt over all threads
+    // (consecutive threads on consecutive column pairs: conflict-free)
+    auto plane_frame = [&](int f) {
+        constexpr int PR = 8;  // rows per item
+        const unsigned char *fblk = record(f);
+        const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
+        const FacPlane *pl = reinterpret_cast<const FacPlane *>(fblk + sizeof(FacHdr) + (size_t)KT * sizeof(FacSlot));
+        constexpr int NCP = TW / 2;
+        const int nrows = fh->nrows, prow = nrows - 4, nrc = (prow + PR - 1) / PR;
+        const int n = fh->pad * nrc * NCP;
+        for (int it = threadIdx.x; it < n; it += blockDim.x) {
+            const int cp = it % NCP, rest = it / NCP, rc = rest % nrc, j = rest / nrc;
+            const float4 u4 = *reinterpret_cast<const float4 *>(pl[j].uy);
+            const float u[5] = {u4.x, u4.y, u4.z, u4.w, pl[j].uy[4]};
+            const float *src = hbuf + (size_t)(PR * rc) * HP + 2 * cp;
+            float *dst = pbuf + (size_t)j * BH * HP + (size_t)(PR * rc) * HP + 2 * cp;
+            float2 o[PR];
+#pragma unroll
+            for (int r = 0; r < PR; r++) o[r] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < PR + 4; i++) {
+                // rows past the frame's window hold nothing the stored rows use
+                const float2 h = PR * rc + i < nrows ? *reinterpret_cast<const float2 *>(src + i * HP)
+                                                     : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < 5; b++) {
+                    const int r = i - b;
+                    if (r >= 0 && r < PR) {
+                        o[r].x = fmaf(u[b], h.x, o[r].x);
+                        o[r].y = fmaf(u[b], h.y, o[r].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < PR; r++)
+                if (PR * rc + r < prow) *reinterpret_cast<float2 *>(dst + (size_t)r * HP) = o[r];
+        }
+    };
+    // the gather of frame f: each output adds its trajectory's plane value at
+    // the row the column pass would have started from
+    auto gather = [&](int f) {
+        if (!active) return;
+        const unsigned char *fblk = record(f);
+        const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
+        const float *col = pbuf + (size_t)fs->plane * BH * HP + (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x +
+                           2 * cp;
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            const float2 v = *reinterpret_cast<const float2 *>(col + r * HP);
+            blk[2 * r] += v.x;
+            blk[2 * r + 1] += v.y;
         }
     };
 
     bool bad = false;
     int s = 0;  // stage of frame t and its phase
     uint32_t par = 0;
-    for (int t = t0; t < t1; t += 2) {
+    if constexpr (QG) {
+        // one frame at a time: row pass -> barrier -> planes -> barrier ->
+        // gathers; the next row pass overwrites the row-pass buffer only after
+        // the barrier that ends every thread's plane work, and the next planes
+        // the plane buffers only after the barrier every thread reaches past
+        // its gathers
+        for (int t = t0; t < t1; t++) {
+            const bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
+            if (ready) row_pair(t, s, s, false);
+            if (__syncthreads_or(!ready)) {
+                bad = true;
+                break;
+            }
+            if (threadIdx.x == 0 && t + NS < t1) {
+                fence_proxy_async();
+                const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t));
+                issue(t + NS, s, fh->next_roy, fh->next_rox);
+            }
+            plane_frame(t);
+            __syncthreads();
+            gather(t);
+            if ((t - t0 + 1) % kFrameBlock == 0) {
+#pragma unroll
+                for (int r = 0; r < 32; r++) {
+                    acc[r] += blk[r];
+                    blk[r] = 0.f;
+                }
+            }
+            s = (s + 1 == NS) ? 0 : s + 1;
+            par = (s == 0) ? (par ^ 1u) : par;
+        }
+    }
+    for (int t = t0; t < t1 && !QG; t += 2) {  // column passes (the loop is empty for QG)
         const bool two = t + 1 < t1;
         const int s1 = (s + 1 == NS) ? 0 : s + 1;
         const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
@@ -333,18 +501,27 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     return true;
 }
 
-template <int TW, int TAPS>
+template <int TW, int TAPS, typename E>
 __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant__ CUtensorMap ymap,
                                                           const FacParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    fac_tile<TW, TAPS>(ymap, p, (long long)blockIdx.x, smem);
+    fac_tile<TW, TAPS, E>(ymap, p, (long long)blockIdx.x, smem);
+}
+
+// The factored numerator with phase planes (phase-quantised banks).
+template <int TW>
+__global__ void __launch_bounds__(512, 1) k_numerator_fac_planes(const __grid_constant__ CUtensorMap ymap,
+                                                                 const FacParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    fac_tile<TW, 5, float, true>(ymap, p, (long long)blockIdx.x, smem);
 }
 
 // Persistent factored numerator over a batch of searches: one CTA per SM
 // takes (search, tile, group) work entries from a global counter until the
 // list is exhausted, running the same per-tile code as k_numerator_fac.
-template <int TW>
+template <int TW, typename E>
 __global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMap *__restrict__ maps,
                                                                 const FacBatchItem *__restrict__ items,
                                                                 int n_items, long long total,
@@ -373,7 +550,7 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMa
         const FacParams &p = items[i].p;
         // the five-tap code: single-tap footprints give the same sums (zero
         // taps add exact zeros), so a batch of mixed tables needs one kernel
-        if (!fac_tile<TW, 5>(maps[i], p, w - items[i].cta_begin, smem)) break;
+        if (!fac_tile<TW, 5, E>(maps[i], p, w - items[i].cta_begin, smem)) break;
         __syncthreads();
     }
 }
@@ -450,9 +627,35 @@ int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P,
     return 0;
 }
 
-int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen) {
-    cudaError_t e = cudaFuncSetAttribute(tw == 64 ? k_numerator_fac_batch<64> : k_numerator_fac_batch<32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+
+typedef void (*FacBatchKernel)(const CUtensorMap *, const FacBatchItem *, int, long long, unsigned long long *);
+typedef void (*FacKernel)(const CUtensorMap, const FacParams);
+
+FacBatchKernel pick_fac_batch(int tw, int etype) {
+    if (etype == MF_BF16) return tw == 64 ? k_numerator_fac_batch<64, __nv_bfloat16> : k_numerator_fac_batch<32, __nv_bfloat16>;
+    if (etype == MF_F16) return tw == 64 ? k_numerator_fac_batch<64, __half> : k_numerator_fac_batch<32, __half>;
+    return tw == 64 ? k_numerator_fac_batch<64, float> : k_numerator_fac_batch<32, float>;
+}
+
+template <typename E>
+FacKernel pick_fac_e(int tw, int taps) {
+    return tw == 64 ? (taps == 1 ? k_numerator_fac<64, 1, E> : k_numerator_fac<64, 5, E>)
+                    : (taps == 1 ? k_numerator_fac<32, 1, E> : k_numerator_fac<32, 5, E>);
+}
+
+FacKernel pick_fac(int tw, int taps, int etype, bool planes) {
+    if (planes) return tw == 64 ? k_numerator_fac_planes<64> : k_numerator_fac_planes<32>;
+    if (etype == MF_BF16) return pick_fac_e<__nv_bfloat16>(tw, taps);
+    if (etype == MF_F16) return pick_fac_e<__half>(tw, taps);
+    return pick_fac_e<float>(tw, taps);
+}
+
+}  // namespace
+
+int fac_batch_attr(int tw, int etype, size_t smem, char *err, size_t errlen) {
+    cudaError_t e = cudaFuncSetAttribute(pick_fac_batch(tw, etype), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) {
         snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
         return (int)e;
@@ -461,10 +664,9 @@ int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen) {
 }
 
 int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, long long total,
-                      unsigned long long *counter, int tw, int warps, size_t smem, int grid, void *stream, char *err,
-                      size_t errlen) {
-    void (*kern)(const CUtensorMap *, const FacBatchItem *, int, long long, unsigned long long *) =
-        tw == 64 ? k_numerator_fac_batch<64> : k_numerator_fac_batch<32>;
+                      unsigned long long *counter, int tw, int etype, int warps, size_t smem, int grid, void *stream,
+                      char *err, size_t errlen) {
+    FacBatchKernel kern = pick_fac_batch(tw, etype);
     cudaError_t e;
     if (total <= 0 || grid <= 0) return 0;
     kern<<<grid, warps * 32, smem, (cudaStream_t)stream>>>(reinterpret_cast<const CUtensorMap *>(maps), items,
@@ -477,12 +679,10 @@ int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, 
     return 0;
 }
 
-int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int taps, int warps, size_t smem,
+int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int taps, int etype, int warps, size_t smem,
                 long long nblocks, void *stream, char *err, size_t errlen) {
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(tensor_map);
-    void (*kern)(const CUtensorMap, const FacParams) =
-        tw == 64 ? (taps == 1 ? k_numerator_fac<64, 1> : k_numerator_fac<64, 5>)
-                 : (taps == 1 ? k_numerator_fac<32, 1> : k_numerator_fac<32, 5>);
+    FacKernel kern = pick_fac(tw, taps, etype, p.npl > 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         snprintf(err, errlen, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));

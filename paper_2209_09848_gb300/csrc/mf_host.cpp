@@ -312,6 +312,9 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
         int spread_max = 0, G = 0;
         for (int kt = 1; kt <= 16; kt++) {
             if (t.forced_group && kt != t.forced_group) continue;
+            // phase planes: at most one per rounded y-phase (Q + 1 of them) or
+            // per trajectory of the CTA, whichever is fewer
+            const int npl = t.forced_kernel == 3 ? std::min(kt, t.phase_steps + 1) : 0;
             std::vector<Geo> geos;
             for (int tw : {32, 64}) {
                 if (t.forced_tw && tw != t.forced_tw) continue;
@@ -394,7 +397,7 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
                 if (bh > 256) continue;
                 int ns = 0;
                 for (int c = t.forced_stages ? t.forced_stages : mf::kFacMaxStages; c >= 2; c--) {
-                    if (mf::fac_smem_bytes(geo.tw, bh, c, kt) <= (size_t)mf::kSmemBudget &&
+                    if (mf::fac_smem_bytes(geo.tw, bh, c, kt, npl) <= (size_t)mf::kSmemBudget &&
                         (size_t)c * mf::fac_stage_floats(geo.tw, bh) * 4 >= (size_t)geo.th * geo.tw * 8) {
                         ns = c;
                         break;
@@ -451,6 +454,7 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
                     for (size_t i = 0; i < gmax; i++) p.seg_ref[gj * kt + i] = seg_ref[gj * gmax + i];
                 p.f_ns = ns;
                 p.f_bh = bh;
+                p.f_planes = npl;
                 p.cost = cost;
                 p.G = G;
                 p.members.assign((size_t)G * kt, -1);
@@ -528,6 +532,7 @@ struct HostLayouts {
     std::vector<unsigned char> blocks;
     std::vector<int32_t> segs;  // factored: [G][S][4]
     std::vector<mf::RunRec> runs;
+    std::vector<mf::DenBox> boxes;
     std::vector<int32_t> run_off;
     std::vector<float> wts;
 };
@@ -535,13 +540,13 @@ struct HostLayouts {
 size_t layout_bytes(const mf_prf_table *t, const HostLayouts &h) {
     return h.blocks.size() + h.hdr.size() * sizeof(mf::FrameHdr) + t->plan.members.size() * sizeof(int32_t) +
            h.segs.size() * sizeof(int32_t) + t->plan.seg_ref.size() * sizeof(int32_t) +
-           h.runs.size() * sizeof(mf::RunRec) +
+           h.runs.size() * sizeof(mf::RunRec) + h.boxes.size() * sizeof(mf::DenBox) +
            h.run_off.size() * sizeof(int32_t) + h.wts.size() * sizeof(float) + t->taps.size() * sizeof(double) +
            t->shifts.size() * sizeof(int32_t);
 }
 
 void general_layouts(mf_prf_table *t, HostLayouts &out);
-void fac_layouts(mf_prf_table *t, HostLayouts &out);
+bool fac_layouts(mf_prf_table *t, HostLayouts &out);
 void denominator_layouts(mf_prf_table *t, HostLayouts &out);
 
 // Plan the groups and build the layouts the kernels read: frame headers and
@@ -554,13 +559,14 @@ mf_status host_layouts(mf_prf_table *t, HostLayouts &out) {
         mf::Plan fp;
         factored = plan_factored(*t, fp);
         if (factored) t->plan = std::move(fp);
-        else if (t->forced_kernel == 2)
+        else if (t->forced_kernel >= 2)
             return fail(t->fx.empty() ? MF_EINVAL : MF_EUNSUPPORTED,
                         t->fx.empty() ? "the factored numerator needs a separable (Gaussian PRF) table"
                                       : "no factored layout holds these trajectories' frame windows");
     }
     if (factored) {
-        fac_layouts(t, out);
+        if (!fac_layouts(t, out))
+            return fail(MF_EUNSUPPORTED, "a frame needs more phase planes than the layout holds");
     } else {
         mf_status s = plan_groups(*t);
         if (s != MF_OK) return s;
@@ -625,7 +631,7 @@ void general_layouts(mf_prf_table *t, HostLayouts &out) {
 // window origin (rows from min s_y - 2, columns from s_x - 2 rounded down to
 // a multiple of 4 for the TMA box), the row-pass rows, u_x, and per slot u_y
 // and the slot's row offset in the row-pass buffer.
-void fac_layouts(mf_prf_table *t, HostLayouts &out) {
+bool fac_layouts(mf_prf_table *t, HostLayouts &out) {
     const int T = t->T;
     const mf::Plan &p = t->plan;
     const int kt = p.f_kt, S = p.f_seg;
@@ -655,7 +661,8 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
             h.pad = (int32_t)(sx - 2 - h.rox);  // column phase
         }
     }
-    const size_t bb = mf::fac_block_bytes(kt);
+    const int npl = p.f_planes;
+    const size_t bb = mf::fac_block_bytes(kt, npl);
     std::vector<unsigned char> blocks((size_t)p.G * T * bb, 0);
     for (int g = 0; g < p.G; g++) {
         const int k0 = p.members[(size_t)g * kt];
@@ -670,10 +677,14 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
                 fh.next_rox = hdr[(size_t)g * T + fn].rox;
             }
             fh.cofs = h.pad;
+            fh.cofs8 = (int32_t)(t->shifts[((size_t)k0 * T + f) * 2 + 0] - 2 - 8 * floor_div(
+                                     t->shifts[((size_t)k0 * T + f) * 2 + 0] - 2, 8));
             fh.nrows = h.nrows;
             fh.inv_nrows = 1.0f / (float)h.nrows;
             for (int a = 0; a < 5; a++) fh.ux[a] = (float)t->fx[((size_t)k0 * T + f) * 5 + a];
-            std::memcpy(b, &fh, sizeof fh);
+            // phase planes: the distinct column-pass taps among the slots
+            // (one per rounded y-phase present), in order of first use
+            std::vector<mf::FacPlane> planes;
             for (int w = 0; w < kt; w++) {
                 const int k = p.members[(size_t)g * kt + w];
                 mf::FacSlot fs;
@@ -682,9 +693,29 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
                     const size_t ktf = (size_t)k * T + f;
                     for (int c = 0; c < 5; c++) fs.uy[c] = (float)t->fy[ktf * 5 + c];
                     fs.oy = rel(g, w, f) - 2 - h.roy;
+                    if (npl > 0) {
+                        size_t j = 0;
+                        while (j < planes.size() && std::memcmp(planes[j].uy, fs.uy, sizeof fs.uy) != 0) j++;
+                        if (j == planes.size()) {
+                            mf::FacPlane pl;
+                            std::memset(&pl, 0, sizeof pl);
+                            std::memcpy(pl.uy, fs.uy, sizeof pl.uy);
+                            planes.push_back(pl);
+                        }
+                        fs.plane = (int32_t)j;
+                    }
                 }
                 std::memcpy(b + sizeof fh + (size_t)w * sizeof fs, &fs, sizeof fs);
             }
+            if (npl > 0) {
+                // the bank rounds every phase to one of Q + 1 values, so a
+                // frame never needs more than the planner allowed
+                if ((int)planes.size() > npl) return false;
+                fh.pad = (int32_t)planes.size();
+                std::memcpy(b + sizeof fh + (size_t)kt * sizeof(mf::FacSlot), planes.data(),
+                            planes.size() * sizeof(mf::FacPlane));
+            }
+            std::memcpy(b, &fh, sizeof fh);
         }
     }
     // per (group, segment): first frame, end frame, min s_y, spread
@@ -700,6 +731,7 @@ void fac_layouts(mf_prf_table *t, HostLayouts &out) {
     out.hdr = std::move(hdr);
     out.blocks = std::move(blocks);
     out.segs = std::move(segs);
+    return true;
 }
 
 // Denominator layout: constant-shift runs of the collapsed kernels.
@@ -803,6 +835,48 @@ void denominator_layouts(mf_prf_table *t, HostLayouts &out) {
     run_off[K] = (int32_t)runs.size();
     t->n_seg = (int)runs.size();
     t->g_nnz = nnz_total;
+    // bounding boxes for the staged denominator, and its tile height: the
+    // tallest of 32, 16, 8 rows whose largest lambda box fits shared memory
+    std::vector<mf::DenBox> boxes(K);
+    int rows_max = 1, cols_max = 4, nw_max = 4, nr_max = 1;
+    for (int k = 0; k < K; k++) {
+        mf::DenBox b{};
+        const int r0 = run_off[k], r1 = run_off[k + 1];
+        if (r1 > r0) {
+            int dy0 = INT32_MAX, dy1 = INT32_MIN, x0 = INT32_MAX, x1 = INT32_MIN;
+            for (int r = r0; r < r1; r++) {
+                dy0 = std::min(dy0, runs[r].dy);
+                dy1 = std::max(dy1, runs[r].dy);
+                x0 = std::min(x0, runs[r].x0);
+                x1 = std::max(x1, runs[r].x0 + 4 * runs[r].nch);
+            }
+            b.dy0 = dy0;
+            b.rows = dy1 - dy0 + 1;
+            b.x0 = x0;
+            b.cols = x1 - x0;
+            b.w0 = runs[r0].woff;
+            b.nw = runs[r1 - 1].woff + 4 * runs[r1 - 1].nch - b.w0;
+        } else {
+            b.rows = 1;
+            b.cols = 4;
+        }
+        rows_max = std::max(rows_max, b.rows);
+        cols_max = std::max(cols_max, b.cols);
+        nw_max = std::max(nw_max, b.nw);
+        nr_max = std::max(nr_max, run_off[k + 1] - run_off[k]);
+        boxes[k] = b;
+    }
+    t->den_th = 0;
+    t->den_smem = 0;
+    for (int th : {32, 16, 8}) {
+        const size_t sm = mf::den_box_smem(th, rows_max, cols_max, nw_max, nr_max);
+        if (sm <= (size_t)mf::kSmemBudget) {
+            t->den_th = th;
+            t->den_smem = sm;
+            break;
+        }
+    }
+    out.boxes = std::move(boxes);
     out.runs = std::move(runs);
     out.run_off = std::move(run_off);
     out.wts = std::move(wts);
@@ -821,6 +895,7 @@ mf_status finish_table(mf_prf_table *t) {
         blk.add(&t->d_refs, t->plan.seg_ref.data(), t->plan.seg_ref.size());
     }
     blk.add(&t->d_runs, h.runs.data(), h.runs.size());
+    blk.add(&t->d_boxes, h.boxes.data(), h.boxes.size());
     blk.add(&t->d_run_off, h.run_off.data(), h.run_off.size());
     blk.add(&t->d_wts, h.wts.data(), h.wts.size());
     blk.add(&t->d_taps64, t->taps.data(), t->taps.size());
@@ -852,6 +927,8 @@ void fill_info(const mf_prf_table *t, mf_table_info *info) {
     info->stages = fac ? t->plan.f_ns : mf::kStages;
     info->time_segments = fac ? t->plan.f_seg : 1;
     info->taps = fac ? t->plan.f_taps : 5;
+    info->den_tile_h = t->den_th;
+    info->phase_planes = fac ? t->plan.f_planes : 0;
     info->device_bytes = (int64_t)t->device_bytes;
 }
 
@@ -872,6 +949,7 @@ void free_device(mf_prf_table *t) {
     t->d_segs = nullptr;
     t->d_refs = nullptr;
     t->d_runs = nullptr;
+    t->d_boxes = nullptr;
     t->d_run_off = nullptr;
     t->d_wts = nullptr;
     t->d_taps64 = nullptr;
@@ -930,23 +1008,27 @@ long long fac_ctas(const mf_prf_table &tab, int64_t H, int64_t W, int seg) {
     return (H + spread + p.f_th - 1) / p.f_th * tiles_x * p.G;
 }
 
-WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab) {
+WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, int32_t dtype, const mf_prf_table *tab) {
     WorkspaceLayout L;
     // zero border wide enough for every denominator read: shifts up to
     // max_abs_shift, footprint 2, run padding and the last partial row block
     L.pad = round_up((int64_t)tab->plan.max_abs_shift + 2 + 16, 4);
     L.lam_w = round_up(round_up(W, kDenCols) + 2 * L.pad + 32, 4);
     L.lam_h = round_up(H, 8) + 2 * L.pad;
-    L.y_pitch = round_up(W, 4);
+    // a bf16 / fp16 stack searched by the factored numerator keeps its
+    // weighted stack in its own 16-bit type (rows a multiple of 16 bytes)
+    L.ybytes = (dtype != MF_F32 && tab->plan.kernel == 2 && tab->plan.f_planes == 0) ? 2 : 4;
+    L.y_pitch = round_up(W, L.ybytes == 2 ? 8 : 4);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off = (size_t)round_up((int64_t)(off + bytes), 256);
         return o;
     };
-    L.status_off = take(sizeof(int));  // offset 0 (mf_search_status reads it there)
+    L.status_off = take(16);  // offset 0 (mf_search_status reads it there); bytes 8..11: largest lambda
     L.lam_off = take((size_t)L.lam_w * L.lam_h * sizeof(float));
-    L.y_off = take((size_t)T * H * L.y_pitch * sizeof(float));
+    L.y_off = take((size_t)T * H * L.y_pitch * L.ybytes);
+    L.beta_off = take((size_t)T * sizeof(float));
     L.isd_off = take((size_t)tab->K * H * W * sizeof(float));
     L.keys_off = take((size_t)H * W * sizeof(unsigned long long));
     L.planes_off = take(tab->plan.kernel == 2 ? (size_t)tab->K * H * W * sizeof(float) : 0);
@@ -990,6 +1072,7 @@ static mf_status build_gauss_host(const mf_prf_params *prf, const double *vx, co
     auto *t = new mf_prf_table;
     t->K = K;
     t->T = T;
+    t->phase_steps = prf->phase_steps;
     t->shifts.resize((size_t)K * T * 2);
     t->taps.resize((size_t)K * T * 25);
     t->fx.resize((size_t)K * T * 5);
@@ -1042,9 +1125,13 @@ static mf_status apply_opts(mf_prf_table *t, const mf_plan_opts *opts) {
         delete t;
         return fail(MF_EINVAL, "vec %d must be 0, 1, 2 or 4", opts->vec);
     }
-    if (opts->kernel < 0 || opts->kernel > 2) {
+    if (opts->kernel < 0 || opts->kernel > 3) {
         delete t;
-        return fail(MF_EINVAL, "kernel %d must be 0, 1 or 2", opts->kernel);
+        return fail(MF_EINVAL, "kernel %d must be 0, 1, 2 or 3", opts->kernel);
+    }
+    if (opts->kernel == 3 && t->phase_steps == 0) {
+        delete t;
+        return fail(MF_EINVAL, "kernel 3 (phase planes) needs a phase-quantised bank (phase_steps > 0)");
     }
     if (opts->group < 0 || opts->group > 16 || opts->tile_h < 0 || opts->tile_h % 32 != 0 ||
         (opts->tile_w != 0 && opts->tile_w != 32 && opts->tile_w != 64) || opts->stages < 0 ||
@@ -1186,7 +1273,7 @@ mf_status mf_search_workspace_size(const mf_stack *stack, const mf_prf_table *ta
     if (!table) return fail(MF_EINVAL, "table is NULL");
     if (!stack) return fail(MF_EINVAL, "stack is NULL");
     if (stack->T < 1 || stack->H < 0 || stack->W < 0) return fail(MF_EINVAL, "bad stack shape");
-    *bytes = mf::search_layout(stack->T, stack->H, stack->W, table).total;
+    *bytes = mf::search_layout(stack->T, stack->H, stack->W, stack->dtype, table).total;
     return ok();
 }
 
@@ -1203,7 +1290,7 @@ mf_status mf_search(const mf_stack *stack, const float *sigma, const uint8_t *ma
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != table->device)
         return fail(MF_EINVAL, "table lives on device %d, current device is %d", table->device, dev);
-    const mf::WorkspaceLayout L = mf::search_layout(stack->T, stack->H, stack->W, table);
+    const mf::WorkspaceLayout L = mf::search_layout(stack->T, stack->H, stack->W, stack->dtype, table);
     if (!workspace || workspace_bytes < L.total)
         return fail(MF_EINVAL, "workspace of %zu bytes needed, %zu given", L.total, workspace_bytes);
     if ((uintptr_t)workspace % 256 != 0) return fail(MF_EINVAL, "workspace must be 256-byte aligned");
@@ -1248,7 +1335,8 @@ size_t batch_item_offsets(const mf_batch *b, std::vector<size_t> *offs) {
     size_t off = 0;
     for (const auto &it : b->items) {
         if (offs) offs->push_back(off);
-        off += (size_t)round_up((int64_t)mf::search_layout(it.stack.T, it.stack.H, it.stack.W, it.table).total, 256);
+        off += (size_t)round_up(
+            (int64_t)mf::search_layout(it.stack.T, it.stack.H, it.stack.W, it.stack.dtype, it.table).total, 256);
     }
     return off;
 }
@@ -1296,6 +1384,8 @@ mf_status mf_batch_add(mf_batch *b, const mf_stack *stack, const float *sigma, c
     if (stack->H * stack->W == 0) return fail(MF_EINVAL, "empty stack in a batch");
     if (!sigma || !snr_max || !argmax) return fail(MF_EINVAL, "sigma, snr_max and argmax are required");
     if (table->device != b->device) return fail(MF_EINVAL, "table and batch live on different devices");
+    if (table->plan.kernel == 2 && table->plan.f_planes > 0)
+        return fail(MF_EUNSUPPORTED, "the phase-plane numerator (kernel 3) is not batched; use mf_search");
     b->items.push_back({*stack, sigma, mask, table, snr_max, argmax, snr_all});
     if (index) *index = (int32_t)b->items.size() - 1;
     return ok();
@@ -1322,7 +1412,8 @@ mf_status mf_batch_prepare(mf_batch *b, void *workspace, size_t workspace_bytes)
     b->ws = (char *)workspace;
     b->layouts.clear();
     b->args.clear();
-    for (const auto &it : b->items) b->layouts.push_back(mf::search_layout(it.stack.T, it.stack.H, it.stack.W, it.table));
+    for (const auto &it : b->items)
+        b->layouts.push_back(mf::search_layout(it.stack.T, it.stack.H, it.stack.W, it.stack.dtype, it.table));
     for (size_t i = 0; i < b->items.size(); i++) {
         const auto &it = b->items[i];
         b->args.push_back(mf::SearchArgs{&it.stack, it.sigma, it.mask, it.table, it.snr_max, it.argmax, it.snr_all,
@@ -1588,7 +1679,7 @@ HostSearchLayout host_search_layout(const mf_stack *st, const mf_prf_table *tabl
     size_t off = 0;
     // the search's own workspace first: its status slot is then at offset 0
     // of this workspace too (mf_search_status)
-    L.search_bytes = mf::search_layout(T, H, W, table).total;
+    L.search_bytes = mf::search_layout(T, H, W, st->dtype, table).total;
     L.search_off = off;
     off = align256(off + L.search_bytes);
     L.stack_off = off;

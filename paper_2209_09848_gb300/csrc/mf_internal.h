@@ -70,6 +70,26 @@ struct alignas(16) RunRec {
     int32_t dy, x0, nch, woff;  // woff: index of the first weight (multiple of 4)
 };
 
+// Bounding box of G_k's runs: row offsets dy0 .. dy0 + rows - 1, columns x0 ..
+// x0 + cols - 1 (x0 and cols multiples of 4), weights w0 .. w0 + nw - 1.  The
+// staged denominator copies, per (trajectory, tile of th x kDenBoxCols start
+// pixels), the lambda box those start pixels reach into shared memory.
+struct alignas(16) DenBox {
+    int32_t dy0, rows, x0, cols, w0, nw, pad[2];
+};
+constexpr int kDenBoxCols = 256;  // start pixels per row of a staged-denominator tile
+// Float4 chunk j of a staged lambda row sits at chunk j ^ ((j >> 3) & 1): the
+// eight lanes of a quarter warp, 8 columns (2 chunks) apart, then read eight
+// distinct 16-byte bank groups whatever the row's start.
+__host__ __device__ constexpr int den_chunk(int j) { return j ^ ((j >> 3) & 1); }
+// Row pitch in chunks for `cols` box columns, and the dynamic shared memory of
+// a tile th rows high.
+__host__ __device__ constexpr int den_pitch(int cols) { return ((kDenBoxCols + cols) / 4 + 1) / 2 * 2; }
+// Box, weights and the trajectory's runs (nruns RunRec) in shared memory.
+inline size_t den_box_smem(int th, int rows, int cols, int nw, int nruns) {
+    return (size_t)(th + rows - 1) * den_pitch(cols) * 16 + (size_t)(nw + 4) * 4 + (size_t)nruns * 16 + 64;
+}
+
 // ------------------------------------------------ factored numerator ---
 // When every footprint factors as W(a, b) = u_x(a) u_y(b) (the Gaussian PRF
 // tables do: the pixel-integrated Gaussian is a product of two erf
@@ -89,16 +109,30 @@ struct alignas(16) FacHdr {
     int32_t nrows;               // row-pass rows this frame needs
     float ux[5];                 // u_x(a), a = -2..2
     float inv_nrows;             // 1 / nrows, rounded to FP32 (splits row-pass items)
-    int32_t pad[2];
+    int32_t cofs8;               // the same for a window starting at a multiple of 8 columns (0..7):
+                                 // 16-bit stacks, whose TMA boxes start at 16-byte boundaries
+    int32_t pad;
 };
 static_assert(sizeof(FacHdr) == 48, "FacHdr is 48 bytes");
 struct alignas(16) FacSlot {
-    float uy[5];  // u_y(b), b = -2..2
-    int32_t oy;   // row-pass row of (tile row 0 + s_y - 2)
-    int32_t pad[2];
+    float uy[5];    // u_y(b), b = -2..2
+    int32_t oy;     // row-pass row of (tile row 0 + s_y - 2)
+    int32_t plane;  // phase planes: the plane of this slot's rounded y-phase at this frame
+    int32_t pad;
 };
 static_assert(sizeof(FacSlot) == 32, "FacSlot is 32 bytes");
-__host__ __device__ inline size_t fac_block_bytes(int kt) { return sizeof(FacHdr) + (size_t)kt * sizeof(FacSlot); }
+// Phase planes (the precompute-then-gather numerator of a phase-quantised
+// bank): the column-pass taps of one rounded y-phase present among a CTA's
+// trajectories at a frame.  A frame block then ends with `npl` of these and
+// its FacHdr.pad holds how many are in use.
+struct alignas(16) FacPlane {
+    float uy[5];
+    int32_t pad[3];
+};
+static_assert(sizeof(FacPlane) == 32, "FacPlane is 32 bytes");
+__host__ __device__ inline size_t fac_block_bytes(int kt, int npl = 0) {
+    return sizeof(FacHdr) + (size_t)kt * sizeof(FacSlot) + (size_t)npl * sizeof(FacPlane);
+}
 // Row-pass outputs per row: tile_w, in items of 16 (the column phase 0..3
 // is applied when the row pass reads the window, so the column pass reads
 // aligned columns); an item reads 24 window values from a 16-aligned start.
@@ -109,22 +143,33 @@ __host__ __device__ constexpr int fac_hcols(int tw) { return tw; }
 __host__ __device__ constexpr int fac_odd4(int n) { return (n / 4) % 2 ? n : n + 4; }
 __host__ __device__ constexpr int fac_hpitch(int tw) { return fac_odd4(fac_hcols(tw)); }
 __host__ __device__ constexpr int fac_rpitch(int tw) { return fac_odd4(fac_hcols(tw) + 8); }
+// 16-bit weighted stacks: the window starts at a multiple of 8 columns (16
+// bytes), an item reads 32 values (4 x 128 bits) from a 16-aligned start, and
+// the row pitch is an odd multiple of 8 values (16 bytes) for the same
+// conflict-free 128-bit accesses.
+__host__ __device__ constexpr int fac_odd8(int n) { return (n / 8) % 2 ? n : n + 8; }
+__host__ __device__ constexpr int fac_rpitch16(int tw) { return fac_odd8(fac_hcols(tw) + 16); }
 constexpr int kFacMaxStages = 6;
 // Frame records arrive in chunks of kFacRecordChunk frames (one bulk copy per
 // chunk, two chunk buffers); a chunk buffer is refilled while frame t + stages
 // is issued, so kFacRecordChunk >= kFacMaxStages keeps frame t's chunk intact.
 constexpr int kFacRecordChunk = 8;
 static_assert(kFacRecordChunk >= kFacMaxStages, "record chunks must outlive the frames in flight");
-// Floats of one window stage, rounded to 128 bytes (TMA destination alignment).
+// Floats of one window stage, rounded to 128 bytes (TMA destination alignment);
+// a stage of a 16-bit stack (bh x fac_rpitch16 values) is never larger.
 __host__ __device__ constexpr int fac_stage_floats(int tw, int bh) { return (bh * fac_rpitch(tw) + 31) / 32 * 32; }
+static_assert(2 * fac_rpitch16(32) <= 4 * fac_rpitch(32) && 2 * fac_rpitch16(64) <= 4 * fac_rpitch(64),
+              "a 16-bit window fits the stage of a 32-bit one");
 // Row-pass buffers: the CTA makes the row passes of two frames, meets at one
 // barrier, then runs both column passes; the next pair writes the other two
 // buffers, so one barrier per two frames orders writes and reuse.
 constexpr int kFacHBufs = 4;
-inline size_t fac_smem_bytes(int tw, int bh, int ns, int kt) {
+// With phase planes (npl > 0) a CTA makes one frame at a time: one row-pass
+// buffer, then npl planes over the window, then the gathers.
+inline size_t fac_smem_bytes(int tw, int bh, int ns, int kt, int npl = 0) {
     return 1024 + (size_t)ns * fac_stage_floats(tw, bh) * sizeof(float) +
-           (size_t)kFacHBufs * bh * fac_hpitch(tw) * sizeof(float) +
-           2 * (size_t)kFacRecordChunk * fac_block_bytes(kt) +
+           (size_t)(npl > 0 ? 1 + npl : kFacHBufs) * bh * fac_hpitch(tw) * sizeof(float) +
+           2 * (size_t)kFacRecordChunk * fac_block_bytes(kt, npl) +
            (size_t)ns * (sizeof(uint64_t) + sizeof(int)) + sizeof(int) + 64;
 }
 
@@ -139,6 +184,7 @@ struct Plan {
     // members' spread there; per (group, segment, slot) that member's s_y
     int f_seg = 1;
     int f_taps = 5;      // factored footprint taps per axis: 5, or 1 (single centre tap)
+    int f_planes = 0;    // phase planes per frame (precompute-then-gather numerator), 0: column passes
     std::vector<int32_t> seg_t0;      // f_seg + 1
     std::vector<int32_t> seg_qy;      // G * f_seg * 2: (min s_y, spread)
     std::vector<int32_t> seg_ref;     // G * f_seg * kt, INT32_MIN for an empty slot
@@ -170,7 +216,7 @@ inline size_t numerator_smem_bytes(int S, int BH, int kt) {
 }
 
 inline size_t Plan::smem() const {
-    return kernel == 2 ? fac_smem_bytes(f_tw, f_bh, f_ns, f_kt) : numerator_smem_bytes(S, BH, kt());
+    return kernel == 2 ? fac_smem_bytes(f_tw, f_bh, f_ns, f_kt, f_planes) : numerator_smem_bytes(S, BH, kt());
 }
 
 }  // namespace mf
@@ -187,7 +233,8 @@ struct mf_prf_table {
     std::vector<double> vx, vy;   // K
     mf::Plan plan;
     int forced_segments = 0;  // factored time segments, 0: automatic
-    int forced_kernel = 0;  // 0: automatic, 1: general, 2: factored
+    int forced_kernel = 0;  // 0: automatic, 1: general, 2: factored, 3: factored with phase planes
+    int phase_steps = 0;    // Q of a phase-quantised bank (0: exact phases)
     int forced_group = 0, forced_th = 0, forced_tw = 0, forced_stages = 0;  // factored geometry, 0: automatic
     int forced_shape = -1;  // -1: cost model
     int forced_vec = 0;     // 0: default
@@ -204,6 +251,9 @@ struct mf_prf_table {
     int32_t *d_refs = nullptr;           // factored: [G][S][kt] s_y of each slot at the segment's first frame
     mf::FrameHdr *d_hdr = nullptr;       // [G][T]
     mf::RunRec *d_runs = nullptr;        // [n_seg]
+    mf::DenBox *d_boxes = nullptr;       // [K] staged denominator: G_k's bounding box
+    int den_th = 0;                      // staged denominator tile rows (0: the unstaged kernel)
+    size_t den_smem = 0;                 // its dynamic shared memory
     int32_t *d_run_off = nullptr;        // [K + 1]
     float *d_wts = nullptr;              // run weights
     double *d_taps64 = nullptr;          // [K][T][25]
@@ -215,15 +265,20 @@ namespace mf {
 // The first 256 bytes of a search workspace hold the search's status slot:
 // 0, or the code of a bounded wait of that search that gave up (its kernels
 // write and read this slot only, so a failure stays with its own search).
+// The weighted stack y is FP32, or 16-bit (the stack's own type) when the
+// stack is bf16 / fp16 and the factored numerator reads it; y_t = beta_t *
+// stored value, beta [T] FP32 (bf16: 1; fp16: a power of two per frame).
+// Bytes 8..11 of the status area hold the largest lambda (fp16 scales).
 struct WorkspaceLayout {
-    size_t status_off, lam_off, y_off, isd_off, keys_off, planes_off, total;
+    size_t status_off, lam_off, y_off, beta_off, isd_off, keys_off, planes_off, total;
+    int ybytes;        // 4 or 2
     int64_t pad;       // zero border of the padded lambda image
     int64_t lam_w;     // padded lambda row pitch
     int64_t lam_h;
     int64_t y_pitch;   // weighted-stack row pitch (floats, multiple of 4)
 };
 
-WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, const mf_prf_table *tab);
+WorkspaceLayout search_layout(int64_t T, int64_t H, int64_t W, int32_t dtype, const mf_prf_table *tab);
 
 struct SearchArgs {
     const mf_stack *stack;
@@ -345,8 +400,10 @@ struct FacParams {
     const int32_t *segs;          // [G][S][4] first frame, end frame, min s_y, spread
     const int32_t *refs;          // [G][S][kt] s_y of each slot at the segment's first frame
     float *plane;                 // [K][H][W] numerator: segment 0 stores, later segments add
-    int *status;                  // device status word
+    int *status;                  // the search's status slot
+    const float *beta;            // [T] scale of a 16-bit weighted stack, or null (1)
     int T, G, kt, th, bh, ns, S, K;
+    int npl;                      // phase planes per frame block (0: column passes)
     int seg;                      // the segment this launch computes
     int warps;                    // warps of the layout (a batched launch may have more)
     int64_t H, W;
@@ -367,13 +424,14 @@ struct FacBatchItem {
     long long cta_begin;  // first entry of this search in the batch's work list
 };
 // Shared-memory limit of the persistent kernel (set once, outside capture).
-int fac_batch_attr(int tw, size_t smem, char *err, size_t errlen);
+// etype: element type of the weighted stack, an mf_dtype (MF_F32, MF_BF16, MF_F16).
+int fac_batch_attr(int tw, int etype, size_t smem, char *err, size_t errlen);
 int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, long long total,
-                      unsigned long long *counter, int tw, int warps, size_t smem, int grid, void *stream, char *err,
-                      size_t errlen);
+                      unsigned long long *counter, int tw, int etype, int warps, size_t smem, int grid, void *stream,
+                      char *err, size_t errlen);
 // taps: 5, or 1 when every footprint is a single centre tap (the shift-stack
 // filter), which runs the row and column passes on the centre tap only.
-int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int taps, int warps, size_t smem,
+int fac_enqueue(const void *tensor_map, const FacParams &p, int tw, int taps, int etype, int warps, size_t smem,
                 long long nblocks, void *stream, char *err, size_t errlen);
 
 // Record an error message for mf_last_error() and return the status.

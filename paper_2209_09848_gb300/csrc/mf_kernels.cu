@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <type_traits>
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -57,12 +58,13 @@ __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(
 
 // ------------------------------------------------------------- lambda ---
 
+// Also the largest lambda, into *lmax_bits (cleared before; lambda >= 0, so
+// the float bits order as unsigned integers).
 __global__ void k_lambda(const float *__restrict__ sigma, const uint8_t *__restrict__ mask, int64_t H,
-                         int64_t W, int64_t pad, int64_t lw, int64_t lh, float *__restrict__ lam, int *status) {
+                         int64_t W, int64_t pad, int64_t lw, int64_t lh, float *__restrict__ lam,
+                         unsigned int *lmax_bits) {
     const int64_t n = lw * lh;
-    // the search's status slot starts clear (the kernels after this one in
-    // stream order write it only on a failure)
-    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+    float vmax = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t yy = i / lw - pad, xx = i % lw - pad;
         float v = 0.f;
@@ -73,15 +75,48 @@ __global__ void k_lambda(const float *__restrict__ sigma, const uint8_t *__restr
             if (!m && s > 0.f && isfinite(s)) v = (float)(1.0 / ((double)s * (double)s));
         }
         lam[i] = v;
+        vmax = fmaxf(vmax, v);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(lmax_bits, __float_as_uint(vmax));
 }
 
 // ------------------------------------------------------------- weight ---
 
-template <typename TIn>
+// y_t = lambda * (scale_t * r_t) in FP32; stored as FP32 (TOut = float) or
+// in the stack's own 16-bit type (TOut = TIn): bf16 as is (beta_t = 1), fp16
+// times 1 / beta_t, beta_t the power of two at or above lambda_max * scale_t,
+// so that no value overflows (|stored r| <= 65504) and the scaling is exact.
+// The thread of (frame t, row 0, first column quad) writes beta[t].
+__device__ __forceinline__ float fp16_frame_beta(float lmax, float sc, float *inv) {
+    const float x = lmax * sc;
+    if (!(x > 0.f)) {
+        *inv = 1.f;
+        return 1.f;
+    }
+    // x = 1.m * 2^(e - 127) <= 2^(e - 126): beta = 2^(e - 126), from the bits
+    const int e = min((int)((__float_as_uint(x) >> 23) & 0xFFu), 253);
+    *inv = __uint_as_float((uint32_t)(253 - e) << 23);  // 2^(126 - e)
+    return __uint_as_float((uint32_t)(e + 1) << 23);    // 2^(e - 126)
+}
+
+template <typename T>
+__device__ __forceinline__ T from_f32(float v);
+template <>
+__device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+template <typename TIn, typename TOut>
 __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rstride,
                          const float *__restrict__ scale, const float *__restrict__ lam, int64_t pad, int64_t lw,
-                         float *__restrict__ y, int64_t T, int64_t H, int64_t W, int64_t yp) {
+                         TOut *__restrict__ y, int64_t T, int64_t H, int64_t W, int64_t yp,
+                         const unsigned int *lmax_bits, float *__restrict__ beta) {
+    constexpr bool kHalfScaled = std::is_same<TOut, __half>::value;
+    const float lmax = kHalfScaled ? __uint_as_float(*lmax_bits) : 0.f;
     const int64_t wq = (W + 3) / 4;
     const int64_t n = T * H * wq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -90,6 +125,9 @@ __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rst
         const int64_t yy = rest % H;
         const int64_t t = rest / H;
         const float sc = scale ? scale[t] : 1.f;
+        float inv = 1.f, bt = 1.f;
+        if (kHalfScaled) bt = fp16_frame_beta(lmax, sc, &inv);
+        if (beta && yy == 0 && xq == 0) beta[t] = bt;
         const float *lrow = lam + (yy + pad) * lw + pad;
         const TIn *rrow = r + t * fstride + yy * rstride;
         float o[4];
@@ -97,8 +135,15 @@ __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rst
         for (int j = 0; j < 4; j++) {
             const int64_t x = xq * 4 + j;
             o[j] = (x < W) ? lrow[x] * (sc * to_f32(rrow[x])) : 0.f;
+            if (kHalfScaled) o[j] *= inv;  // a power of two: exact
         }
-        *reinterpret_cast<float4 *>(y + (t * H + yy) * yp + xq * 4) = make_float4(o[0], o[1], o[2], o[3]);
+        TOut *dst = y + (t * H + yy) * yp + xq * 4;
+        if (std::is_same<TOut, float>::value) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+            TOut q[4] = {from_f32<TOut>(o[0]), from_f32<TOut>(o[1]), from_f32<TOut>(o[2]), from_f32<TOut>(o[3])};
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(q);
+        }
     }
 }
 
@@ -175,6 +220,101 @@ __global__ void __launch_bounds__(256) k_denominator(const float *__restrict__ l
             for (int c = 0; c < 8; c++) {
                 const double dd = d[c] + (double)a[c];
                 const int64_t px = px0 + c;
+                if (px < W) isd[(int64_t)k * P + py * W + px] = dd > 0.0 ? rsqrtf((float)dd) : 0.f;
+            }
+        }
+    }
+}
+
+// The same sums from a staged box.  A CTA owns `th` rows x kDenBoxCols start
+// pixels of one trajectory k: it copies the lambda box its start pixels
+// reach through G_k (rows dy0 .., columns x0 .. of the box, plus the tile),
+// G_k's weights and its runs into shared memory, then each warp takes rows
+// of the tile and runs the same register-window loop as k_denominator over
+// shared memory (conflict-free 128-bit reads, see den_chunk) instead of the
+// L1 cache, whose 32-byte sectors the lanes' 16-byte reads 32 bytes apart
+// used only half of.  Same FP32 products, same FP64 accumulation.
+__global__ void __launch_bounds__(1024) k_den_box(const float *__restrict__ lam, int64_t lw, int64_t lh, int64_t pad,
+                                                 const RunRec *__restrict__ runs, const int32_t *__restrict__ run_off,
+                                                 const float *__restrict__ wts, const DenBox *__restrict__ boxes,
+                                                 int K, int64_t H, int64_t W, int nbx, int th,
+                                                 float *__restrict__ isd) {
+    extern __shared__ __align__(16) float4 dsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int64_t py0 = (int64_t)(blockIdx.x / nbx) * th;
+    const int64_t px0 = (int64_t)(blockIdx.x % nbx) * kDenBoxCols;
+    const int64_t P = H * W;
+    for (int k = blockIdx.y; k < K; k += gridDim.y) {
+        const DenBox bx = boxes[k];
+        const int R = th + bx.rows - 1, NC = (kDenBoxCols + bx.cols) / 4, PC = den_pitch(bx.cols);
+        const int r0 = run_off[k], nr = run_off[k + 1] - r0;
+        float4 *wsm = dsm + (size_t)R * PC;                           // weights after the box
+        RunRec *rsm = reinterpret_cast<RunRec *>(wsm + bx.nw / 4);    // then the runs
+        __syncthreads();                                               // the previous trajectory's reads are done
+        // lambda rows py0 + dy0 .. of the padded image (zero beyond its last row)
+        const int64_t gy0 = py0 + bx.dy0 + pad, gx0 = px0 + bx.x0 + pad;
+        for (int i = threadIdx.x; i < R * NC; i += blockDim.x) {
+            const int r = i / NC, j = i % NC;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gy0 + r < lh) v = __ldg(reinterpret_cast<const float4 *>(lam + (gy0 + r) * lw + gx0) + j);
+            dsm[(size_t)r * PC + den_chunk(j)] = v;
+        }
+        for (int i = threadIdx.x; i < bx.nw / 4; i += blockDim.x)
+            wsm[i] = __ldg(reinterpret_cast<const float4 *>(wts + bx.w0) + i);
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) rsm[i] = runs[r0 + i];
+        __syncthreads();
+        for (int y = warp; y < th; y += nwarp) {
+            const int64_t py = py0 + y;
+            if (py >= H) break;
+            double d[8];
+            float a[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                d[c] = 0.0;
+                a[c] = 0.f;
+            }
+            int taps = 0;
+            for (int r = 0; r < nr; r++) {
+                const RunRec rr = rsm[r];
+                const float4 *row = dsm + (size_t)(y + rr.dy - bx.dy0) * PC;
+                const int j0 = (rr.x0 - bx.x0) / 4 + 2 * lane;  // the lane's first chunk
+                const float4 *wp = wsm + (rr.woff - bx.w0) / 4;
+                float v[12];
+                {
+                    const float4 p0 = row[den_chunk(j0)], p1 = row[den_chunk(j0 + 1)];
+                    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+                    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+                }
+                for (int ch = 0; ch < rr.nch; ch += 3) {
+#pragma unroll
+                    for (int u = 0; u < 3; u++) {
+                        if (ch + u < rr.nch) {
+                            const float4 pn = row[den_chunk(j0 + ch + u + 2)];
+                            const int ns = ((u + 2) % 3) * 4;
+                            v[ns] = pn.x; v[ns + 1] = pn.y; v[ns + 2] = pn.z; v[ns + 3] = pn.w;
+                            const float4 w4 = wp[ch + u];
+                            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                            for (int i = 0; i < 4; i++)
+#pragma unroll
+                                for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[(4 * u + i + c) % 12], a[c]);
+                        }
+                    }
+                }
+                taps += rr.nch * 4;
+                if (taps >= kDenTaps) {
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                        d[c] += (double)a[c];
+                        a[c] = 0.f;
+                    }
+                    taps = 0;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const double dd = d[c] + (double)a[c];
+                const int64_t px = px0 + 8 * lane + c;
                 if (px < W) isd[(int64_t)k * P + py * W + px] = dd > 0.0 ? rsqrtf((float)dd) : 0.f;
             }
         }
@@ -678,13 +818,22 @@ int enqueue_pre(const SearchArgs &a, cudaStream_t stream, char *err, size_t errl
     const WorkspaceLayout &L = a.L;
     const int64_t T = st.T, H = st.H, W = st.W, P = H * W;
     float *lam = reinterpret_cast<float *>(a.ws + L.lam_off);
-    float *y = reinterpret_cast<float *>(a.ws + L.y_off);
+    void *y = a.ws + L.y_off;
+    float *beta = reinterpret_cast<float *>(a.ws + L.beta_off);
     float *isd = reinterpret_cast<float *>(a.ws + L.isd_off);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.ws + L.keys_off);
+    unsigned int *lmax = reinterpret_cast<unsigned int *>(a.ws + L.status_off + 8);
+    // the search's status slot and the lambda maximum start clear (the
+    // kernels after this in stream order write the slot only on a failure)
+    cudaError_t e0 = cudaMemsetAsync(a.ws + L.status_off, 0, 16, stream);
+    if (e0 != cudaSuccess) {
+        snprintf(err, errlen, "cudaMemsetAsync: %s", cudaGetErrorString(e0));
+        return (int)e0;
+    }
     {
         LaunchScope ls(kKLambda, stream);
-        k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(
-            a.sigma, a.mask, H, W, L.pad, L.lam_w, L.lam_h, lam, reinterpret_cast<int *>(a.ws + L.status_off));
+        k_lambda<<<grid_for(L.lam_w * L.lam_h, 256), 256, 0, stream>>>(a.sigma, a.mask, H, W, L.pad, L.lam_w,
+                                                                        L.lam_h, lam, lmax);
     }
     MF_CHECK_LAUNCH("k_lambda");
 
@@ -692,26 +841,48 @@ int enqueue_pre(const SearchArgs &a, cudaStream_t stream, char *err, size_t errl
     const int64_t fs = st.frame_stride, rs = st.row_stride;
     {
         LaunchScope ls(kKWeight, stream);
-        switch (st.dtype) {
-            case MF_F32:
-                k_weight<float><<<grid_for(nw, 256), 256, 0, stream>>>((const float *)st.data, fs, rs,
-                                                                       st.frame_scale, lam, L.pad, L.lam_w, y, T,
-                                                                       H, W, L.y_pitch);
-                break;
-            case MF_BF16:
-                k_weight<__nv_bfloat16><<<grid_for(nw, 256), 256, 0, stream>>>(
-                    (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, lam, L.pad, L.lam_w, y, T, H, W,
-                    L.y_pitch);
-                break;
-            default:
-                k_weight<__half><<<grid_for(nw, 256), 256, 0, stream>>>((const __half *)st.data, fs, rs,
-                                                                        st.frame_scale, lam, L.pad, L.lam_w, y,
-                                                                        T, H, W, L.y_pitch);
-                break;
-        }
+        const int gw = grid_for(nw, 256);
+        const bool y16 = L.ybytes == 2;
+        if (st.dtype == MF_F32)
+            k_weight<float, float><<<gw, 256, 0, stream>>>((const float *)st.data, fs, rs, st.frame_scale, lam, L.pad,
+                                                           L.lam_w, (float *)y, T, H, W, L.y_pitch, lmax, beta);
+        else if (st.dtype == MF_BF16 && y16)
+            k_weight<__nv_bfloat16, __nv_bfloat16><<<gw, 256, 0, stream>>>(
+                (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, lam, L.pad, L.lam_w, (__nv_bfloat16 *)y, T,
+                H, W, L.y_pitch, lmax, beta);
+        else if (st.dtype == MF_BF16)
+            k_weight<__nv_bfloat16, float><<<gw, 256, 0, stream>>>((const __nv_bfloat16 *)st.data, fs, rs,
+                                                                   st.frame_scale, lam, L.pad, L.lam_w, (float *)y,
+                                                                   T, H, W, L.y_pitch, lmax, beta);
+        else if (y16)
+            k_weight<__half, __half><<<gw, 256, 0, stream>>>((const __half *)st.data, fs, rs, st.frame_scale, lam,
+                                                             L.pad, L.lam_w, (__half *)y, T, H, W, L.y_pitch, lmax,
+                                                             beta);
+        else
+            k_weight<__half, float><<<gw, 256, 0, stream>>>((const __half *)st.data, fs, rs, st.frame_scale, lam,
+                                                            L.pad, L.lam_w, (float *)y, T, H, W, L.y_pitch, lmax,
+                                                            beta);
     }
     MF_CHECK_LAUNCH("k_weight");
-    {
+    if (tab.den_th > 0) {
+        // staged: one CTA per (tile of den_th x 256 start pixels, trajectory)
+        static_assert(kDenBoxCols == 256, "a warp covers 256 start pixels of a row");
+        const int th = tab.den_th;
+        const int nbx = (int)((W + kDenBoxCols - 1) / kDenBoxCols);
+        const int nby = (int)((H + th - 1) / th);
+        dim3 grid((unsigned)(nbx * nby), (unsigned)std::min(tab.K, 65535));
+        cudaError_t ea = cudaFuncSetAttribute(k_den_box, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)tab.den_smem);
+        if (ea != cudaSuccess) {
+            snprintf(err, errlen, "cudaFuncSetAttribute(k_den_box): %s", cudaGetErrorString(ea));
+            return (int)ea;
+        }
+        LaunchScope ls(kKDenominator, stream);
+        k_den_box<<<grid, 32 * th, tab.den_smem, stream>>>(
+            lam, L.lam_w, L.lam_h, L.pad, tab.d_runs, tab.d_run_off, tab.d_wts, tab.d_boxes, tab.K, H, W, nbx, th,
+            isd);
+        MF_CHECK_LAUNCH("k_den_box");
+    } else {
         const int nbx = (int)((W + kDenCols - 1) / kDenCols);
         const int nby = (int)((H + 7) / 8);
         dim3 grid((unsigned)(nbx * nby), (unsigned)std::min(tab.K, 65535));
@@ -779,12 +950,16 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     int rc = get_encode(err, errlen);
     if (rc) return rc;
     int *status = reinterpret_cast<int *>(a.ws + L.status_off);
-    float *y = reinterpret_cast<float *>(a.ws + L.y_off);
+    void *y = a.ws + L.y_off;
+    const bool y16 = L.ybytes == 2;
     cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
-    cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * 4, (cuuint64_t)(H * L.y_pitch * 4)};
-    cuuint32_t box[3] = {(cuuint32_t)fac_rpitch(pl.f_tw), (cuuint32_t)pl.f_bh, 1};
+    cuuint64_t strides[2] = {(cuuint64_t)L.y_pitch * L.ybytes, (cuuint64_t)(H * L.y_pitch * L.ybytes)};
+    cuuint32_t box[3] = {(cuuint32_t)(y16 ? fac_rpitch16(pl.f_tw) : fac_rpitch(pl.f_tw)), (cuuint32_t)pl.f_bh, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, y, dims, strides, box, estr,
+    const CUtensorMapDataType ty = !y16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                        : (st.dtype == MF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    CUresult cr = g_encode(map, ty, 3, y, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
@@ -798,9 +973,12 @@ int fac_params(const SearchArgs &a, CUtensorMap *map, FacParams *fp, long long *
     fp->refs = tab.d_refs;
     fp->plane = reinterpret_cast<float *>(a.ws + L.planes_off);
     fp->status = status;
+    // fp16 weighted stacks carry a power-of-two scale per frame; bf16 ones none
+    fp->beta = (y16 && st.dtype == MF_F16) ? reinterpret_cast<const float *>(a.ws + L.beta_off) : nullptr;
     fp->T = (int)T;
     fp->G = pl.G;
     fp->kt = pl.f_kt;
+    fp->npl = pl.f_planes;
     fp->th = pl.f_th;
     fp->bh = pl.f_bh;
     fp->ns = pl.f_ns;
@@ -883,9 +1061,9 @@ int launch_search(const SearchArgs &a, char *err, size_t errlen) {
         for (int j = 0; j < pl.f_seg; j++) {
             fp.seg = j;
             LaunchScope ls(kKNumerator, stream);
-            rc = fac_enqueue(&map, fp, pl.f_tw, pl.f_taps, pl.launch_warps(), pl.smem(), fac_ctas(*a.tab, a.stack->H,
-                                                                                       a.stack->W, j),
-                             stream, err, errlen);
+            rc = fac_enqueue(&map, fp, pl.f_tw, pl.f_taps, a.L.ybytes == 2 ? a.stack->dtype : MF_F32,
+                             pl.launch_warps(), pl.smem(), fac_ctas(*a.tab, a.stack->H, a.stack->W, j), stream, err,
+                             errlen);
             if (rc) return rc;
         }
         return enqueue_finalize(a, stream, err, errlen);
@@ -932,6 +1110,7 @@ struct BatchDevice {
     // layout needs
     struct FacGroup {
         int tw = 32;
+        int etype = MF_F32;        // element type of the weighted stacks
         int seg = 0;               // time segment (groups run in segment order)
         int first = 0, count = 0;  // range in d_fmaps / d_fitems
         long long total = 0;       // CTA work entries
@@ -1001,15 +1180,20 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
     int max_seg = 0;
     for (int i = 0; i < n; i++)
         if (items[i].tab->plan.kernel == 2) max_seg = std::max(max_seg, items[i].tab->plan.f_seg);
+    // one persistent launch per (segment, tile width, element type of the
+    // weighted stack)
     for (int j = 0; j < max_seg; j++) {
-        for (int tw : {32, 64}) {
+        for (int tw : {32, 64})
+        for (int et : {(int)MF_F32, (int)MF_BF16, (int)MF_F16}) {
             BatchDevice::FacGroup grp;
             grp.tw = tw;
+            grp.etype = et;
             grp.seg = j;
             grp.first = (int)fitems.size();
             for (int i = 0; i < n; i++) {
                 const Plan &pl = items[i].tab->plan;
-                if (pl.kernel != 2 || pl.f_tw != tw || j >= pl.f_seg) continue;
+                const int item_et = items[i].L.ybytes == 2 ? items[i].stack->dtype : MF_F32;
+                if (pl.kernel != 2 || pl.f_tw != tw || item_et != et || j >= pl.f_seg) continue;
                 CUtensorMap m;
                 FacBatchItem fi;
                 std::memset(&fi, 0, sizeof fi);
@@ -1065,17 +1249,18 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         batch_free(b);
         return (int)e;
     }
-    for (int tw : {32, 64}) {  // one attribute per kernel: the largest layout of that tile width
-        size_t smem = 0;
-        for (const auto &grp : b->fac)
-            if (grp.tw == tw) smem = std::max(smem, grp.smem);
-        if (smem == 0) continue;
-        const int rc = fac_batch_attr(tw, smem, err, errlen);
-        if (rc) {
-            batch_free(b);
-            return rc;
+    for (int tw : {32, 64})  // one attribute per kernel: the largest layout of that tile width and type
+        for (int et : {(int)MF_F32, (int)MF_BF16, (int)MF_F16}) {
+            size_t smem = 0;
+            for (const auto &grp : b->fac)
+                if (grp.tw == tw && grp.etype == et) smem = std::max(smem, grp.smem);
+            if (smem == 0) continue;
+            const int rc = fac_batch_attr(tw, et, smem, err, errlen);
+            if (rc) {
+                batch_free(b);
+                return rc;
+            }
         }
-    }
     *out = b;
     return 0;
 }
@@ -1120,7 +1305,8 @@ int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream_v
         const int grid = (int)std::min<long long>(grp.total, (long long)b->sms);
         LaunchScope ls(kKNumerator, stream);
         int rc = fac_batch_enqueue(b->d_fmaps + grp.first, b->d_fitems + grp.first, grp.count, grp.total,
-                                   b->d_fcounters + gi, grp.tw, grp.warps, grp.smem, grid, stream, err, errlen);
+                                   b->d_fcounters + gi, grp.tw, grp.etype, grp.warps, grp.smem, grid, stream, err,
+                                   errlen);
         if (rc) return rc;
     }
     for (int i = 0; i < n; i++) {

@@ -88,7 +88,7 @@ def footprint_bytes(req: Request, table) -> int:
     n = T * H * W * req.stack.element_size() + H * W * 4
     n += H * W if req.mask is not None else 0
     n += T * 4 if req.frame_scale is not None else 0
-    n += mf.search_workspace_size((T, H, W), table) + H * W * 8 + table.info()["device_bytes"]
+    n += mf.search_workspace_size((T, H, W), table, req.stack.dtype) + H * W * 8 + table.info()["device_bytes"]
     if req.k_top:
         n += mf.rescore_workspace_size(H, W, req.k_top) + req.k_top * mf.CANDIDATE_BYTES + 4
     return int(n)
@@ -221,7 +221,8 @@ class Server:
             sigma = req.sigma.to(dev, non_blocking=True)
             mask = None if req.mask is None else req.mask.to(dev, non_blocking=True)
             fs = None if req.frame_scale is None else req.frame_scale.to(dev, non_blocking=True)
-            ws = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
+            ws = torch.empty(mf.search_workspace_size((T, H, W), table, req.stack.dtype), dtype=torch.uint8,
+                             device=dev)
             snr_max = torch.empty((H, W), dtype=torch.float32, device=dev)
             argmax = torch.empty((H, W), dtype=torch.int32, device=dev)
             evk0 = torch.cuda.Event(enable_timing=True)

@@ -27,7 +27,7 @@ def test_flop_per_unit(bench):
 
 
 def test_peak_and_paper_rate(bench):
-    assert bench._fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench._fp32_peak_tflops(2070.0, sms=152) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
     assert bench.PAPER_RATE == pytest.approx(100 * 1000 * 2048 * 2048 / 300.0)
     assert bench.job_throughput(10.0, 4, 2.0) == 20.0
 

@@ -86,6 +86,16 @@ def test_batch_equals_individual_searches(mf, oracle):
     N, D = oracle.search_full(it["c"]["res"], lam, sh, tp)
     gm, ga, gall = b.outputs[0]
     check_search(gm.cpu().numpy(), ga.cpu().numpy(), gall.cpu().numpy(), N, D, oracle, label="batch item 0")
+    # and the bf16 item (factored numerator on the 16-bit weighted stack)
+    it = items[1]
+    assert it["table"].info()["kernel"] == 2
+    sh, tp = oracle.trajectory_table(it["vx"], it["vy"], it["data"].shape[0])
+    lam = oracle.inverse_variance(it["c"]["sigma"], it["c"]["mask"])
+    q, beta = oracle.weighted_stack16(it["data"].float().cpu().numpy(), it["c"]["sigma"], it["c"]["mask"], None,
+                                      "bf16")
+    N, D = oracle.search_weighted(q, beta, lam, sh, tp)
+    gm, ga, gall = b.outputs[1]
+    check_search(gm.cpu().numpy(), ga.cpu().numpy(), gall.cpu().numpy(), N, D, oracle, label="batch item 1 (bf16)")
     b.destroy()
 
 

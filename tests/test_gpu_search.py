@@ -79,22 +79,72 @@ def test_random_shapes(mf, oracle, T, H, W, K, seed, mask_frac, vmax, custom):
     check_search(smax, amax, sall, N, D, oracle, label="case %s" % ((T, H, W, K),))
 
 
-def test_frame_scale_and_half_precision_storage(mf, oracle):
+@pytest.mark.parametrize("T,H,W,grid,vmax,layout", [
+    (12, 48, 80, (3, 3), 0.3, {}),
+    (41, 203, 157, (5, 7), 0.45, {}),                                         # several tiles, ragged edges
+    (23, 70, 130, (4, 2), 0.3, dict(kernel=2, group=2, tile_w=64)),           # 64-column tiles
+    (40, 96, 100, (3, 3), 0.6, dict(kernel=2, segments=3)),                   # time segments
+])
+def test_frame_scale_and_half_precision_storage(mf, oracle, T, H, W, grid, vmax, layout):
+    # bf16 / fp16 stacks: the factored numerator reads the weighted stack in
+    # the stack's own 16-bit type (the precision form); the oracle forms that
+    # stack from its definition and the matched filter on it
+    from paper_2209_09848_gb300 import synth
+    c = synth.small_case(T, H, W, 7, mask_frac=0.01, movers=2)
+    vx, vy = synth.velocity_grid(*grid, -vmax, vmax)
+    table = mf.prf_table_create(vx, vy, T, **layout)
+    assert table.info()["kernel"] == 2
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "fp16")):
+        scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14).astype(np.float32) if dt == torch.float16 \
+            else np.exp(np.random.default_rng(T).uniform(-1, 1, T)).astype(np.float32)
+        q = torch.from_numpy(c["res"] / scale[:, None, None]).to(dt)
+        deq = q.float().numpy()  # the stored values
+        y16, beta = oracle.weighted_stack16(deq, c["sigma"], c["mask"], scale, name)
+        N, D = oracle.search_weighted(y16, beta, lam, sh, tp)
+        smax, amax, sall = _run(mf, deq, c["sigma"], c["mask"], table, frame_scale=scale, dtype=dt)
+        check_search(smax, amax, sall, N, D, oracle, label="%s %s" % (name, (T, H, W)))
+
+
+def test_half_precision_storage_general_kernel(mf, oracle):
+    # the general numerator keeps an FP32 weighted stack: it matches the
+    # oracle on the stored values exactly as the FP32 path does
     from paper_2209_09848_gb300 import synth
     T, H, W = 12, 48, 80
     c = synth.small_case(T, H, W, 7, mask_frac=0.01, movers=2)
     vx, vy = synth.velocity_grid(3, 3, -0.3, 0.3)
-    table = mf.prf_table_create(vx, vy, T)
+    table = mf.prf_table_create(vx, vy, T, kernel=1)
     sh, tp = oracle.trajectory_table(vx, vy, T)
     lam = oracle.inverse_variance(c["sigma"], c["mask"])
     for dt in (torch.bfloat16, torch.float16):
         scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14).astype(np.float32) if dt == torch.float16 \
             else np.ones(T, np.float32)
         q = torch.from_numpy(c["res"] / scale[:, None, None]).to(dt)
-        deq = q.float().numpy()  # the values the GPU reads, before scaling
+        deq = q.float().numpy()
         N, D = oracle.search_full(deq, lam, sh, tp, frame_scale=scale.astype(np.float64))
-        smax, amax, sall = _run(mf, q.float().numpy(), c["sigma"], c["mask"], table, frame_scale=scale, dtype=dt)
+        smax, amax, sall = _run(mf, deq, c["sigma"], c["mask"], table, frame_scale=scale, dtype=dt)
         check_search(smax, amax, sall, N, D, oracle, label=str(dt))
+
+
+def test_half_precision_shift_stack(mf, oracle):
+    # single-tap footprints read the 16-bit stage directly (no row pass)
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 30, 77, 101
+    c = synth.small_case(T, H, W, 19, mask_frac=0.02, movers=2)
+    vx, vy = synth.velocity_grid(4, 3, -0.4, 0.4)
+    table = mf.prf_table_create(vx, vy, T, kind=2)
+    assert table.info()["taps"] == 1
+    sh, tp = oracle.trajectory_table(vx, vy, T, kind=2)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "fp16")):
+        scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 12).astype(np.float32)
+        q = torch.from_numpy(c["res"] / scale[:, None, None]).to(dt)
+        deq = q.float().numpy()
+        y16, beta = oracle.weighted_stack16(deq, c["sigma"], c["mask"], scale, name)
+        N, D = oracle.search_weighted(y16, beta, lam, sh, tp)
+        smax, amax, sall = _run(mf, deq, c["sigma"], c["mask"], table, frame_scale=scale, dtype=dt)
+        check_search(smax, amax, sall, N, D, oracle, label="shift-stack " + name)
 
 
 def test_velocity_zero_and_single_pixel_frames(mf, oracle):
@@ -157,6 +207,24 @@ def test_unusable_sigma_is_masked(mf, oracle):
                                   cands["k"].astype(np.int32))
     ok = Dc > 0
     np.testing.assert_allclose(cands["snr"][ok], Nc[ok] / np.sqrt(Dc[ok]), rtol=1e-9, atol=1e-12)
+
+
+def test_denominator_staged_and_unstaged(mf, oracle):
+    # the paper's slow movers: each CTA stages the lambda box its trajectory
+    # reaches in shared memory; movers so fast that the box cannot fit go
+    # through the unstaged denominator -- both match the oracle
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 30, 70, 290
+    c = synth.small_case(T, H, W, 23, mask_frac=0.03, movers=2)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    for vx, vy, staged in (([0.3, -0.2, 0.1, 0.0], [0.1, 0.25, -0.3, 0.05], True),
+                           ([8.0, -7.0, 0.3], [8.0, 6.0, -0.2], False)):
+        table = mf.prf_table_create(vx, vy, T)
+        assert (table.info()["den_tile_h"] > 0) == staged
+        sh, tp = oracle.trajectory_table(vx, vy, T)
+        N, D = oracle.search_full(c["res"], lam, sh, tp)
+        smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+        check_search(smax, amax, sall, N, D, oracle, label="staged denominator %s" % staged)
 
 
 def test_empty_frame_is_a_no_op(mf):

@@ -389,6 +389,92 @@ def test_unusable_sigma_counts_as_masked(oracle):
     assert np.all(np.isfinite(N1)) and np.all(np.isfinite(D1))
 
 
+# ------------------------------------------------- precision form (16-bit) --
+
+def test_bf16_rounding_is_round_to_nearest_even(oracle):
+    # the oracle's bf16 rounding (written from the definition) against the
+    # library conversion of torch, on random values, exact ties with an odd
+    # and an even kept part, negatives, zeros and subnormals
+    torch = pytest.importorskip("torch")
+    g = _rng(41)
+    x = (g.standard_normal(20000) * np.exp(g.uniform(-30, 30, 20000))).astype(np.float32)
+    ties = np.array([0x3F808000, 0x3F818000, 0xBF808000, 0xBF818000, 0x00018000, 0x7F7F7FFF], np.uint32)
+    x = np.concatenate([x, ties.view(np.float32), np.array([0.0, -0.0, 1e-42, -1e-42], np.float32)])
+    got = oracle.round_to_bf16(x)
+    want = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    # ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and goes to the even 1
+    assert got[-10] == np.float32(1.0) and got[-9] == np.float32(1.0 + 2.0 ** -6)
+
+
+def test_weighted_stack16_exact_when_representable(oracle):
+    # lambda and the frame scales powers of two and small integer residuals:
+    # lambda * alpha * r is exact in 16 bits, so the stored stack times beta
+    # equals it and the weighted search equals the plain one exactly
+    g = _rng(42)
+    T, H, W = 7, 19, 23
+    r = g.integers(-60, 61, size=(T, H, W)).astype(np.float32)
+    sigma = (2.0 ** g.integers(-2, 3, size=(H, W))).astype(np.float32)
+    mask = (g.random((H, W)) < 0.05).astype(np.uint8)
+    alpha = (2.0 ** g.integers(-3, 4, size=T)).astype(np.float32)
+    vx = np.array([0.3, -0.25, 0.0])
+    vy = np.array([0.1, 0.2, -0.35])
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma, mask)
+    N0, D0 = oracle.search_full(r, lam, shifts, taps, frame_scale=alpha.astype(np.float64))
+    for dt in ("bf16", "fp16"):
+        q, beta = oracle.weighted_stack16(r, sigma, mask, alpha, dt)
+        y = lam[None] * alpha[:, None, None, ] * r.astype(np.float64)
+        np.testing.assert_array_equal(q * beta[:, None, None], y)
+        N, D = oracle.search_weighted(q, beta, lam, shifts, taps)
+        np.testing.assert_allclose(N, N0, rtol=1e-13, atol=1e-13)
+        np.testing.assert_array_equal(D, D0)
+
+
+def test_fp16_frame_scale_bounds(oracle):
+    # beta_t is the power of two with beta / 2 < lambda_max * alpha_t <= beta:
+    # the largest storable residual at the largest weight stays finite
+    g = _rng(43)
+    T, H, W = 9, 12, 14
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    alpha = np.exp(g.uniform(-12, 12, T)).astype(np.float32)
+    r = np.full((T, H, W), 65504.0, np.float32)
+    q, beta = oracle.weighted_stack16(r, sigma, None, alpha, "fp16")
+    lam = oracle.inverse_variance(sigma)
+    x = (np.float32(lam.astype(np.float32).max()) * alpha).astype(np.float64)
+    m, e = np.frexp(beta)
+    assert np.all(m == 0.5)  # powers of two
+    assert np.all((beta / 2 < x) & (x <= beta))
+    assert np.all(np.isfinite(q)) and np.abs(q).max() <= 65504
+
+
+def test_weighted_stack16_rounding_error_bound(oracle):
+    # each stored value is the weighted residual to within half a unit in
+    # the last place of its 16-bit type: relative 2^-8 for bf16 (8
+    # significant bits), 2^-11 for normal fp16 values (11 bits), so N moves
+    # by at most that times sum |W y|
+    g = _rng(44)
+    T, H, W = 10, 30, 33
+    r = (g.standard_normal((T, H, W)) * 40).astype(np.float32)
+    sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
+    alpha = np.exp(g.uniform(-2, 2, T)).astype(np.float32)
+    vx = np.array([0.2, -0.4])
+    vy = np.array([0.15, 0.05])
+    shifts, taps = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(sigma)
+    y = lam.astype(np.float32)[None] * (alpha[:, None, None] * r)
+    N0, _ = oracle.search_full(r, lam, shifts, taps, frame_scale=alpha.astype(np.float64))
+    Nabs, _ = oracle.search_full(np.abs(y), np.ones((H, W)), shifts, np.abs(taps))
+    for dt, u in (("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)):
+        q, beta = oracle.weighted_stack16(r, sigma, None, alpha, dt)
+        big = np.abs(y) > 1e-3 * beta[:, None, None]  # fp16: normal range
+        rel = np.abs(q * beta[:, None, None] - y.astype(np.float64)) / np.abs(y)
+        assert rel[big].max() <= u * (1 + 1e-6)
+        assert rel[big].max() > u / 4  # the bound is attained in order of magnitude
+        N, _ = oracle.search_weighted(q, beta, lam, shifts, taps)
+        assert np.all(np.abs(N - N0) <= (u + 1e-6) * Nabs + 1e-12)
+
+
 # ------------------------------------------------------------ statistics --
 
 def test_pure_noise_snr_is_standard_normal(oracle):

@@ -134,7 +134,7 @@ def _oracle_requests(seed=21):
                             frame_scale=None if scale is None else torch.from_numpy(scale).pin_memory(),
                             k_top=24, tag=i, times=times, jitter=jitter))
         meta.append(dict(deq=q.float().numpy(), sigma=c["sigma"], mask=c["mask"], vx=vx, vy=vy, T=T, times=times,
-                         jitter=jitter, scale=scale))
+                         jitter=jitter, scale=scale, dtype=dt))
     return reqs, meta
 
 
@@ -146,6 +146,16 @@ def _oracle_maps(oracle, m):
     lam = oracle.inverse_variance(m["sigma"], m["mask"])
     fs = None if m["scale"] is None else m["scale"].astype(np.float64)
     return sh, tp, lam, fs
+
+
+def _oracle_search(oracle, m, sh, tp, lam, fs):
+    # 16-bit requests are searched in the precision form (the weighted stack
+    # in 16 bits); float32 ones with the plain definition
+    if m["dtype"] == torch.float32:
+        return oracle.search_full(m["deq"], lam, sh, tp, frame_scale=fs)
+    name = "bf16" if m["dtype"] == torch.bfloat16 else "fp16"
+    q, beta = oracle.weighted_stack16(m["deq"], m["sigma"], m["mask"], m["scale"], name)
+    return oracle.search_weighted(q, beta, lam, sh, tp)
 
 
 def test_served_results_match_the_oracle(oracle):
@@ -162,7 +172,7 @@ def test_served_results_match_the_oracle(oracle):
     assert mf.device_status() == 0 and srv.failed == 0
     for res, m in zip(out, meta):
         sh, tp, lam, fs = _oracle_maps(oracle, m)
-        N, D = oracle.search_full(m["deq"], lam, sh, tp, frame_scale=fs)
+        N, D = _oracle_search(oracle, m, sh, tp, lam, fs)
         check_search(res.snr_max, res.argmax, None, N, D, oracle, label="served request %d" % res.tag)
         c = res.candidates
         assert len(c) > 0
@@ -197,7 +207,7 @@ def test_a_request_whose_search_times_out_fails_alone(oracle):
             continue
         res = f.result(timeout=300)
         sh, tp, lam, fs = _oracle_maps(oracle, m)
-        N, D = oracle.search_full(m["deq"], lam, sh, tp, frame_scale=fs)
+        N, D = _oracle_search(oracle, m, sh, tp, lam, fs)
         check_search(res.snr_max, res.argmax, None, N, D, oracle, label="request %d beside a failed one" % i)
     srv.close()
     assert srv.failed == 1
