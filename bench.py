@@ -41,7 +41,7 @@ T_FR, HH, WW, NXG, NYG, VMAX = 1000, 2048, 2048, 10, 10, 0.1
 PAPER_RATE = NXG * NYG * T_FR * HH * WW / 300.0
 K_TOP = 4096
 FLOP_PER_UNIT_GENERAL = 50  # 25 FP32 FMAs per (trajectory, pixel, frame): the general 5x5 footprint
-SM_COUNT, FP32_LANES = 152, 128
+FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 
 
 def _peaks():
@@ -54,9 +54,16 @@ def _peaks():
         return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
 
 
-def _fp32_peak_tflops(sm_mhz):
+def _sm_count():
+    """Streaming multiprocessors of the GPU the benchmark runs on."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def _fp32_peak_tflops(sm_mhz, sms=None):
     """FFMA peak from unit counts and clock: SMs x FP32 lanes x 2 flop x clock."""
-    return SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    sms = _sm_count() if sms is None else sms
+    return sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -408,6 +415,17 @@ def run_ours(args):
         parity = {"crop": [int(y0), int(x0), int(side)], "max_rel_err_snr_max": float(err.max()),
                   "tolerance": 1e-5}
 
+    # the serving form and the precision form, each measured on its own after
+    # the timed search (rank 0 at N = 1: they are single-GPU workloads)
+    serve = precision = None
+    if rank == 0 and ws == 1 and (not args.no_serve or not args.no_precision):
+        del case, res, sigma, mask, ws_search, ws_rescore, snr_max, argmax
+        torch.cuda.empty_cache()
+        if not args.no_precision:
+            precision = precision_measure(args, dev, T, H, W, 2, args.precision_px)
+        if not args.no_serve:
+            serve = serve_measure(args, dev, args.serve_duration, args.pool)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -426,8 +444,9 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "k_numerator_fac" if info["kernel"] == 2 else "k_numerator",
                          "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s)" % (
-                             float(peaks.get("sm_max_mhz", 2070.0)), peak_src),
+                         "peak_source": "%d SMs (device properties) x 128 FP32 lanes x 2 flop x %.0f MHz "
+                                        "(sm_max_mhz, %s)" % (_sm_count(), float(peaks.get("sm_max_mhz", 2070.0)),
+                                                              peak_src),
                          "flop_per_unit": fpu,
                          # the same launches counted at the general 5 x 5 form's
                          # 50 flop per unit: a rate of the search, not of the FP32 pipe
@@ -442,6 +461,10 @@ def run_ours(args):
         }
         if parity:
             line["parity"] = parity
+        if precision:
+            line["precision"] = precision
+        if serve:
+            line["serve"] = serve
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -529,20 +552,19 @@ def run_batch(args):
     return 0
 
 
-def run_serve(args):
+def serve_measure(args, dev, duration, pool_n, rate=None):
     """Serving form: Poisson request stream, admission by footprint against
     a memory budget, continuous batching on several streams; p50/p99 latency
-    and throughput, against the same stream served one request at a time."""
+    and throughput, against the same stream served one request at a time.
+    Requests are drawn from `pool_n` distinct pregenerated cutouts (each a
+    config-2-like stack of its own size, frame count and trajectory grid)."""
     import torch
 
-    from paper_2209_09848_gb300 import _build
     from paper_2209_09848_gb300.serve import Request, Server, percentile
-    _build.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    rate = args.rate if rate is None else rate
     rng = np.random.default_rng(5)
     pool = []
-    for i in range(args.pool):
+    for i in range(pool_n):
         side = int(rng.choice([256, 512, 768, 1024]))
         T = int(rng.integers(300, 1301))
         K = int(rng.integers(10, 201))
@@ -554,8 +576,8 @@ def run_serve(args):
         pool.append(req)
         del c
     torch.cuda.empty_cache()
-    n_req = int(args.rate * args.duration)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    n_req = int(rate * duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     picks = rng.integers(0, len(pool), n_req)
 
     def serve(streams):
@@ -575,41 +597,57 @@ def run_serve(args):
         span = max(r.done for r in res) - min(r.arrival for r in res)
         units = sum(r.tag for r in res)
         return {"p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "mean_ms": float(np.mean(lat)),
-                "throughput": units / span, "requests": len(res), "span_s": span,
-                "peak_bytes": srv.peak}
+                "throughput": units / span, "unit": UNIT, "requests": len(res), "span_s": span,
+                "peak_bytes": srv.peak, "failed": srv.failed}
 
     mix = serve(args.streams)
     one = serve(1)
+    del pool
+    torch.cuda.empty_cache()
+    return {"p50_ms": mix["p50_ms"], "p99_ms": mix["p99_ms"], "throughput": mix["throughput"], "unit": UNIT,
+            "workload": "Poisson %.0f req/s for %.0f s (%d requests), cutouts as the batched form (sides "
+                        "{256,512,768,1024}, 300-1300 frames, fp32 or bf16) with 10-200 trajectories, top-64 FP64 "
+                        "rescore each, budget %.0f GB, %d streams; requests drawn from %d distinct pregenerated "
+                        "cutouts" % (rate, duration, n_req, args.budget_gb, args.streams, pool_n),
+            "distinct_requests": pool_n, "served": mix, "one_request_at_a_time": one}
+
+
+def run_serve(args):
+    """The serving form alone, as its own JSON line."""
+    import torch
+
+    from paper_2209_09848_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = serve_measure(args, dev, args.duration, args.pool)
+    mix = r["served"]
     line = {"metric": "serve p50/p99 latency (ms) and traj*pixel*frame/s under a Poisson request stream",
             "value": mix["throughput"], "unit": UNIT, "n_gpus": 1, "steps": mix["requests"],
             "warmup": 1, "ms_per_step": mix["mean_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 and bf16 storage, f32 arithmetic", "data": "synthetic",
-            "config": {"workload": "serving form: Poisson %.0f req/s for %.0f s, cutouts as the batched form with "
-                                   "10-200 trajectories, top-64 FP64 rescore each, budget %.0f GB, %d streams"
-                                   % (args.rate, args.duration, args.budget_gb, args.streams),
-                       "distinct_requests": len(pool)},
-            "serve": mix, "one_request_at_a_time": one}
+            "config": {"workload": "serving form: " + r["workload"], "distinct_requests": args.pool},
+            "serve": mix, "one_request_at_a_time": r["one_request_at_a_time"]}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_precision(args):
+def precision_measure(args, dev, T, H, W, steps, n_px):
     """Precision form: the paper-shaped stack stored as FP32, BF16 (scale 1)
     and FP16 (per-frame scale max|r_t| / 2^14), 1000 trajectories (40 x 25
-    grid), FP32 accumulation; each form timed and its SNR error against the
-    FP64 oracle (evaluated on the FP32 master) reported on sampled pixels, plus
-    the error of the FP64 re-score on 64 pixels chosen from a host-generated
-    score map (the oracle evaluated at its own selection of them)."""
+    grid), FP32 accumulation; a bf16 / fp16 stack's weighted copy stays
+    16-bit.  For each form: its rate, its workspace and stack bytes, and on
+    sampled start pixels (every trajectory) the SNR error against the FP64
+    oracle evaluated on the FP32 master (the error the storage costs) and
+    against the oracle of the form itself (the oracle's 16-bit weighted
+    stack: the kernel's own error); plus the FP64 re-score from the FP32
+    master on 64 pixels chosen from a host-generated score map."""
     import torch
 
     import oracle
     import paper_2209_09848_gb300 as mf
-    from paper_2209_09848_gb300 import _build, synth
-    _build.build()
+    from paper_2209_09848_gb300 import synth
     oracle.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    T, H, W = args.frames, args.size, args.size
     case = synth.paper_case_gpu(T=T, H=H, W=W, seed=3, device=dev)
     vx, vy = synth.velocity_grid(40, 25, -args.vmax, args.vmax)
     K = len(vx)
@@ -619,21 +657,23 @@ def run_precision(args):
     forms = {"f32": (master, None), "bf16": (master.to(torch.bfloat16), None),
              "f16": ((master / scale16[:, None, None]).to(torch.float16), scale16)}
     rng = np.random.default_rng(11)
-    n_px = args.sample_px
     ys = rng.integers(0, H, n_px).astype(np.int32)
     xs = rng.integers(0, W, n_px).astype(np.int32)
+    pys, pxs = np.repeat(ys, K), np.repeat(xs, K)
+    pks = np.tile(np.arange(K, dtype=np.int32), n_px)
     res_host = master.cpu().numpy()
     sh, tp = oracle.trajectory_table(vx, vy, T)
     lam = oracle.inverse_variance(case["sigma_np"], case["mask_np"])
+
+    def best(N, D):
+        N = N.reshape(n_px, K)
+        D = D.reshape(n_px, K)
+        snr = np.where(D > 0, N / np.sqrt(np.where(D > 0, D, 1.0)), 0.0)
+        return np.where(D > 0, snr, -np.inf).max(axis=1)
+
     t0 = time.perf_counter()
-    N, D = oracle.search_points(res_host, lam, sh, tp, np.repeat(ys, K), np.repeat(xs, K),
-                                np.tile(np.arange(K, dtype=np.int32), n_px))
+    o_max = best(*oracle.search_points(res_host, lam, sh, tp, pys, pxs, pks))
     oracle_s = time.perf_counter() - t0
-    N = N.reshape(n_px, K)
-    D = D.reshape(n_px, K)
-    o_snr = np.where(D > 0, N / np.sqrt(np.where(D > 0, D, 1.0)), 0.0)
-    o_max = np.where(D > 0, o_snr, -np.inf).max(axis=1)
-    ws = torch.empty(mf.search_workspace_size((T, H, W), table), dtype=torch.uint8, device=dev)
     chk_s, chk_a = synth.score_map(H, W, seed=21, K=K, mask_frac=0.0)
     chk_want = oracle.topk_order(chk_s, chk_a, 64)
     Nc, Dc = oracle.search_points(res_host, lam, sh, tp, (chk_want // W).astype(np.int32),
@@ -644,6 +684,8 @@ def run_precision(args):
     units = K * T * H * W
     mf.profile_enable(True)
     for name, (stack, fs) in forms.items():
+        ws_bytes = mf.search_workspace_size((T, H, W), table, stack.dtype)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         smax = torch.empty((H, W), device=dev)
         amax = torch.empty((H, W), dtype=torch.int32, device=dev)
         mf.search(stack, case["sigma"], table, mask=case["mask"], frame_scale=fs, workspace=ws, out=(smax, amax, None))
@@ -651,17 +693,26 @@ def run_precision(args):
         mf.profile_read(reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             mf.search(stack, case["sigma"], table, mask=case["mask"], frame_scale=fs, workspace=ws,
                       out=(smax, amax, None))
             raw, n = mf.rescore_topk(master, case["sigma"], table, smax, amax, K_TOP, mask=case["mask"])
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         prof = mf.profile_read(reset=True)
-        num_ms = prof["k_numerator"][1] / args.steps  # per step: one launch per time segment
+        num_ms = prof["k_numerator"][1] / steps  # per step: one launch per time segment
         g_max = smax.cpu().numpy()[ys, xs].astype(np.float64)
         err = np.abs(g_max - o_max) / np.maximum(1.0, np.abs(o_max))
+        form_err = None
+        if name != "f32":
+            # the oracle of the precision form: its 16-bit weighted stack
+            q, beta = oracle.weighted_stack16(stack.float().cpu().numpy(), case["sigma_np"], case["mask_np"],
+                                              None if fs is None else fs.cpu().numpy(),
+                                              "bf16" if name == "bf16" else "fp16")
+            f_max = best(*oracle.search_weighted_points(q, beta, lam, sh, tp, pys, pxs, pks))
+            del q
+            form_err = float((np.abs(g_max - f_max) / np.maximum(1.0, np.abs(f_max))).max())
         # the FP64 re-score on 64 pixels chosen from a host-generated score
         # map (the oracle is evaluated at its own selection of them)
         raw64, n64 = mf.rescore_topk(master, case["sigma"], table, torch.from_numpy(chk_s).to(dev),
@@ -669,21 +720,47 @@ def run_precision(args):
         cands = mf.decode_candidates(raw64, int(n64.item()))
         ok = Dc > 0
         rerr = np.abs(cands["snr"][ok] - Nc[ok] / np.sqrt(Dc[ok])) / np.maximum(1.0, np.abs(Nc[ok] / np.sqrt(Dc[ok])))
-        out[name] = {"value": units / (ms * 1e-3), "ms_per_step": ms, "numerator_ms": num_ms,
+        y_bytes = T * H * W * (4 if name == "f32" or table.info()["kernel"] != 2 else 2)
+        out[name] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "numerator_ms": num_ms,
                      "frac": units * flop_per_unit(table.info()["kernel"], vx) / (num_ms * 1e-3) / 1e12 / peak_tf,
                      "stack_gb": stack.numel() * stack.element_size() / 1e9,
-                     "snr_max_rel_err_vs_fp64_oracle": {"max": float(err.max()), "median": float(np.median(err))},
+                     "workspace_gb": ws_bytes / 1e9, "weighted_stack_gb": y_bytes / 1e9,
+                     "numerator_algorithmic_dram_gb": y_bytes / 1e9,
+                     "snr_max_rel_err_vs_fp64_oracle_on_fp32_master": {"max": float(err.max()),
+                                                                       "median": float(np.median(err))},
+                     "snr_max_rel_err_vs_oracle_of_this_form": form_err,
                      "fp64_rescore_rel_err": float(rerr.max()) if ok.any() else None,
                      "rescore_selection_equals_oracle": bool(np.array_equal(
                          cands["y"].astype(np.int64) * W + cands["x"], chk_want))}
+        del ws
+        torch.cuda.empty_cache()
+    mf.profile_enable(False)
+    del case, master, forms
+    torch.cuda.empty_cache()
+    return {"workload": "%d frames x %dx%d, %d trajectories (40x25 grid, |v|<=%.2f), search + top-%d FP64 rescore "
+                        "from the FP32 master; %d steps per form" % (T, H, W, K, args.vmax, K_TOP, steps),
+            "error_sample": "%d random start pixels x all trajectories, FP64 oracle on the FP32 master (%.1f s)"
+                            % (n_px, oracle_s),
+            "forms": out}
+
+
+def run_precision(args):
+    """The precision forms alone, as their own JSON line."""
+    import torch
+
+    from paper_2209_09848_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    T, H, W = args.frames, args.size, args.size
+    r = precision_measure(args, dev, T, H, W, args.steps, args.sample_px)
+    out = r["forms"]
+    K = 1000
     line = {"metric": "traj*pixel*frame/s, precision forms at %dx%d^2x%d traj" % (T, H, K), "value": out["bf16"]["value"],
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": out["bf16"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 storage (f32 and f16 alongside), f32 arithmetic", "data": "synthetic",
-            "config": {"workload": "precision form: %d frames x %dx%d, %d trajectories (40x25 grid), "
-                                   "search + top-%d FP64 rescore from the FP32 master" % (T, H, W, K, K_TOP),
-                       "error_sample": "%d random start pixels x all trajectories, FP64 oracle on the FP32 master "
-                                       "(%.1f s)" % (n_px, oracle_s)},
+            "config": {"workload": "precision form: " + r["workload"], "error_sample": r["error_sample"]},
             "forms": out}
     print(json.dumps(line), flush=True)
     return 0
@@ -921,9 +998,15 @@ def main():
                     default="search",
                     help="search: the paper-shaped search (default); batch / serve: the batched and serving forms")
     ap.add_argument("--items", type=int, default=64, help="batch: cutouts in the batch")
-    ap.add_argument("--pool", type=int, default=16, help="serve: distinct pregenerated requests")
+    ap.add_argument("--pool", type=int, default=32, help="serve: distinct pregenerated requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
-    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve workload: seconds of arrivals")
+    ap.add_argument("--serve-duration", type=float, default=15.0,
+                    help="seconds of arrivals of the serving form in the default line")
+    ap.add_argument("--no-serve", action="store_true", help="default line without the serving form")
+    ap.add_argument("--no-precision", action="store_true", help="default line without the precision forms")
+    ap.add_argument("--precision-px", type=int, default=128,
+                    help="start pixels of the precision forms' error sample in the default line")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: admission budget")
     ap.add_argument("--streams", type=int, default=4, help="serve: searches in flight")
     ap.add_argument("--sample-px", type=int, default=256, help="precision: start pixels checked against the oracle")
