@@ -289,7 +289,9 @@ def run_ours(args):
     from paper_2209_09848_gb300 import synth
 
     T, H, W = args.frames, args.size, args.size
-    case = synth.paper_case_gpu(T=T, H=H, W=W, seed=1 + rank, device=dev)
+    # 200 movers on the 2048 x 2048 frame; a smaller frame gets them in proportion to its area
+    n_mov = max(1, int(round(200 * H * W / (HH * WW))))
+    case = synth.paper_case_gpu(T=T, H=H, W=W, n_movers=n_mov, seed=1 + rank, device=dev)
     vx, vy = synth.velocity_grid(NXG, NYG, -args.vmax, args.vmax)
     K = len(vx)
     kind = 2 if args.prf == "shiftstack" else 0
@@ -423,6 +425,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if not args.no_precision:
             precision = precision_measure(args, dev, T, H, W, 2, args.precision_px)
+            precision["phase_quantised"] = quantised_measure(args, dev, T, H, W)
         if not args.no_serve:
             serve = serve_measure(args, dev, args.serve_duration, args.pool)
 
@@ -742,6 +745,62 @@ def precision_measure(args, dev, T, H, W, steps, n_px):
             "error_sample": "%d random start pixels x all trajectories, FP64 oracle on the FP32 master (%.1f s)"
                             % (n_px, oracle_s),
             "forms": out}
+
+
+def quantised_measure(args, dev, T, H, W, Q=4, steps=1):
+    """The phase-quantised bank on the 1000-trajectory grid (40 x 25, the
+    precision form's): the exact bank with column passes, the quantised bank
+    (phases rounded to multiples of 1/Q) with column passes and with the
+    precompute-then-gather numerator (phase planes); the quantisation loss
+    as the SNR at the 200 injected movers' start pixels, quantised over
+    exact (the movers' velocities are off the grid, as in the paper's
+    injections)."""
+    import torch
+
+    import paper_2209_09848_gb300 as mf
+    from paper_2209_09848_gb300 import synth
+    case = synth.paper_case_gpu(T=T, H=H, W=W, seed=3, device=dev)
+    vx, vy = synth.velocity_grid(40, 25, -args.vmax, args.vmax)
+    K = len(vx)
+    units = K * T * H * W
+    mv = case["movers"]
+    my = np.clip(np.round(mv[:, 0]).astype(np.int64), 0, H - 1)
+    mx = np.clip(np.round(mv[:, 1]).astype(np.int64), 0, W - 1)
+    out, at_movers = {}, {}
+    mf.profile_enable(True)
+    for name, kw in (("exact_column_passes", {}), ("quantised_column_passes", dict(phase_steps=Q, kernel=2)),
+                     ("quantised_phase_planes", dict(phase_steps=Q, kernel=3))):
+        tab = mf.prf_table_create(vx, vy, T, **kw)
+        ws = torch.empty(mf.search_workspace_size((T, H, W), tab), dtype=torch.uint8, device=dev)
+        smax = torch.empty((H, W), device=dev)
+        amax = torch.empty((H, W), dtype=torch.int32, device=dev)
+        mf.search(case["res"], case["sigma"], tab, mask=case["mask"], workspace=ws, out=(smax, amax, None))
+        torch.cuda.synchronize()
+        mf.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            mf.search(case["res"], case["sigma"], tab, mask=case["mask"], workspace=ws, out=(smax, amax, None))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = mf.profile_read(reset=True)
+        info = tab.info()
+        out[name] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "numerator_ms": prof["k_numerator"][1] / steps, "phase_planes": info["phase_planes"],
+                     "plan": {x: info[x] for x in ("groups", "warps_per_group", "tile_h", "window_rows")}}
+        at_movers[name] = smax.cpu().numpy()[my, mx].astype(np.float64)
+        del ws, tab
+        torch.cuda.empty_cache()
+    mf.profile_enable(False)
+    del case
+    torch.cuda.empty_cache()
+    ratio = at_movers["quantised_column_passes"] / np.where(at_movers["exact_column_passes"] > 0,
+                                                             at_movers["exact_column_passes"], np.nan)
+    return {"workload": "%d frames x %dx%d float32, %d trajectories (40x25 grid), Q = %d, search only, %d step(s)"
+                        % (T, H, W, K, Q, steps), "forms": out,
+            "quantisation_loss": {"snr_max_at_movers_quantised_over_exact_median": float(np.nanmedian(ratio)),
+                                  "min": float(np.nanmin(ratio)), "movers": int(len(my))}}
 
 
 def run_precision(args):
