@@ -160,14 +160,16 @@ def flop_per_unit(kernel: int, vx, taps: int = 5) -> float:
 
 
 def _traffic_from_profiles(kernel: int = 2):
-    """DRAM bytes of the numerator per step (all its launches) from the
-    committed ncu summary of the kernel the plan uses, if any."""
+    """DRAM bytes of the numerator per traj*pixel*frame (all its launches),
+    from the committed ncu summary of the kernel the plan uses: measured on a
+    small case of the same plan (counters beyond the launch time are not
+    taken on the full workload), to be scaled by the units of a step."""
     name = "k_numerator_fac_paper_shaped.md" if kernel == 2 else "k_numerator_paper_shaped.md"
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             for line in f:
-                if line.startswith("traffic_bytes_per_step:"):
+                if line.startswith("traffic_bytes_per_unit:"):
                     v = line.split(":", 1)[1].strip()
                     return None if v in ("", "null") else float(v)
     except OSError:
@@ -350,7 +352,8 @@ def run_ours(args):
     # the committed ncu figure holds for the profiled workload only: the
     # default paper-shaped search with the Gaussian footprint
     profiled = (T, H, args.vmax, kind) == (T_FR, HH, VMAX, 0)
-    traffic = _traffic_from_profiles(info["kernel"]) if profiled else None
+    traffic_per_unit = _traffic_from_profiles(info["kernel"]) if profiled else None
+    traffic = None if traffic_per_unit is None else traffic_per_unit * units_rank
     kernel_ms = {k: round(v[1] / args.steps, 3) for k, v in prof.items() if k != "_launches" and v[0]}
     launches = int(prof["_launches"])
 
@@ -447,6 +450,9 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "k_numerator_fac" if info["kernel"] == 2 else "k_numerator",
                          "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
+                         "traffic_source": None if traffic is None else (
+                             "DRAM bytes per step: %.4f bytes per traj*pixel*frame from the ncu capture of the same "
+                             "plan on 1000 x 512^2 (profiles/), times this step's units" % traffic_per_unit),
                          "peak_source": "%d SMs (device properties) x 128 FP32 lanes x 2 flop x %.0f MHz "
                                         "(sm_max_mhz, %s)" % (_sm_count(), float(peaks.get("sm_max_mhz", 2070.0)),
                                                               peak_src),

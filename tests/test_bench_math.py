@@ -33,13 +33,14 @@ def test_peak_and_paper_rate(bench):
 
 
 def test_traffic_comes_from_the_committed_summaries(bench):
-    # the bench's roofline.traffic is the DRAM bytes per step recorded in the
-    # ncu summary of the kernel the plan uses
+    # the bench's roofline.traffic is the DRAM bytes per traj*pixel*frame
+    # recorded in the ncu summary of the kernel the plan uses (a small case
+    # of the same plan), times the step's units
     import re
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for kernel, name in ((2, "k_numerator_fac_paper_shaped.md"), (1, "k_numerator_paper_shaped.md")):
         text = open(os.path.join(root, "profiles", name)).read()
-        m = re.search(r"^traffic_bytes_per_step:\s*(\S+)", text, re.M)
+        m = re.search(r"^traffic_bytes_per_unit:\s*(\S+)", text, re.M)
         want = None if m is None or m.group(1) == "null" else float(m.group(1))
         assert bench._traffic_from_profiles(kernel) == want
-    assert bench._traffic_from_profiles(2) == pytest.approx(57.03e9)
+    assert bench._traffic_from_profiles(2) == pytest.approx(0.1232)
