@@ -40,6 +40,11 @@
  *     finalisation copies it into a device-wide status word, which
  *     mf_device_status() reads.  A failure in one search does not stop
  *     others, on the same or other streams.
+ *   - The library looks up the device addresses of its own device-side
+ *     variables (the status word, mf_search_noalloc's scratch) once per
+ *     device and keeps them for the process: they do not survive
+ *     cudaDeviceReset, after which the library must not be used again in
+ *     that process.
  */
 #ifndef MF_H
 #define MF_H

@@ -42,3 +42,50 @@ def test_wait_runs_out_and_the_context_survives(oracle):
     lam = oracle.inverse_variance(c["sigma"], c["mask"])
     N, D = oracle.search_full(c["res"], lam, sh, tp)
     check_search(smax.cpu().numpy(), amax.cpu().numpy(), sall.cpu().numpy(), N, D, oracle, label="after the probe")
+
+
+def test_search_status_slot_is_per_search(oracle):
+    # each search reports through its own status slot: 0 after a clean
+    # search; the probe aimed at one search's workspace makes that search
+    # (and only it) report code 4, read without synchronising the device;
+    # a search enqueued after the failure on another workspace is unaffected
+    import paper_2209_09848_gb300 as mf
+    from paper_2209_09848_gb300 import synth
+    mf.load()
+    assert mf.device_status() == 0
+    T, H, W = 10, 48, 64
+    c = synth.small_case(T, H, W, 8, mask_frac=0.02, movers=1)
+    vx, vy = synth.velocity_grid(3, 3, -0.3, 0.3)
+    table = mf.prf_table_create(vx, vy, T)
+    r = torch.from_numpy(c["res"]).cuda()
+    s = torch.from_numpy(c["sigma"]).cuda()
+    m = torch.from_numpy(c["mask"]).cuda()
+    nbytes = mf.search_workspace_size((T, H, W), table)
+    ws_a = torch.full((nbytes,), 0xAB, dtype=torch.uint8, device="cuda")  # stale bytes: the search clears its slot
+    ws_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st_a = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+    st_b = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+    mf.search(r, s, table, mask=m, workspace=ws_a)
+    mf.search_status(ws_a, st_a)
+    torch.cuda.synchronize()
+    assert int(st_a[0]) == 0 and mf.device_status() == 0
+    mf.search(r, s, table, mask=m, workspace=ws_a)
+    mf.wait_probe_search(ws_a)
+    mf.search_status(ws_a, st_a)
+    smax, amax, sall = mf.search(r, s, table, mask=m, workspace=ws_b, want_all=True)
+    mf.search_status(ws_b, st_b)
+    torch.cuda.synchronize()
+    assert int(st_a[0]) == 4 and int(st_b[0]) == 0
+    sh, tp = oracle.trajectory_table(vx, vy, T)
+    lam = oracle.inverse_variance(c["sigma"], c["mask"])
+    N, D = oracle.search_full(c["res"], lam, sh, tp)
+    check_search(smax.cpu().numpy(), amax.cpu().numpy(), sall.cpu().numpy(), N, D, oracle, label="beside a failure")
+    # the probe also wrote the device-wide word; reading it clears it
+    assert mf.device_status() == mf.MF_ETIMEOUT
+    assert mf.device_status() == 0
+    # a device status slot copied into device memory works the same way
+    dst = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    mf.search(r, s, table, mask=m, workspace=ws_a)
+    mf.search_status(ws_a, dst)
+    torch.cuda.synchronize()
+    assert int(dst.item()) == 0
