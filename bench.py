@@ -430,7 +430,7 @@ def run_ours(args):
             precision = precision_measure(args, dev, T, H, W, 2, args.precision_px)
             precision["phase_quantised"] = quantised_measure(args, dev, T, H, W)
         if not args.no_serve:
-            serve = serve_measure(args, dev, args.serve_duration, args.pool)
+            serve = serve_measure(args, dev, args.serve_duration, args.pool, extra_rates=(2 * args.rate,))
 
     if rank == 0:
         line = {
@@ -561,12 +561,14 @@ def run_batch(args):
     return 0
 
 
-def serve_measure(args, dev, duration, pool_n, rate=None):
+def serve_measure(args, dev, duration, pool_n, rate=None, extra_rates=()):
     """Serving form: Poisson request stream, admission by footprint against
     a memory budget, continuous batching on several streams; p50/p99 latency
     and throughput, against the same stream served one request at a time.
     Requests are drawn from `pool_n` distinct pregenerated cutouts (each a
-    config-2-like stack of its own size, frame count and trajectory grid)."""
+    config-2-like stack of its own size, frame count and trajectory grid).
+    `extra_rates`: further mean arrival rates run on the same pool (to show
+    how the two schedules hold up as the offered load grows)."""
     import torch
 
     from paper_2209_09848_gb300.serve import Request, Server, percentile
@@ -585,11 +587,8 @@ def serve_measure(args, dev, duration, pool_n, rate=None):
         pool.append(req)
         del c
     torch.cuda.empty_cache()
-    n_req = int(rate * duration)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
-    picks = rng.integers(0, len(pool), n_req)
 
-    def serve(streams):
+    def serve(streams, arrivals, picks):
         srv = Server(budget_bytes=int(args.budget_gb * 1e9), streams=streams, planners=8, device=dev)
         # warm the planners and the allocator on one request
         srv.submit(pool[0]).result()
@@ -609,16 +608,29 @@ def serve_measure(args, dev, duration, pool_n, rate=None):
                 "throughput": units / span, "unit": UNIT, "requests": len(res), "span_s": span,
                 "peak_bytes": srv.peak, "failed": srv.failed}
 
-    mix = serve(args.streams)
-    one = serve(1)
+    def stream(r, dur):
+        n_req = int(r * dur)
+        arrivals = np.cumsum(rng.exponential(1.0 / r, n_req))
+        picks = rng.integers(0, len(pool), n_req)
+        offered = sum(pool[k].tag for k in picks) / dur
+        return arrivals, picks, offered
+
+    arr, picks, offered = stream(rate, duration)
+    mix = serve(args.streams, arr, picks)
+    one = serve(1, arr, picks)
+    out = {"p50_ms": mix["p50_ms"], "p99_ms": mix["p99_ms"], "throughput": mix["throughput"], "unit": UNIT,
+           "workload": "Poisson %.0f req/s for %.0f s (%d requests), cutouts as the batched form (sides "
+                       "{256,512,768,1024}, 300-1300 frames, fp32 or bf16) with 10-200 trajectories, top-64 FP64 "
+                       "rescore each, budget %.0f GB, %d streams; requests drawn from %d distinct pregenerated "
+                       "cutouts" % (rate, duration, len(picks), args.budget_gb, args.streams, pool_n),
+           "offered": offered, "distinct_requests": pool_n, "served": mix, "one_request_at_a_time": one}
+    for r2 in extra_rates:
+        arr, picks, offered = stream(r2, duration)
+        out["at_%g_per_s" % r2] = {"offered": offered, "served": serve(args.streams, arr, picks),
+                                   "one_request_at_a_time": serve(1, arr, picks)}
     del pool
     torch.cuda.empty_cache()
-    return {"p50_ms": mix["p50_ms"], "p99_ms": mix["p99_ms"], "throughput": mix["throughput"], "unit": UNIT,
-            "workload": "Poisson %.0f req/s for %.0f s (%d requests), cutouts as the batched form (sides "
-                        "{256,512,768,1024}, 300-1300 frames, fp32 or bf16) with 10-200 trajectories, top-64 FP64 "
-                        "rescore each, budget %.0f GB, %d streams; requests drawn from %d distinct pregenerated "
-                        "cutouts" % (rate, duration, n_req, args.budget_gb, args.streams, pool_n),
-            "distinct_requests": pool_n, "served": mix, "one_request_at_a_time": one}
+    return out
 
 
 def run_serve(args):

@@ -235,9 +235,9 @@ def weighted_stack16(stored, sigma, mask=None, frame_scale=None, dtype="bf16"):
     rounded to FP32 (0 where masked or sigma unusable), alpha_t the frame
     scale, r_t the stored 16-bit value -- and stored in the stack's own
     16-bit type: bf16 as it is (scale beta_t = 1); fp16 divided by beta_t,
-    the power of two at or above lambda_max * alpha_t (lambda_max the largest
-    lambda), which keeps every stored value within fp16's range and makes
-    the division exact.  Rounding is to nearest, ties to even.
+    the power of two at or above lambda_max * |alpha_t| (lambda_max the
+    largest lambda), which keeps every stored value within fp16's range and
+    makes the division exact.  Rounding is to nearest, ties to even.
 
     Returns (q, beta): q [T, H, W] float32 holding the 16-bit values,
     beta [T] float64, so that the weighted residual is beta_t * q_t.  The
@@ -257,7 +257,7 @@ def weighted_stack16(stored, sigma, mask=None, frame_scale=None, dtype="bf16"):
     if dtype != "fp16":
         raise ValueError(dtype)
     lmax = np.float32(lam.max())
-    x = (lmax * alpha).astype(np.float32)
+    x = (lmax * np.abs(alpha)).astype(np.float32)
     e = np.minimum((x.view(np.uint32) >> 23) & 0xFF, 253).astype(np.int64)  # x = 1.m 2^(e - 127)
     beta = np.where(x > 0, np.ldexp(1.0, e - 126), 1.0)
     inv = np.where(x > 0, np.ldexp(1.0, 126 - e), 1.0).astype(np.float32)

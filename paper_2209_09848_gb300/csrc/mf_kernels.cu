@@ -87,7 +87,8 @@ __global__ void k_lambda(const float *__restrict__ sigma, const uint8_t *__restr
 // y_t = lambda * (scale_t * r_t) in FP32; stored as FP32 (TOut = float) or
 // in the stack's own 16-bit type (TOut = TIn): bf16 as is (beta_t = 1), fp16
 // times 1 / beta_t, beta_t the power of two at or above lambda_max * scale_t,
-// so that no value overflows (|stored r| <= 65504) and the scaling is exact.
+// (of |scale_t|), so that no value overflows (|stored r| <= 65504) and the
+// scaling is exact.
 // The thread of (frame t, row 0, first column quad) writes beta[t].
 __device__ __forceinline__ float fp16_frame_beta(float lmax, float sc, float *inv) {
     const float x = lmax * sc;
@@ -126,7 +127,7 @@ __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rst
         const int64_t t = rest / H;
         const float sc = scale ? scale[t] : 1.f;
         float inv = 1.f, bt = 1.f;
-        if (kHalfScaled) bt = fp16_frame_beta(lmax, sc, &inv);
+        if (kHalfScaled) bt = fp16_frame_beta(lmax, fabsf(sc), &inv);
         if (beta && yy == 0 && xq == 0) beta[t] = bt;
         const float *lrow = lam + (yy + pad) * lw + pad;
         const TIn *rrow = r + t * fstride + yy * rstride;

@@ -97,8 +97,10 @@ def test_frame_scale_and_half_precision_storage(mf, oracle, T, H, W, grid, vmax,
     sh, tp = oracle.trajectory_table(vx, vy, T)
     lam = oracle.inverse_variance(c["sigma"], c["mask"])
     for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "fp16")):
-        scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14).astype(np.float32) if dt == torch.float16 \
-            else np.exp(np.random.default_rng(T).uniform(-1, 1, T)).astype(np.float32)
+        # fp16: max|r_t| / 2^14, negative on every third frame (the stored
+        # values flip with it); bf16: any positive scale
+        scale = (np.abs(c["res"]).max(axis=(1, 2)) / 2.0 ** 14 * np.where(np.arange(T) % 3 == 0, -1, 1)).astype(
+            np.float32) if dt == torch.float16 else np.exp(np.random.default_rng(T).uniform(-1, 1, T)).astype(np.float32)
         q = torch.from_numpy(c["res"] / scale[:, None, None]).to(dt)
         deq = q.float().numpy()  # the stored values
         y16, beta = oracle.weighted_stack16(deq, c["sigma"], c["mask"], scale, name)

@@ -432,16 +432,18 @@ def test_weighted_stack16_exact_when_representable(oracle):
 
 
 def test_fp16_frame_scale_bounds(oracle):
-    # beta_t is the power of two with beta / 2 < lambda_max * alpha_t <= beta:
-    # the largest storable residual at the largest weight stays finite
+    # beta_t is the power of two with beta / 2 < lambda_max * |alpha_t| <=
+    # beta: the largest storable residual at the largest weight stays finite
+    # (negative frame scales included)
     g = _rng(43)
     T, H, W = 9, 12, 14
     sigma = np.exp(0.3 * g.standard_normal((H, W))).astype(np.float32)
-    alpha = np.exp(g.uniform(-12, 12, T)).astype(np.float32)
+    alpha = (np.exp(g.uniform(-12, 12, T)) * np.where(np.arange(T) % 3 == 0, -1, 1)).astype(np.float32)
     r = np.full((T, H, W), 65504.0, np.float32)
+    r[:, 0, 0] = -65504.0
     q, beta = oracle.weighted_stack16(r, sigma, None, alpha, "fp16")
     lam = oracle.inverse_variance(sigma)
-    x = (np.float32(lam.astype(np.float32).max()) * alpha).astype(np.float64)
+    x = (np.float32(lam.astype(np.float32).max()) * np.abs(alpha)).astype(np.float64)
     m, e = np.frexp(beta)
     assert np.all(m == 0.5)  # powers of two
     assert np.all((beta / 2 < x) & (x <= beta))
