@@ -41,8 +41,8 @@ namespace {
 
 using namespace dev;
 
-__device__ __forceinline__ int status_now() { return dev::status_now(&g_status); }
-
+// A bounded wait that records a failure in the device-wide word (the search
+// kernels record theirs in their own search's status slot instead).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code) {
     return dev::mbar_wait(bar, parity, code, &g_status);
 }
