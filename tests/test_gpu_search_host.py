@@ -99,3 +99,26 @@ def test_pipelined_calls_keep_their_own_results(mf):
         torch.cuda.synchronize()
         assert torch.equal(smax, dm.cpu()) and torch.equal(amax, da.cpu())
         assert torch.equal(cand, raw.cpu()) and int(n.item()) == int(dn.item())
+
+
+def test_host_search_status_slot(mf):
+    # the host-stack search's workspace starts with its search's status
+    # slot: mf_search_status reads it there (0 for a clean search, the probe's
+    # code when a wait aimed at it runs out)
+    c, vx, vy = _case(T=9, H=40, W=52, seed=13)
+    T, H, W = c["res"].shape
+    table = mf.prf_table_create(vx, vy, T)
+    sigma = torch.from_numpy(c["sigma"]).cuda()
+    host = torch.from_numpy(c["res"]).clone().pin_memory()
+    ws = torch.empty(mf.search_host_workspace_size(host, table, 0), dtype=torch.uint8, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+    mf.search_host(host, sigma, table, workspace=ws)
+    mf.search_status(ws, st)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0
+    mf.search_host(host, sigma, table, workspace=ws)
+    mf.wait_probe_search(ws)
+    mf.search_status(ws, st)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 4
+    assert mf.device_status() == mf.MF_ETIMEOUT and mf.device_status() == 0
