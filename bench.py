@@ -838,7 +838,7 @@ def run_precision(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 storage (f32 and f16 alongside), f32 arithmetic", "data": "synthetic",
             "config": {"workload": "precision form: " + r["workload"], "error_sample": r["error_sample"]},
-            "forms": out}
+            "forms": out, "phase_quantised": quantised_measure(args, dev, T, H, W)}
     print(json.dumps(line), flush=True)
     return 0
 

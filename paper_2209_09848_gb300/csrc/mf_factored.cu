@@ -186,8 +186,8 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     constexpr int EPF = 4 / (int)sizeof(E);                              // window values per float of a stage
     E *rwin = reinterpret_cast<E *>(smem);                               // [NS] windows of BH x RP values
     float *hbuf = reinterpret_cast<float *>(smem) + (size_t)NS * SF;     // [kFacHBufs][BH][HP] (QG: [1])
-    float *pbuf = hbuf + (size_t)(QG ? 1 : kFacHBufs) * BH * HP;         // QG: [npl][BH][HP] phase planes
-    unsigned char *fb = reinterpret_cast<unsigned char *>(pbuf + (size_t)(QG ? p.npl : 0) * BH * HP);  // [2][R]
+    float *pbuf = hbuf + (size_t)(QG ? 2 : kFacHBufs) * BH * HP;         // QG: [2][npl][BH][HP] phase planes
+    unsigned char *fb = reinterpret_cast<unsigned char *>(pbuf + (size_t)(QG ? 2 * p.npl : 0) * BH * HP);  // [2][R]
     uint64_t *bars = reinterpret_cast<uint64_t *>(fb + 2 * R * kBB);
     int *last_issued = reinterpret_cast<int *>(bars + NS);
     int *bad_flag = last_issued + NS;
@@ -300,7 +300,7 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
             const int nrows = fh->nrows;
             const int m = (int)(((float)j + 0.5f) * fh->inv_nrows), row = j - m * nrows;
             const E *src = rwin + (size_t)st * SF * EPF + row * RP + kFacItem * m;
-            float *dst = hbuf + (size_t)(QG ? 0 : f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
+            float *dst = hbuf + (size_t)(QG ? (f & 1) : f % kFacHBufs) * BH * HP + row * HP + kFacItem * m;
             if constexpr (k16) {
                 // the taps carry the frame's scale of a 16-bit weighted stack
                 // (a power of two: u_x * beta is exact)
@@ -329,23 +329,31 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         }
     };
 
-    // phase planes of frame f: plane j row i = sum_b u_j(b) H(i + b), rows
-    // 0 .. nrows - 5, items of 8 rows x 2 columns dealt over all threads
-    // (consecutive threads on consecutive column pairs: conflict-free)
-    auto plane_frame = [&](int f) {
+    // phase planes of frames f0 and f0 + 1 (if `two`): plane j row i =
+    // sum_b u_j(b) H(i + b), rows 0 .. nrows - 5, items of 8 rows x 2
+    // columns dealt over all threads (consecutive threads on consecutive
+    // column pairs: conflict-free); frame f's planes go to set f & 1
+    auto plane_pair = [&](int f0, bool two) {
         constexpr int PR = 8;  // rows per item
-        const unsigned char *fblk = record(f);
-        const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
-        const FacPlane *pl = reinterpret_cast<const FacPlane *>(fblk + sizeof(FacHdr) + (size_t)KT * sizeof(FacSlot));
         constexpr int NCP = TW / 2;
-        const int nrows = fh->nrows, prow = nrows - 4, nrc = (prow + PR - 1) / PR;
-        const int n = fh->pad * nrc * NCP;
-        for (int it = threadIdx.x; it < n; it += blockDim.x) {
-            const int cp = it % NCP, rest = it / NCP, rc = rest % nrc, j = rest / nrc;
+        int n[2], nrc[2];
+        for (int e = 0; e < 2; e++) {
+            const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(f0 + (two ? e : 0)));
+            nrc[e] = (fh->nrows - 4 + PR - 1) / PR;
+            n[e] = (e == 0 || two) ? fh->pad * nrc[e] * NCP : 0;
+        }
+        for (int it = threadIdx.x; it < n[0] + n[1]; it += blockDim.x) {
+            const int e = it >= n[0], k = e ? it - n[0] : it, f = f0 + e;
+            const unsigned char *fblk = record(f);
+            const FacHdr *fh = reinterpret_cast<const FacHdr *>(fblk);
+            const FacPlane *pl =
+                reinterpret_cast<const FacPlane *>(fblk + sizeof(FacHdr) + (size_t)KT * sizeof(FacSlot));
+            const int nrows = fh->nrows, prow = nrows - 4;
+            const int cp = k % NCP, rest = k / NCP, rc = rest % nrc[e], j = rest / nrc[e];
             const float4 u4 = *reinterpret_cast<const float4 *>(pl[j].uy);
             const float u[5] = {u4.x, u4.y, u4.z, u4.w, pl[j].uy[4]};
-            const float *src = hbuf + (size_t)(PR * rc) * HP + 2 * cp;
-            float *dst = pbuf + (size_t)j * BH * HP + (size_t)(PR * rc) * HP + 2 * cp;
+            const float *src = hbuf + (size_t)(f & 1) * BH * HP + (size_t)(PR * rc) * HP + 2 * cp;
+            float *dst = pbuf + ((size_t)(f & 1) * p.npl + j) * BH * HP + (size_t)(PR * rc) * HP + 2 * cp;
             float2 o[PR];
 #pragma unroll
             for (int r = 0; r < PR; r++) o[r] = make_float2(0.f, 0.f);
@@ -374,8 +382,8 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
         if (!active) return;
         const unsigned char *fblk = record(f);
         const FacSlot *fs = reinterpret_cast<const FacSlot *>(fblk + sizeof(FacHdr)) + slot;
-        const float *col = pbuf + (size_t)fs->plane * BH * HP + (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x +
-                           2 * cp;
+        const float *col = pbuf + ((size_t)(f & 1) * p.npl + fs->plane) * BH * HP +
+                           (32 * sub_y + 16 * rh + fs->oy) * HP + 32 * sub_x + 2 * cp;
 #pragma unroll
         for (int r = 0; r < 16; r++) {
             const float2 v = *reinterpret_cast<const float2 *>(col + r * HP);
@@ -388,35 +396,47 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
     int s = 0;  // stage of frame t and its phase
     uint32_t par = 0;
     if constexpr (QG) {
-        // one frame at a time: row pass -> barrier -> planes -> barrier ->
-        // gathers; the next row pass overwrites the row-pass buffer only after
-        // the barrier that ends every thread's plane work, and the next planes
-        // the plane buffers only after the barrier every thread reaches past
-        // its gathers
-        for (int t = t0; t < t1; t++) {
-            const bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
-            if (ready) row_pair(t, s, s, false);
+        // two frames at a time: row passes -> barrier -> planes -> barrier ->
+        // gathers.  The next pair's row passes overwrite the row-pass
+        // buffers only after the barrier that ends every thread's plane
+        // work, and its planes the plane sets only after the barrier every
+        // thread reaches past its gathers (frame f uses row-pass buffer and
+        // plane set f & 1, which differ for the two frames of a pair)
+        for (int t = t0; t < t1; t += 2) {
+            const bool two = t + 1 < t1;
+            const int s1 = (s + 1 == NS) ? 0 : s + 1;
+            const uint32_t par1 = (s + 1 == NS) ? (par ^ 1u) : par;
+            bool ready = mbar_wait(smem_u32(&bars[s]), par, 1, p.status);
+            if (ready && two) ready = mbar_wait(smem_u32(&bars[s1]), par1, 1, p.status);
+            if (ready) row_pair(t, s, s1, two);
             if (__syncthreads_or(!ready)) {
                 bad = true;
                 break;
             }
-            if (threadIdx.x == 0 && t + NS < t1) {
+            if (threadIdx.x == 0) {
                 fence_proxy_async();
-                const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t));
-                issue(t + NS, s, fh->next_roy, fh->next_rox);
+                if (t + NS < t1) {
+                    const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t));
+                    issue(t + NS, s, fh->next_roy, fh->next_rox);
+                }
+                if (two && t + 1 + NS < t1) {
+                    const FacHdr *fh = reinterpret_cast<const FacHdr *>(record(t + 1));
+                    issue(t + 1 + NS, s1, fh->next_roy, fh->next_rox);
+                }
             }
-            plane_frame(t);
+            plane_pair(t, two);
             __syncthreads();
             gather(t);
-            if ((t - t0 + 1) % kFrameBlock == 0) {
+            if (two) gather(t + 1);
+            if ((t - t0 + 2) % kFrameBlock == 0) {
 #pragma unroll
                 for (int r = 0; r < 32; r++) {
                     acc[r] += blk[r];
                     blk[r] = 0.f;
                 }
             }
-            s = (s + 1 == NS) ? 0 : s + 1;
-            par = (s == 0) ? (par ^ 1u) : par;
+            s = (s1 + 1 == NS) ? 0 : s1 + 1;
+            par = (s1 + 1 == NS) ? (par1 ^ 1u) : par1;
         }
     }
     for (int t = t0; t < t1 && !QG; t += 2) {  // column passes (the loop is empty for QG)

@@ -78,13 +78,11 @@ struct alignas(16) DenBox {
     int32_t dy0, rows, x0, cols, w0, nw, pad[2];
 };
 constexpr int kDenBoxCols = 256;  // start pixels per row of a staged-denominator tile
-// Float4 chunk j of a staged lambda row sits at chunk j ^ ((j >> 3) & 1): the
-// eight lanes of a quarter warp, 8 columns (2 chunks) apart, then read eight
-// distinct 16-byte bank groups whatever the row's start.
-__host__ __device__ constexpr int den_chunk(int j) { return j ^ ((j >> 3) & 1); }
-// Row pitch in chunks for `cols` box columns, and the dynamic shared memory of
-// a tile th rows high.
-__host__ __device__ constexpr int den_pitch(int cols) { return ((kDenBoxCols + cols) / 4 + 1) / 2 * 2; }
+constexpr int kDenOut = 8;        // start pixels per thread of the staged denominator
+// Row pitch in 16-byte chunks of a staged lambda box for `cols` box columns:
+// odd, so that the same chunk of 8 consecutive rows falls in 8 distinct bank
+// groups.
+__host__ __device__ constexpr int den_pitch(int cols) { return (kDenBoxCols + cols) / 4 | 1; }
 // Box, weights and the trajectory's runs (nruns RunRec) in shared memory.
 inline size_t den_box_smem(int th, int rows, int cols, int nw, int nruns) {
     return (size_t)(th + rows - 1) * den_pitch(cols) * 16 + (size_t)(nw + 4) * 4 + (size_t)nruns * 16 + 64;
@@ -164,11 +162,12 @@ static_assert(2 * fac_rpitch16(32) <= 4 * fac_rpitch(32) && 2 * fac_rpitch16(64)
 // barrier, then runs both column passes; the next pair writes the other two
 // buffers, so one barrier per two frames orders writes and reuse.
 constexpr int kFacHBufs = 4;
-// With phase planes (npl > 0) a CTA makes one frame at a time: one row-pass
-// buffer, then npl planes over the window, then the gathers.
+// With phase planes (npl > 0) a CTA makes two frames at a time: two
+// row-pass buffers, then npl planes per frame over the window, then the
+// gathers.
 inline size_t fac_smem_bytes(int tw, int bh, int ns, int kt, int npl = 0) {
     return 1024 + (size_t)ns * fac_stage_floats(tw, bh) * sizeof(float) +
-           (size_t)(npl > 0 ? 1 + npl : kFacHBufs) * bh * fac_hpitch(tw) * sizeof(float) +
+           (size_t)(npl > 0 ? 2 + 2 * npl : kFacHBufs) * bh * fac_hpitch(tw) * sizeof(float) +
            2 * (size_t)kFacRecordChunk * fac_block_bytes(kt, npl) +
            (size_t)ns * (sizeof(uint64_t) + sizeof(int)) + sizeof(int) + 64;
 }

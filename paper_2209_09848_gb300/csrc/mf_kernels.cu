@@ -230,21 +230,31 @@ __global__ void __launch_bounds__(256) k_denominator(const float *__restrict__ l
 // The same sums from a staged box.  A CTA owns `th` rows x kDenBoxCols start
 // pixels of one trajectory k: it copies the lambda box its start pixels
 // reach through G_k (rows dy0 .., columns x0 .. of the box, plus the tile),
-// G_k's weights and its runs into shared memory, then each warp takes rows
-// of the tile and runs the same register-window loop as k_denominator over
-// shared memory (conflict-free 128-bit reads, see den_chunk) instead of the
-// L1 cache, whose 32-byte sectors the lanes' 16-byte reads 32 bytes apart
-// used only half of.  Same FP32 products, same FP64 accumulation.
-__global__ void __launch_bounds__(1024) k_den_box(const float *__restrict__ lam, int64_t lw, int64_t lh, int64_t pad,
-                                                 const RunRec *__restrict__ runs, const int32_t *__restrict__ run_off,
-                                                 const float *__restrict__ wts, const DenBox *__restrict__ boxes,
-                                                 int K, int64_t H, int64_t W, int nbx, int th,
-                                                 float *__restrict__ isd) {
+// G_k's weights and its runs into shared memory.  A thread then owns NO
+// consecutive start pixels of one tile row and slides an NO-wide register
+// window along each run, so that every 128-bit read of lambda feeds 4 NO
+// FMAs.  A warp covers 8 rows x 4 NO columns: the 8 threads of a quarter
+// warp hold the same columns of 8 consecutive rows, which an odd row pitch
+// (in 16-byte chunks) puts in 8 distinct bank groups, so the reads are
+// conflict-free at plain row-major addresses (base + chunk, no per-read
+// index arithmetic).  Same FP32 products, same FP64 accumulation as
+// k_denominator.
+template <int NO>
+__global__ void __launch_bounds__(32 * kDenBoxCols / NO) k_den_box(
+    const float *__restrict__ lam, int64_t lw, int64_t lh, int64_t pad, const RunRec *__restrict__ runs,
+    const int32_t *__restrict__ run_off, const float *__restrict__ wts, const DenBox *__restrict__ boxes, int K,
+    int64_t H, int64_t W, int nbx, int th, float *__restrict__ isd) {
+    static_assert(NO % 4 == 0 && kDenBoxCols % (4 * NO) == 0, "whole chunks, whole warps per 8 rows");
+    constexpr int WR = kDenBoxCols / (4 * NO);  // warps per 8 tile rows
+    constexpr int S = NO / 4 + 1;                // window slots of 4 values
     extern __shared__ __align__(16) float4 dsm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const int64_t py0 = (int64_t)(blockIdx.x / nbx) * th;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // tile row y and first column xs of this thread's NO start pixels
+    const int y = 8 * (warp / WR) + (lane & 7), xs = 4 * NO * (warp % WR) + NO * (lane >> 3);
+    const int64_t py = (int64_t)(blockIdx.x / nbx) * th + y;
     const int64_t px0 = (int64_t)(blockIdx.x % nbx) * kDenBoxCols;
     const int64_t P = H * W;
+    const bool vec = (W & 3) == 0;  // rows (and planes) start on 16-byte boundaries
     for (int k = blockIdx.y; k < K; k += gridDim.y) {
         const DenBox bx = boxes[k];
         const int R = th + bx.rows - 1, NC = (kDenBoxCols + bx.cols) / 4, PC = den_pitch(bx.cols);
@@ -253,71 +263,83 @@ __global__ void __launch_bounds__(1024) k_den_box(const float *__restrict__ lam,
         RunRec *rsm = reinterpret_cast<RunRec *>(wsm + bx.nw / 4);    // then the runs
         __syncthreads();                                               // the previous trajectory's reads are done
         // lambda rows py0 + dy0 .. of the padded image (zero beyond its last row)
-        const int64_t gy0 = py0 + bx.dy0 + pad, gx0 = px0 + bx.x0 + pad;
+        const int64_t gy0 = py - y + bx.dy0 + pad, gx0 = px0 + bx.x0 + pad;
         for (int i = threadIdx.x; i < R * NC; i += blockDim.x) {
             const int r = i / NC, j = i % NC;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gy0 + r < lh) v = __ldg(reinterpret_cast<const float4 *>(lam + (gy0 + r) * lw + gx0) + j);
-            dsm[(size_t)r * PC + den_chunk(j)] = v;
+            dsm[(size_t)r * PC + j] = v;
         }
         for (int i = threadIdx.x; i < bx.nw / 4; i += blockDim.x)
             wsm[i] = __ldg(reinterpret_cast<const float4 *>(wts + bx.w0) + i);
         for (int i = threadIdx.x; i < nr; i += blockDim.x) rsm[i] = runs[r0 + i];
         __syncthreads();
-        for (int y = warp; y < th; y += nwarp) {
-            const int64_t py = py0 + y;
-            if (py >= H) break;
-            double d[8];
-            float a[8];
+        if (py >= H) continue;
+        double d[NO];
+        float a[NO];
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                d[c] = 0.0;
-                a[c] = 0.f;
+        for (int c = 0; c < NO; c++) {
+            d[c] = 0.0;
+            a[c] = 0.f;
+        }
+        int taps = 0;
+        for (int r = 0; r < nr; r++) {
+            const RunRec rr = rsm[r];
+            // the thread's first chunk of the run
+            const float4 *row = dsm + (size_t)(y + rr.dy - bx.dy0) * PC + (rr.x0 - bx.x0 + xs) / 4;
+            const float4 *wp = wsm + (rr.woff - bx.w0) / 4;
+            // window of NO + 4 lambda values in S float4 slots that rotate:
+            // chunk ch (4 taps) uses slot ch mod S onwards and, before its
+            // FMAs, loads the slot S - 1 ahead; unrolled by S so that every
+            // register index is static
+            float v[4 * S];
+#pragma unroll
+            for (int q = 0; q < S - 1; q++) {
+                const float4 pq = row[q];
+                v[4 * q] = pq.x; v[4 * q + 1] = pq.y; v[4 * q + 2] = pq.z; v[4 * q + 3] = pq.w;
             }
-            int taps = 0;
-            for (int r = 0; r < nr; r++) {
-                const RunRec rr = rsm[r];
-                const float4 *row = dsm + (size_t)(y + rr.dy - bx.dy0) * PC;
-                const int j0 = (rr.x0 - bx.x0) / 4 + 2 * lane;  // the lane's first chunk
-                const float4 *wp = wsm + (rr.woff - bx.w0) / 4;
-                float v[12];
-                {
-                    const float4 p0 = row[den_chunk(j0)], p1 = row[den_chunk(j0 + 1)];
-                    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
-                    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
-                }
-                for (int ch = 0; ch < rr.nch; ch += 3) {
+            for (int ch = 0; ch < rr.nch; ch += S) {
 #pragma unroll
-                    for (int u = 0; u < 3; u++) {
-                        if (ch + u < rr.nch) {
-                            const float4 pn = row[den_chunk(j0 + ch + u + 2)];
-                            const int ns = ((u + 2) % 3) * 4;
-                            v[ns] = pn.x; v[ns + 1] = pn.y; v[ns + 2] = pn.z; v[ns + 3] = pn.w;
-                            const float4 w4 = wp[ch + u];
-                            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+                for (int u = 0; u < S; u++) {
+                    if (ch + u < rr.nch) {
+                        const float4 pn = row[ch + u + S - 1];
+                        const int ns = ((u + S - 1) % S) * 4;  // slot receiving columns 4 (ch + u + S - 1) ..
+                        v[ns] = pn.x; v[ns + 1] = pn.y; v[ns + 2] = pn.z; v[ns + 3] = pn.w;
+                        const float4 w4 = wp[ch + u];
+                        const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                            for (int i = 0; i < 4; i++)
+                        for (int i = 0; i < 4; i++)
 #pragma unroll
-                                for (int c = 0; c < 8; c++) a[c] = fmaf(w[i], v[(4 * u + i + c) % 12], a[c]);
-                        }
+                            for (int c = 0; c < NO; c++) a[c] = fmaf(w[i], v[(4 * u + i + c) % (4 * S)], a[c]);
                     }
                 }
-                taps += rr.nch * 4;
-                if (taps >= kDenTaps) {
+            }
+            taps += rr.nch * 4;
+            if (taps >= kDenTaps) {
 #pragma unroll
-                    for (int c = 0; c < 8; c++) {
-                        d[c] += (double)a[c];
-                        a[c] = 0.f;
-                    }
-                    taps = 0;
+                for (int c = 0; c < NO; c++) {
+                    d[c] += (double)a[c];
+                    a[c] = 0.f;
                 }
+                taps = 0;
             }
+        }
+        float o[NO];
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                const double dd = d[c] + (double)a[c];
-                const int64_t px = px0 + 8 * lane + c;
-                if (px < W) isd[(int64_t)k * P + py * W + px] = dd > 0.0 ? rsqrtf((float)dd) : 0.f;
-            }
+        for (int c = 0; c < NO; c++) {
+            const double dd = d[c] + (double)a[c];
+            o[c] = dd > 0.0 ? rsqrtf((float)dd) : 0.f;
+        }
+        const int64_t px = px0 + xs;
+        float *dst = isd + (int64_t)k * P + py * W + px;
+        if (vec && px + NO <= W) {
+#pragma unroll
+            for (int q = 0; q < NO / 4; q++)
+                reinterpret_cast<float4 *>(dst)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < NO; c++)
+                if (px + c < W) dst[c] = o[c];
         }
     }
 }
@@ -867,19 +889,18 @@ int enqueue_pre(const SearchArgs &a, cudaStream_t stream, char *err, size_t errl
     MF_CHECK_LAUNCH("k_weight");
     if (tab.den_th > 0) {
         // staged: one CTA per (tile of den_th x 256 start pixels, trajectory)
-        static_assert(kDenBoxCols == 256, "a warp covers 256 start pixels of a row");
         const int th = tab.den_th;
         const int nbx = (int)((W + kDenBoxCols - 1) / kDenBoxCols);
         const int nby = (int)((H + th - 1) / th);
         dim3 grid((unsigned)(nbx * nby), (unsigned)std::min(tab.K, 65535));
-        cudaError_t ea = cudaFuncSetAttribute(k_den_box, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t ea = cudaFuncSetAttribute(k_den_box<kDenOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)tab.den_smem);
         if (ea != cudaSuccess) {
             snprintf(err, errlen, "cudaFuncSetAttribute(k_den_box): %s", cudaGetErrorString(ea));
             return (int)ea;
         }
         LaunchScope ls(kKDenominator, stream);
-        k_den_box<<<grid, 32 * th, tab.den_smem, stream>>>(
+        k_den_box<kDenOut><<<grid, th * kDenBoxCols / kDenOut, tab.den_smem, stream>>>(
             lam, L.lam_w, L.lam_h, L.pad, tab.d_runs, tab.d_run_off, tab.d_wts, tab.d_boxes, tab.K, H, W, nbx, th,
             isd);
         MF_CHECK_LAUNCH("k_den_box");

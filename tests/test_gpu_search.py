@@ -213,20 +213,26 @@ def test_unusable_sigma_is_masked(mf, oracle):
 
 def test_denominator_staged_and_unstaged(mf, oracle):
     # the paper's slow movers: each CTA stages the lambda box its trajectory
-    # reaches in shared memory; movers so fast that the box cannot fit go
-    # through the unstaged denominator -- both match the oracle
+    # reaches in shared memory, in tiles of 32, 16 or 8 rows as the box
+    # allows; movers so fast that the box cannot fit go through the unstaged
+    # denominator -- all match the oracle, for widths with a ragged last
+    # 256-column tile that are (292: 16-byte row stores) and are not (290) a
+    # multiple of four
     from paper_2209_09848_gb300 import synth
-    T, H, W = 30, 70, 290
-    c = synth.small_case(T, H, W, 23, mask_frac=0.03, movers=2)
-    lam = oracle.inverse_variance(c["sigma"], c["mask"])
-    for vx, vy, staged in (([0.3, -0.2, 0.1, 0.0], [0.1, 0.25, -0.3, 0.05], True),
-                           ([8.0, -7.0, 0.3], [8.0, 6.0, -0.2], False)):
-        table = mf.prf_table_create(vx, vy, T)
-        assert (table.info()["den_tile_h"] > 0) == staged
-        sh, tp = oracle.trajectory_table(vx, vy, T)
-        N, D = oracle.search_full(c["res"], lam, sh, tp)
-        smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
-        check_search(smax, amax, sall, N, D, oracle, label="staged denominator %s" % staged)
+    T = 30
+    for H, W in ((70, 290), (45, 292)):
+        c = synth.small_case(T, H, W, 23, mask_frac=0.03, movers=2)
+        lam = oracle.inverse_variance(c["sigma"], c["mask"])
+        for vx, vy, th in (([0.3, -0.2, 0.1, 0.0], [0.1, 0.25, -0.3, 0.05], 32),
+                           ([0.3, 0.0], [0.1, 6.0], 16),
+                           ([0.3, 0.0], [0.1, -6.3], 8),
+                           ([8.0, -7.0, 0.3], [8.0, 6.0, -0.2], 0)):
+            table = mf.prf_table_create(vx, vy, T)
+            assert table.info()["den_tile_h"] == th
+            sh, tp = oracle.trajectory_table(vx, vy, T)
+            N, D = oracle.search_full(c["res"], lam, sh, tp)
+            smax, amax, sall = _run(mf, c["res"], c["sigma"], c["mask"], table)
+            check_search(smax, amax, sall, N, D, oracle, label="denominator tile %d, %d x %d" % (th, H, W))
 
 
 def test_empty_frame_is_a_no_op(mf):
