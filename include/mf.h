@@ -163,7 +163,7 @@ mf_status mf_prf_table_create(const mf_prf_params *prf, const double *vx, const 
  * kernel = 0 selects the general kernel.
  *
  * Factored kernel: group = trajectories per CTA (all with one v_x), tile_h a
- * multiple of 32, tile_w 32 or 64, with group * tile_h / 32 * tile_w / 32 <= 16
+ * multiple of 32, tile_w 32 or 64, with group * tile_h / 32 * tile_w / 32 <= 20
  * warps; stages = frame windows in flight (2..6); segments = number of
  * consecutive frame ranges the frames are split into (1..16): within a
  * segment a CTA follows each trajectory from where it stands at the

@@ -522,8 +522,8 @@ __device__ __forceinline__ bool fac_tile(const CUtensorMap &ymap, const FacParam
 }
 
 template <int TW, int TAPS, typename E>
-__global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant__ CUtensorMap ymap,
-                                                          const FacParams p) {
+__global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
+    k_numerator_fac(const __grid_constant__ CUtensorMap ymap, const FacParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     fac_tile<TW, TAPS, E>(ymap, p, (long long)blockIdx.x, smem);
@@ -531,8 +531,8 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac(const __grid_constant_
 
 // The factored numerator with phase planes (phase-quantised banks).
 template <int TW>
-__global__ void __launch_bounds__(512, 1) k_numerator_fac_planes(const __grid_constant__ CUtensorMap ymap,
-                                                                 const FacParams p) {
+__global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
+    k_numerator_fac_planes(const __grid_constant__ CUtensorMap ymap, const FacParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     fac_tile<TW, 5, float, true>(ymap, p, (long long)blockIdx.x, smem);
@@ -542,10 +542,9 @@ __global__ void __launch_bounds__(512, 1) k_numerator_fac_planes(const __grid_co
 // takes (search, tile, group) work entries from a global counter until the
 // list is exhausted, running the same per-tile code as k_numerator_fac.
 template <int TW, typename E>
-__global__ void __launch_bounds__(512, 1) k_numerator_fac_batch(const CUtensorMap *__restrict__ maps,
-                                                                const FacBatchItem *__restrict__ items,
-                                                                int n_items, long long total,
-                                                                unsigned long long *counter) {
+__global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
+    k_numerator_fac_batch(const CUtensorMap *__restrict__ maps, const FacBatchItem *__restrict__ items, int n_items,
+                          long long total, unsigned long long *counter) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ long long work;

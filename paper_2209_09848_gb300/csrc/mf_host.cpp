@@ -310,7 +310,7 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
         std::vector<int32_t> seg_qy, seg_ref;
         std::vector<std::vector<std::pair<int, int>>> hist;
         int spread_max = 0, G = 0;
-        for (int kt = 1; kt <= 16; kt++) {
+        for (int kt = 1; kt <= mf::kFacMaxWarps; kt++) {
             if (t.forced_group && kt != t.forced_group) continue;
             // phase planes: at most one per rounded y-phase (Q + 1 of them) or
             // per trajectory of the CTA, whichever is fewer
@@ -319,11 +319,12 @@ bool plan_factored(const mf_prf_table &t, mf::Plan &out) {
             for (int tw : {32, 64}) {
                 if (t.forced_tw && tw != t.forced_tw) continue;
                 const int per = kt * (tw / 32);  // warps per 32 rows of tile
-                if (per > 16) continue;
+                if (per > mf::kFacMaxWarps) continue;
                 if (t.forced_th) {
-                    if (t.forced_th / 32 * per <= 16) geos.push_back({t.forced_th, tw});
+                    if (t.forced_th / 32 * per <= mf::kFacMaxWarps) geos.push_back({t.forced_th, tw});
                 } else {
-                    for (int th = std::min(224, 32 * (16 / per)); th >= 32; th -= 32) geos.push_back({th, tw});
+                    for (int th = std::min(224, 32 * (mf::kFacMaxWarps / per)); th >= 32; th -= 32)
+                        geos.push_back({th, tw});
                 }
             }
             if (geos.empty()) continue;
@@ -1133,7 +1134,7 @@ static mf_status apply_opts(mf_prf_table *t, const mf_plan_opts *opts) {
         delete t;
         return fail(MF_EINVAL, "kernel 3 (phase planes) needs a phase-quantised bank (phase_steps > 0)");
     }
-    if (opts->group < 0 || opts->group > 16 || opts->tile_h < 0 || opts->tile_h % 32 != 0 ||
+    if (opts->group < 0 || opts->group > mf::kFacMaxWarps || opts->tile_h < 0 || opts->tile_h % 32 != 0 ||
         (opts->tile_w != 0 && opts->tile_w != 32 && opts->tile_w != 64) || opts->stages < 0 ||
         opts->stages == 1 || opts->stages > mf::kFacMaxStages) {
         delete t;

@@ -27,6 +27,10 @@ constexpr int kLoadRows = 8;         // window rows are a multiple of this
 constexpr int kFrameBlock = 16;      // frames per FP32 partial sum in the numerator
 constexpr int kDenTaps = 256;        // denominator taps per FP32 partial before the FP64 add
 constexpr int kDenCols = 256;        // denominator: start pixels per warp (one row)
+// Warps of a factored-numerator CTA at most (its trajectories x sub-tiles,
+// rounded up to a multiple of 4): 20 warps fit the register file at 96
+// registers a thread, which holds the blocked sums of a lane's 32 outputs.
+constexpr int kFacMaxWarps = 20;
 constexpr int kSmemBudget = 220 * 1024;  // dynamic shared memory of one CTA per SM
 
 // CTA shapes: trajectories per CTA x sub-tiles across x sub-tiles down = kWarps.

@@ -372,7 +372,7 @@ def test_factored_needs_separable_table(mf):
     t = mf.prf_table_create_custom(sh, tp)
     assert t.info()["kernel"] == 1
     with pytest.raises(mf.MFError):
-        mf.prf_table_create(np.zeros(2), np.zeros(2), 4, kernel=2, group=17)
+        mf.prf_table_create(np.zeros(2), np.zeros(2), 4, kernel=2, group=21)
 
 
 @pytest.mark.parametrize("layout", [{}, {"kernel": 1}, {"kernel": 2, "group": 3, "tile_w": 64},

@@ -23,7 +23,7 @@ def test_paper_grid_plans_factored(mf):
     info = mf.prf_plan(vx, vy, 1000)
     assert info["kernel"] == 2
     kt, th, tw = info["warps_per_group"], info["tile_h"], info["tile_w"]
-    assert kt * (th // 32) * (tw // 32) <= 16 and th % 32 == 0 and tw in (32, 64)
+    assert kt * (th // 32) * (tw // 32) <= 20 and th % 32 == 0 and tw in (32, 64)
     # groups never mix v_x: each of the 10 columns of the grid splits on its own
     assert info["groups"] == 10 * -(-10 // kt)
     assert info["window_rows"] <= 256 and info["smem_bytes"] <= 227 * 1024
@@ -60,7 +60,7 @@ def test_forced_geometry_is_reported(mf):
     assert info["window_rows"] == 128 + 4 + spread
 
 
-@pytest.mark.parametrize("opts", [dict(kernel=3), dict(kernel=2, group=17), dict(kernel=2, tile_h=48),
+@pytest.mark.parametrize("opts", [dict(kernel=3), dict(kernel=2, group=21), dict(kernel=2, tile_h=48),
                                   dict(kernel=2, tile_w=96), dict(kernel=2, stages=1), dict(kernel=2, stages=7),
                                   dict(kernel=2, segments=17), dict(kernel=2, segments=-1)])
 def test_invalid_layout_options(mf, opts):
@@ -117,11 +117,11 @@ def test_measured_workloads_keep_their_plans(mf):
     info = mf.prf_plan(vx, vy, 1000)
     got = {k: info[k] for k in ("kernel", "groups", "warps_per_group", "tile_h", "tile_w", "window_rows",
                                 "stages", "time_segments", "taps")}
-    assert got == {"kernel": 2, "groups": 20, "warps_per_group": 5, "tile_h": 96, "tile_w": 32,
-                   "window_rows": 130, "stages": 6, "time_segments": 3, "taps": 5}
+    assert got == {"kernel": 2, "groups": 10, "warps_per_group": 10, "tile_h": 64, "tile_w": 32,
+                   "window_rows": 136, "stages": 5, "time_segments": 3, "taps": 5}
     vx, vy = _grid(40, 25)
     info = mf.prf_plan(vx, vy, 1000)
-    assert (info["groups"], info["warps_per_group"], info["tile_h"], info["time_segments"]) == (80, 13, 32, 2)
+    assert (info["groups"], info["warps_per_group"], info["tile_h"], info["time_segments"]) == (120, 9, 64, 2)
 
 
 def test_plan_with_frame_model(mf):
