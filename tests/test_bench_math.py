@@ -43,4 +43,4 @@ def test_traffic_comes_from_the_committed_summaries(bench):
         m = re.search(r"^traffic_bytes_per_unit:\s*(\S+)", text, re.M)
         want = None if m is None or m.group(1) == "null" else float(m.group(1))
         assert bench._traffic_from_profiles(kernel) == want
-    assert bench._traffic_from_profiles(2) == pytest.approx(0.1232)
+    assert bench._traffic_from_profiles(2) == pytest.approx(0.1070)
