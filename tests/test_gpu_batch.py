@@ -33,6 +33,7 @@ def _items(mf):
         (20, 77, 140, (2, 5), 0.4, torch.float32, 0.01, dict(kernel=2, group=5, tile_h=64, tile_w=32)),
         (12, 100, 61, (3, 3), 0.3, torch.float32, 0.0, dict(kernel=2, group=1, tile_h=32, tile_w=32)),
         (18, 90, 150, (2, 3), 0.3, torch.float32, 0.02, dict(kernel=2, group=3, tile_w=64)),
+        (22, 140, 70, (3, 4), 0.3, torch.bfloat16, 0.01, dict(kernel=2, group=10, tile_h=64)),  # 20 warps
     ]
     out = []
     for i, (T, H, W, (nx, ny), vm, dt, mfrac, layout) in enumerate(specs):
@@ -96,6 +97,17 @@ def test_batch_equals_individual_searches(mf, oracle):
     N, D = oracle.search_weighted(q, beta, lam, sh, tp)
     gm, ga, gall = b.outputs[1]
     check_search(gm.cpu().numpy(), ga.cpu().numpy(), gall.cpu().numpy(), N, D, oracle, label="batch item 1 (bf16)")
+    # and the 20-warp bf16 item (whole v_x classes on 64-row tiles)
+    it = items[-1]
+    inf = it["table"].info()
+    assert (inf["kernel"], inf["warps_per_group"], inf["tile_h"], inf["tile_w"]) == (2, 10, 64, 32)
+    sh, tp = oracle.trajectory_table(it["vx"], it["vy"], it["data"].shape[0])
+    lam = oracle.inverse_variance(it["c"]["sigma"], it["c"]["mask"])
+    q, beta = oracle.weighted_stack16(it["data"].float().cpu().numpy(), it["c"]["sigma"], it["c"]["mask"], None,
+                                      "bf16")
+    N, D = oracle.search_weighted(q, beta, lam, sh, tp)
+    gm, ga, gall = b.outputs[-1]
+    check_search(gm.cpu().numpy(), ga.cpu().numpy(), gall.cpu().numpy(), N, D, oracle, label="batch item (20 warps)")
     b.destroy()
 
 

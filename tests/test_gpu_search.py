@@ -310,6 +310,13 @@ FACTORED = [
     (16, 32, 32, 2, 1),
     (2, 32, 64, 0, 3),
     (4, 64, 32, 3, 5),
+    # 20 warps, the most a CTA has: whole classes on 64-row tiles (the paper
+    # grid's layout), on 32 x 64 tiles, on 32-row tiles with empty slots, and
+    # 5 trajectories on 128-row tiles
+    (10, 64, 32, 0, 2),
+    (10, 32, 64, 0, 0),
+    (20, 32, 32, 2, 3),
+    (5, 128, 32, 3, 0),
 ]
 
 
