@@ -524,10 +524,12 @@ mf_status mf_profile_read(mf_profile *out, int32_t reset);
 
 /* Batched searches (not in the paper).  Many searches -- uneven cutouts,
  * each with its own stack, noise map, mask, filter bank and outputs -- run as
- * one CUDA graph: preparation kernels spread over side streams, one
- * persistent numerator launch per CTA shape present in the batch (one CTA
- * per SM taking (search, tile, trajectory group) work from a global
- * counter), then per-search finalisation.  Each search's results equal those
+ * one CUDA graph: preparation kernels spread over side streams, persistent
+ * numerator launches (one CTA per SM taking (search, tile, trajectory
+ * group) work from a global counter: one launch per general CTA shape
+ * present, and for the factored kernel one per time segment, tile width and
+ * stack element type present, in segment order, each carrying at most 192
+ * searches in its parameters), then per-search finalisation.  Each search's results equal those
  * of mf_search on the same inputs (same per-tile code and summation order).
  *
  * Usage: mf_batch_create; mf_batch_add per search (pointers are the caller's
@@ -551,9 +553,10 @@ mf_status mf_batch_run(mf_batch *batch, mf_stream stream);
  * without waiting: *done = 1 (finished, or never run) or 0 (in flight).
  * Errors: MF_EINVAL (NULL pointers), MF_ECUDA (a failed launch surfaced). */
 mf_status mf_batch_poll(const mf_batch *batch, int32_t *done);
-/* Number of searches, of persistent numerator launches (one per general
- * CTA shape and one per factored tile width present) and whether the graph
- * has been captured. */
+/* Number of searches, of CTA shapes present (one per general CTA shape and
+ * one per factored tile width; the persistent launches of a factored shape
+ * follow its time segments, element types and the 192 searches a launch
+ * carries) and whether the graph has been captured. */
 mf_status mf_batch_info(const mf_batch *batch, int32_t *items, int32_t *shape_groups, int32_t *graph_ready);
 void mf_batch_destroy(mf_batch *batch);
 

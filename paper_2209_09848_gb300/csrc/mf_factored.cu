@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include "mf_device.cuh"
@@ -543,8 +544,8 @@ __global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
 // list is exhausted, running the same per-tile code as k_numerator_fac.
 template <int TW, typename E>
 __global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
-    k_numerator_fac_batch(const CUtensorMap *__restrict__ maps, const FacBatchItem *__restrict__ items, int n_items,
-                          long long total, unsigned long long *counter) {
+    k_numerator_fac_batch(const CUtensorMap *__restrict__ maps, const __grid_constant__ FacBatchArgs a,
+                          unsigned long long *counter) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ long long work;
@@ -552,10 +553,10 @@ __global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
     for (;;) {
         if (threadIdx.x == 0) {
             const long long w = (long long)atomicAdd(counter, 1ull);
-            int lo = 0, hi = n_items - 1;  // last item whose cta_begin <= w
+            int lo = 0, hi = a.n_items - 1;  // last item whose cta_begin <= w
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (items[mid].cta_begin <= w) lo = mid;
+                if (a.items[mid].cta_begin <= w) lo = mid;
                 else hi = mid - 1;
             }
             work = w;
@@ -565,11 +566,11 @@ __global__ void __launch_bounds__(32 * kFacMaxWarps, 1)
         const long long w = work;
         const int i = item;
         __syncthreads();
-        if (w >= total) break;
-        const FacParams &p = items[i].p;
+        if (w >= a.total) break;
+        const FacParams &p = a.items[i].p;
         // the five-tap code: single-tap footprints give the same sums (zero
         // taps add exact zeros), so a batch of mixed tables needs one kernel
-        if (!fac_tile<TW, 5, E>(maps[i], p, w - items[i].cta_begin, smem)) break;
+        if (!fac_tile<TW, 5, E>(maps[i], p, w - a.items[i].cta_begin, smem)) break;
         __syncthreads();
     }
 }
@@ -648,7 +649,7 @@ int fac_finalize_enqueue(const float *plane, const float *isd, int K, int64_t P,
 
 namespace {
 
-typedef void (*FacBatchKernel)(const CUtensorMap *, const FacBatchItem *, int, long long, unsigned long long *);
+typedef void (*FacBatchKernel)(const CUtensorMap *, const FacBatchArgs, unsigned long long *);
 typedef void (*FacKernel)(const CUtensorMap, const FacParams);
 
 FacBatchKernel pick_fac_batch(int tw, int etype) {
@@ -688,8 +689,17 @@ int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, 
     FacBatchKernel kern = pick_fac_batch(tw, etype);
     cudaError_t e;
     if (total <= 0 || grid <= 0) return 0;
-    kern<<<grid, warps * 32, smem, (cudaStream_t)stream>>>(reinterpret_cast<const CUtensorMap *>(maps), items,
-                                                           n_items, total, counter);
+    if (n_items < 1 || n_items > kFacBatchArgItems) {
+        snprintf(err, errlen, "k_numerator_fac_batch: %d searches in one launch (1 .. %d)", n_items,
+                 kFacBatchArgItems);
+        return (int)cudaErrorInvalidValue;
+    }
+    static thread_local FacBatchArgs args;  // 28 KB: off the stack
+    std::memcpy(args.items, items, (size_t)n_items * sizeof(FacBatchItem));
+    args.total = total;
+    args.n_items = n_items;
+    kern<<<grid, warps * 32, smem, (cudaStream_t)stream>>>(reinterpret_cast<const CUtensorMap *>(maps), args,
+                                                           counter);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(err, errlen, "k_numerator_fac_batch: %s", cudaGetErrorString(e));

@@ -426,9 +426,21 @@ struct FacBatchItem {
     FacParams p;
     long long cta_begin;  // first entry of this search in the batch's work list
 };
+// A persistent launch's searches, passed by value in the launch's parameter
+// space (where the one-launch kernel finds its FacParams), at most
+// kFacBatchArgItems per launch.
+constexpr int kFacBatchArgItems = 192;
+struct FacBatchArgs {
+    FacBatchItem items[kFacBatchArgItems];
+    long long total;  // work entries of the launch
+    int n_items;
+};
+static_assert(sizeof(FacBatchArgs) <= 32000, "within the 32 KB of kernel parameters");
 // Shared-memory limit of the persistent kernel (set once, outside capture).
 // etype: element type of the weighted stack, an mf_dtype (MF_F32, MF_BF16, MF_F16).
 int fac_batch_attr(int tw, int etype, size_t smem, char *err, size_t errlen);
+// items: host array of n_items (1 .. kFacBatchArgItems) searches, copied
+// into the launch's parameters.
 int fac_batch_enqueue(const void *maps, const FacBatchItem *items, int n_items, long long total,
                       unsigned long long *counter, int tw, int etype, int warps, size_t smem, int grid, void *stream,
                       char *err, size_t errlen);

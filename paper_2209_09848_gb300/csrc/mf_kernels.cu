@@ -1142,6 +1142,7 @@ struct BatchDevice {
     std::vector<FacGroup> fac;
     CUtensorMap *d_fmaps = nullptr;
     FacBatchItem *d_fitems = nullptr;
+    std::vector<FacBatchItem> h_fitems;  // the same, passed by value to each launch
     unsigned long long *d_fcounters = nullptr;  // one per group
     CUtensorMap *d_maps = nullptr;
     BatchItem *d_items = nullptr;
@@ -1232,6 +1233,16 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
                 grp.warps = std::max(grp.warps, pl.launch_warps());
                 fmaps.push_back(m);
                 fitems.push_back(fi);
+                if ((int)fitems.size() - grp.first == kFacBatchArgItems) {
+                    // a launch takes at most kFacBatchArgItems searches: the
+                    // rest of this segment goes to the next launch
+                    grp.count = kFacBatchArgItems;
+                    b->fac.push_back(grp);
+                    grp.first = (int)fitems.size();
+                    grp.total = 0;
+                    grp.smem = 0;
+                    grp.warps = 0;
+                }
             }
             grp.count = (int)fitems.size() - grp.first;
             if (grp.count > 0) b->fac.push_back(grp);
@@ -1246,6 +1257,7 @@ int batch_build(const SearchArgs *items, int n, BatchDevice **out, char *err, si
         e = cudaMemcpy(b->d_fmaps, fmaps.data(), fmaps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !fitems.empty())
         e = cudaMemcpy(b->d_fitems, fitems.data(), fitems.size() * sizeof(FacBatchItem), cudaMemcpyHostToDevice);
+    b->h_fitems = fitems;
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1326,7 +1338,7 @@ int batch_enqueue(BatchDevice *b, const SearchArgs *items, int n, void *stream_v
         const auto &grp = b->fac[gi];
         const int grid = (int)std::min<long long>(grp.total, (long long)b->sms);
         LaunchScope ls(kKNumerator, stream);
-        int rc = fac_batch_enqueue(b->d_fmaps + grp.first, b->d_fitems + grp.first, grp.count, grp.total,
+        int rc = fac_batch_enqueue(b->d_fmaps + grp.first, b->h_fitems.data() + grp.first, grp.count, grp.total,
                                    b->d_fcounters + gi, grp.tw, grp.etype, grp.warps, grp.smem, grid, stream, err,
                                    errlen);
         if (rc) return rc;

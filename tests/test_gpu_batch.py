@@ -126,6 +126,34 @@ def test_batch_argument_errors(mf):
     b.destroy()
 
 
+def test_batch_splits_launches_past_the_parameter_limit(mf):
+    # a persistent launch carries at most 192 searches in its parameters: 200
+    # searches of one layout take two launches of one time segment, and every
+    # output equals the search on its own
+    from paper_2209_09848_gb300 import synth
+    T, H, W = 10, 24, 40
+    vx, vy = synth.velocity_grid(2, 2, -0.2, 0.2)
+    table = mf.prf_table_create(vx, vy, T, kernel=2)
+    assert table.info()["time_segments"] == 1
+    b = mf.Batch()
+    ins = []
+    for i in range(200):
+        c = synth.small_case(T, H, W, 500 + i, movers=1)
+        r = torch.from_numpy(c["res"]).cuda()
+        s = torch.from_numpy(c["sigma"]).cuda()
+        ins.append((r, s))
+        b.add(r, s, table)
+    b.prepare()
+    b.run()
+    torch.cuda.synchronize()
+    assert mf.device_status() == 0
+    for (r, s), (gm, ga, _) in zip(ins, b.outputs):
+        am, aa, _ = mf.search(r, s, table)
+        torch.cuda.synchronize()
+        assert torch.equal(gm, am) and torch.equal(ga, aa)
+    b.destroy()
+
+
 def test_autotuner_picks_a_timed_layout(mf, oracle):
     """The autotuner times the factored and general layouts, caches the
     winner per bucket, and the tuned table searches correctly."""
