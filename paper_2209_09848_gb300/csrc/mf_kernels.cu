@@ -1502,10 +1502,22 @@ __device__ __forceinline__ double to_f64(TIn v) { return (double)to_f32(v); }
 
 // One warp per candidate: N and D in FP64 from the master stack, the FP64
 // footprints and the FP64 inverse variance.
+// FP64 inverse variance of every pixel for the re-score: 1 / (s * s) from
+// the FP32 noise value s in FP64, 0 where the pixel is masked or s is not a
+// usable noise value (s <= 0 or not finite; a finite FP32 s never makes the
+// FP64 quotient 0).  Computed once per re-score instead of per tap.
+__global__ void k_lambda64(const float *__restrict__ sigma, const uint8_t *__restrict__ mask, int64_t P,
+                           double *__restrict__ lam64) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = (double)sigma[i];
+        lam64[i] = ((mask && mask[i]) || !(s > 0.0) || !isfinite(s)) ? 0.0 : 1.0 / (s * s);
+    }
+}
+
 template <typename TIn>
 __global__ void k_rescore(const TIn *__restrict__ r, int64_t fstride, int64_t rstride,
-                          const float *__restrict__ scale, const float *__restrict__ sigma,
-                          const uint8_t *__restrict__ mask, const double *__restrict__ taps64,
+                          const float *__restrict__ scale, const double *__restrict__ lam64,
+                          const double *__restrict__ taps64,
                           const int32_t *__restrict__ shifts, const float *__restrict__ snr_max,
                           const int32_t *__restrict__ argmax, const unsigned long long *__restrict__ keys,
                           const SelState *st, unsigned int cap, int T, int64_t H, int64_t W,
@@ -1532,9 +1544,8 @@ __global__ void k_rescore(const TIn *__restrict__ r, int64_t fstride, int64_t rs
                 const int64_t qx = px + sx + a - 2;
                 if (qx < 0 || qx >= W) continue;
                 const int64_t q = qy * W + qx;
-                const double s = (double)sigma[q];
-                if ((mask && mask[q]) || !(s > 0.0) || !isfinite(s)) continue;
-                const double lam = 1.0 / (s * s);
+                const double lam = lam64[q];
+                if (lam == 0.0) continue;  // masked, or no usable noise value
                 const double wt = w[b * 5 + a];
                 num += wt * lam * (sc * to_f64(r[t * fstride + qy * rstride + qx]));
                 den += wt * wt * lam;
@@ -1646,21 +1657,27 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
         const int threads = 256;
         const int blocks = (int)(((int64_t)a.k_top * 32 + threads - 1) / threads);
         LaunchScope ls(kKRescore, stream);
+        // the selection is done with the per-pixel keys: their space holds
+        // the FP64 inverse variance (P doubles) the re-score reads
+        static_assert(sizeof(double) == sizeof(unsigned long long), "one double per key");
+        double *lam64 = reinterpret_cast<double *>(a.ws + L.keys_off);
+        k_lambda64<<<grid_for(P, 256), 256, 0, stream>>>(a.sigma, a.mask, P, lam64);
+        MF_CHECK_LAUNCH("k_lambda64");
         const int64_t fs = st.frame_stride, rs = st.row_stride;
         switch (st.dtype) {
             case MF_F32:
                 k_rescore<float><<<blocks, threads, 0, stream>>>(
-                    (const float *)st.data, fs, rs, st.frame_scale, a.sigma, a.mask, tab.d_taps64, tab.d_shifts,
+                    (const float *)st.data, fs, rs, st.frame_scale, lam64, tab.d_taps64, tab.d_shifts,
                     a.snr_max, a.argmax, top, sst, (unsigned)a.k_top, tab.T, H, W, a.out, a.n_out);
                 break;
             case MF_BF16:
                 k_rescore<__nv_bfloat16><<<blocks, threads, 0, stream>>>(
-                    (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, a.sigma, a.mask, tab.d_taps64,
+                    (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, lam64, tab.d_taps64,
                     tab.d_shifts, a.snr_max, a.argmax, top, sst, (unsigned)a.k_top, tab.T, H, W, a.out, a.n_out);
                 break;
             default:
                 k_rescore<__half><<<blocks, threads, 0, stream>>>(
-                    (const __half *)st.data, fs, rs, st.frame_scale, a.sigma, a.mask, tab.d_taps64, tab.d_shifts,
+                    (const __half *)st.data, fs, rs, st.frame_scale, lam64, tab.d_taps64, tab.d_shifts,
                     a.snr_max, a.argmax, top, sst, (unsigned)a.k_top, tab.T, H, W, a.out, a.n_out);
                 break;
         }
