@@ -111,39 +111,70 @@ __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { retu
 template <>
 __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
 
-template <typename TIn, typename TOut>
+// Four consecutive stack values as FP32, from one 128-bit (FP32) or 64-bit
+// (16-bit types) read: p is aligned to four elements.
+template <typename T>
+__device__ __forceinline__ void load4_f32(const T *p, float v[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        const T *e = reinterpret_cast<const T *>(&q);
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = to_f32(e[j]);
+    }
+}
+
+// y_t = lambda * (scale_t * r_t) (16-bit outputs of an fp16 stack also times
+// 2^-e_t, exact).  A warp takes one (frame, row) at a time, so the row's
+// index split is made once per row; lanes walk the row four values each,
+// reading lambda and writing y with aligned vector accesses and the stack
+// with them too when its rows allow (VR: aligned base, strides multiples of
+// four elements).
+template <typename TIn, typename TOut, bool VR>
 __global__ void k_weight(const TIn *__restrict__ r, int64_t fstride, int64_t rstride,
                          const float *__restrict__ scale, const float *__restrict__ lam, int64_t pad, int64_t lw,
                          TOut *__restrict__ y, int64_t T, int64_t H, int64_t W, int64_t yp,
                          const unsigned int *lmax_bits, float *__restrict__ beta) {
     constexpr bool kHalfScaled = std::is_same<TOut, __half>::value;
     const float lmax = kHalfScaled ? __uint_as_float(*lmax_bits) : 0.f;
-    const int64_t wq = (W + 3) / 4;
-    const int64_t n = T * H * wq;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t xq = i % wq;
-        const int64_t rest = i / wq;
-        const int64_t yy = rest % H;
-        const int64_t t = rest / H;
+    const int64_t wq = (W + 3) / 4, rows = T * H;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t ri = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ri < rows; ri += nwarps) {
+        const int64_t t = ri / H, yy = ri - t * H;
         const float sc = scale ? scale[t] : 1.f;
         float inv = 1.f, bt = 1.f;
         if (kHalfScaled) bt = fp16_frame_beta(lmax, fabsf(sc), &inv);
-        if (beta && yy == 0 && xq == 0) beta[t] = bt;
-        const float *lrow = lam + (yy + pad) * lw + pad;
+        if (beta && yy == 0 && lane == 0) beta[t] = bt;
+        const float *lrow = lam + (yy + pad) * lw + pad;  // padded: columns W .. W + 3 exist
         const TIn *rrow = r + t * fstride + yy * rstride;
-        float o[4];
+        TOut *yrow = y + ri * yp;
+        for (int64_t xq = lane; xq < wq; xq += 32) {
+            const int64_t x0 = xq * 4;
+            const float4 l4 = *reinterpret_cast<const float4 *>(lrow + x0);
+            const float l[4] = {l4.x, l4.y, l4.z, l4.w};
+            float v[4];
+            if (VR && x0 + 4 <= W) {
+                load4_f32(rrow + x0, v);
+            } else {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int64_t x = xq * 4 + j;
-            o[j] = (x < W) ? lrow[x] * (sc * to_f32(rrow[x])) : 0.f;
-            if (kHalfScaled) o[j] *= inv;  // a power of two: exact
-        }
-        TOut *dst = y + (t * H + yy) * yp + xq * 4;
-        if (std::is_same<TOut, float>::value) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-        } else {
-            TOut q[4] = {from_f32<TOut>(o[0]), from_f32<TOut>(o[1]), from_f32<TOut>(o[2]), from_f32<TOut>(o[3])};
-            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(q);
+                for (int j = 0; j < 4; j++) v[j] = x0 + j < W ? to_f32(rrow[x0 + j]) : 0.f;
+            }
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                o[j] = (x0 + j < W) ? l[j] * (sc * v[j]) : 0.f;
+                if (kHalfScaled) o[j] *= inv;  // a power of two: exact
+            }
+            TOut *dst = yrow + x0;
+            if (std::is_same<TOut, float>::value) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+                TOut q[4] = {from_f32<TOut>(o[0]), from_f32<TOut>(o[1]), from_f32<TOut>(o[2]), from_f32<TOut>(o[3])};
+                *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(q);
+            }
         }
     }
 }
@@ -860,31 +891,30 @@ int enqueue_pre(const SearchArgs &a, cudaStream_t stream, char *err, size_t errl
     }
     MF_CHECK_LAUNCH("k_lambda");
 
-    const int64_t nw = T * H * ((W + 3) / 4);
     const int64_t fs = st.frame_stride, rs = st.row_stride;
     {
         LaunchScope ls(kKWeight, stream);
-        const int gw = grid_for(nw, 256);
+        const int gw = grid_for(T * H * 32, 256);  // a warp per (frame, row)
         const bool y16 = L.ybytes == 2;
-        if (st.dtype == MF_F32)
-            k_weight<float, float><<<gw, 256, 0, stream>>>((const float *)st.data, fs, rs, st.frame_scale, lam, L.pad,
-                                                           L.lam_w, (float *)y, T, H, W, L.y_pitch, lmax, beta);
-        else if (st.dtype == MF_BF16 && y16)
-            k_weight<__nv_bfloat16, __nv_bfloat16><<<gw, 256, 0, stream>>>(
-                (const __nv_bfloat16 *)st.data, fs, rs, st.frame_scale, lam, L.pad, L.lam_w, (__nv_bfloat16 *)y, T,
-                H, W, L.y_pitch, lmax, beta);
-        else if (st.dtype == MF_BF16)
-            k_weight<__nv_bfloat16, float><<<gw, 256, 0, stream>>>((const __nv_bfloat16 *)st.data, fs, rs,
-                                                                   st.frame_scale, lam, L.pad, L.lam_w, (float *)y,
-                                                                   T, H, W, L.y_pitch, lmax, beta);
-        else if (y16)
-            k_weight<__half, __half><<<gw, 256, 0, stream>>>((const __half *)st.data, fs, rs, st.frame_scale, lam,
-                                                             L.pad, L.lam_w, (__half *)y, T, H, W, L.y_pitch, lmax,
-                                                             beta);
-        else
-            k_weight<__half, float><<<gw, 256, 0, stream>>>((const __half *)st.data, fs, rs, st.frame_scale, lam,
-                                                            L.pad, L.lam_w, (float *)y, T, H, W, L.y_pitch, lmax,
-                                                            beta);
+        const size_t esz = st.dtype == MF_F32 ? 4 : 2;
+        // vector reads of the stack: aligned base, rows and frames on multiples of four elements
+        const bool vr = ((uintptr_t)st.data % (4 * esz)) == 0 && fs % 4 == 0 && rs % 4 == 0;
+        auto go = [&](auto tin, auto tout, auto vrc) {
+            using TI = decltype(tin);
+            using TO = decltype(tout);
+            k_weight<TI, TO, decltype(vrc)::value><<<gw, 256, 0, stream>>>(
+                (const TI *)st.data, fs, rs, st.frame_scale, lam, L.pad, L.lam_w, (TO *)y, T, H, W, L.y_pitch, lmax,
+                beta);
+        };
+        auto go2 = [&](auto tin, auto tout) {
+            if (vr) go(tin, tout, std::true_type{});
+            else go(tin, tout, std::false_type{});
+        };
+        if (st.dtype == MF_F32) go2(float{}, float{});
+        else if (st.dtype == MF_BF16 && y16) go2(__nv_bfloat16{}, __nv_bfloat16{});
+        else if (st.dtype == MF_BF16) go2(__nv_bfloat16{}, float{});
+        else if (y16) go2(__half{}, __half{});
+        else go2(__half{}, float{});
     }
     MF_CHECK_LAUNCH("k_weight");
     if (tab.den_th > 0) {
