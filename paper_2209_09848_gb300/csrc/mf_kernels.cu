@@ -1683,16 +1683,20 @@ int launch_rescore(const RescoreArgs &a, char *err, size_t errlen) {
     unsigned long long *top = reinterpret_cast<unsigned long long *>(a.ws + L.top_off);
     int rc = launch_select(a.snr_max, a.argmax, P, a.k_top, a.ws, L, stream, err, errlen);
     if (rc) return rc;
+    // the selection is done with the per-pixel keys: their space holds the
+    // FP64 inverse variance (P doubles) the re-score reads (both launches
+    // count as the re-score)
+    static_assert(sizeof(double) == sizeof(unsigned long long), "one double per key");
+    double *lam64 = reinterpret_cast<double *>(a.ws + L.keys_off);
+    {
+        LaunchScope ls(kKRescore, stream);
+        k_lambda64<<<grid_for(P, 256), 256, 0, stream>>>(a.sigma, a.mask, P, lam64);
+    }
+    MF_CHECK_LAUNCH("k_lambda64");
     {
         const int threads = 256;
         const int blocks = (int)(((int64_t)a.k_top * 32 + threads - 1) / threads);
         LaunchScope ls(kKRescore, stream);
-        // the selection is done with the per-pixel keys: their space holds
-        // the FP64 inverse variance (P doubles) the re-score reads
-        static_assert(sizeof(double) == sizeof(unsigned long long), "one double per key");
-        double *lam64 = reinterpret_cast<double *>(a.ws + L.keys_off);
-        k_lambda64<<<grid_for(P, 256), 256, 0, stream>>>(a.sigma, a.mask, P, lam64);
-        MF_CHECK_LAUNCH("k_lambda64");
         const int64_t fs = st.frame_stride, rs = st.row_stride;
         switch (st.dtype) {
             case MF_F32:
