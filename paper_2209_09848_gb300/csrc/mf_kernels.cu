@@ -1395,17 +1395,25 @@ namespace {
 __global__ void k_sel_keys(const float *__restrict__ snr_max, const int32_t *__restrict__ argmax, int64_t P,
                            unsigned long long *__restrict__ keys, unsigned int *__restrict__ hist,
                            SelState *st) {
+    unsigned int valid = 0;  // keys this thread made; summed per warp into st->total
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long key = 0ull;
-        if (argmax[i] >= 0) {
+        const bool ok = argmax[i] >= 0;
+        if (ok) {
             uint32_t b = __float_as_uint(snr_max[i]);
             b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
             key = ((unsigned long long)b << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
-            atomicAdd(&hist[key >> 48], 1u);
-            atomicAdd(&st->total, 1u);
+            valid++;
         }
+        // lanes of the warp that fall in the same bin add together: one
+        // atomic per (warp, bin), as neighbouring pixels often share a bin
+        const unsigned int bin = ok ? (unsigned int)(key >> 48) : 0xFFFFFFFFu;  // no key: a bin of its own
+        const unsigned int peers = __match_any_sync(__activemask(), bin);
+        if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned int)__popc(peers));
         keys[i] = key;
     }
+    valid = __reduce_add_sync(0xffffffffu, valid);  // blocks are whole warps
+    if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&st->total, valid);
 }
 
 // Histogram of the next 16 bits among keys that match the selected prefix.
