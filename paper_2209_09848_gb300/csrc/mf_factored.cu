@@ -14,15 +14,18 @@
 // boxes, mbarriers with bounded waits); the CTA's threads split both row
 // passes into items of 16 outputs (the column phase is applied as an item
 // reads the window, so the row-pass buffer holds exactly the tile's columns;
-// items go to the last warps first, so a row-pass-only 16th warp and the
-// warps of empty slots take them); one CTA barrier; thread 0 refills both
+// items go to the last warps first, so the row-pass-only warps that round a
+// CTA up to a multiple of 4 warps and the warps of empty slots take them);
+// one CTA barrier; thread 0 refills both
 // stages with frames t + stages and t + 1 + stages; each warp runs the
 // column passes of its (trajectory slot, 32 x 32 sub-tile) for both frames:
 // a lane owns 2 adjacent columns x 16 rows, reading 20 row-pass pairs with
 // 64-bit loads (a half-warp reads one row's 32 columns, conflict-free).  Four
 // row-pass buffers rotate, so one barrier per two frames orders both their
 // writes and their reuse.  FP32 throughout, with the blocked accumulation of
-// the general kernel (partials over 16 frames).
+// the general kernel (partials over 16 frames).  A CTA has at most
+// kFacMaxWarps = 20 warps (96 registers a thread), enough for a whole v_x
+// class of ten trajectories on two 32-row sub-tiles.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
