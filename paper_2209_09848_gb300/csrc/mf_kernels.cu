@@ -1584,9 +1584,9 @@ __global__ void k_rescore(const TIn *__restrict__ r, int64_t fstride, int64_t rs
                 const int64_t q = qy * W + qx;
                 const double lam = lam64[q];
                 if (lam == 0.0) continue;  // masked, or no usable noise value
-                const double wt = w[b * 5 + a];
-                num += wt * lam * (sc * to_f64(r[t * fstride + qy * rstride + qx]));
-                den += wt * wt * lam;
+                const double wl = w[b * 5 + a] * lam;  // w lambda, shared by both sums
+                num = fma(wl, sc * to_f64(r[t * fstride + qy * rstride + qx]), num);
+                den = fma(w[b * 5 + a], wl, den);
             }
         }
     }
