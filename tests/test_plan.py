@@ -142,3 +142,25 @@ def test_plan_with_frame_model(mf):
         mf.prf_plan(vx, vy, T, jitter=np.full((T, 2), np.nan))
     with pytest.raises(ValueError):
         mf.prf_plan(vx, vy, T, times=np.zeros(T + 1))
+
+
+def test_factored_plans_stay_within_the_kernel_limits(mf):
+    # every factored layout the planner picks fits the kernel it runs on:
+    # at most 20 warps (the 640-thread launch bound), the shared-memory
+    # budget of one CTA and a window of at most 256 rows, over grids of
+    # different shapes, speeds and lengths
+    rng = np.random.default_rng(11)
+    for _ in range(40):
+        nx, ny = int(rng.integers(1, 30)), int(rng.integers(1, 30))
+        vmax = float(rng.choice([0.02, 0.1, 0.3, 1.0]))
+        T = int(rng.integers(8, 1300))
+        vx, vy = _grid(nx, ny, -vmax, vmax)
+        try:
+            info = mf.prf_plan(vx, vy, T)
+        except mf.MFError:
+            continue
+        if info["kernel"] != 2:
+            continue
+        warps = info["warps_per_group"] * (info["tile_h"] // 32) * (info["tile_w"] // 32)
+        assert warps <= 20, (nx, ny, vmax, T, info)
+        assert info["smem_bytes"] <= 227 * 1024 and info["window_rows"] <= 256, (nx, ny, vmax, T, info)
