@@ -1395,25 +1395,47 @@ namespace {
 __global__ void k_sel_keys(const float *__restrict__ snr_max, const int32_t *__restrict__ argmax, int64_t P,
                            unsigned long long *__restrict__ keys, unsigned int *__restrict__ hist,
                            SelState *st) {
+    // the block's bins in a shared-memory table (open addressing, bin ->
+    // count), flushed into the global histogram with one add per distinct
+    // bin: a score map's keys fall in few bins, which global atomics from
+    // every pixel would serialise on; a bin that finds the table full is
+    // added globally at once
+    constexpr int kSlots = 1024;
+    constexpr unsigned int kEmpty = 0xFFFFFFFFu;
+    __shared__ unsigned int slot_bin[kSlots], slot_cnt[kSlots];
+    for (int j = threadIdx.x; j < kSlots; j += blockDim.x) {
+        slot_bin[j] = kEmpty;
+        slot_cnt[j] = 0u;
+    }
+    __syncthreads();
     unsigned int valid = 0;  // keys this thread made; summed per warp into st->total
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long key = 0ull;
-        const bool ok = argmax[i] >= 0;
-        if (ok) {
+        if (argmax[i] >= 0) {
             uint32_t b = __float_as_uint(snr_max[i]);
             b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
             key = ((unsigned long long)b << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
             valid++;
+            const unsigned int bin = (unsigned int)(key >> 48);
+            unsigned int h = (bin * 2654435761u) >> 22;  // 10 bits
+            bool added = false;
+            for (int probe = 0; probe < kSlots; probe++, h = (h + 1) & (kSlots - 1)) {
+                const unsigned int old = atomicCAS(&slot_bin[h], kEmpty, bin);
+                if (old == kEmpty || old == bin) {
+                    atomicAdd(&slot_cnt[h], 1u);
+                    added = true;
+                    break;
+                }
+            }
+            if (!added) atomicAdd(&hist[bin], 1u);
         }
-        // lanes of the warp that fall in the same bin add together: one
-        // atomic per (warp, bin), as neighbouring pixels often share a bin
-        const unsigned int bin = ok ? (unsigned int)(key >> 48) : 0xFFFFFFFFu;  // no key: a bin of its own
-        const unsigned int peers = __match_any_sync(__activemask(), bin);
-        if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned int)__popc(peers));
         keys[i] = key;
     }
     valid = __reduce_add_sync(0xffffffffu, valid);  // blocks are whole warps
     if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&st->total, valid);
+    __syncthreads();
+    for (int j = threadIdx.x; j < kSlots; j += blockDim.x)
+        if (slot_cnt[j]) atomicAdd(&hist[slot_bin[j]], slot_cnt[j]);
 }
 
 // Histogram of the next 16 bits among keys that match the selected prefix.
